@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Throughput of the Vicsek step on GB300: particle-updates/s at N = 2^24.
+
+Workload: standard Vicsek model, N = 2^24 = 16,777,216 particles, L = 2896
+(rho = 2.0004), R = 1, v0 = 0.5, eta = 0.45, periodic, uniform isotropic random
+initial state (seeded Philox), one step = collision + streaming for every
+particle with p(t) measured on the fly.  The state (268 MB per buffer) is
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line.  --impl reference times the FP64 oracle instead, on the
+host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_FULL = 1 << 24
+L_FULL = 2896.0
+ALG_BYTES = 32          # per particle-update: 16 B record read + 16 B written
+METRIC = "particle-updates/s (N*steps/s) at N=2^24, rho=2"
+UNIT = "particle-updates/s"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, line in self.lines:
+            if not (t0 <= ts <= t1):
+                continue
+            f = [s.strip() for s in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for fn in ("aap_kernels.cu", "aap_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2211_15630_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(n):
+    """DRAM bytes per k_step launch from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_step_traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_hash") != _kernel_hash():
+        return None
+    return float(d["bytes_per_particle"]) * n
+
+
+def _cpu_baseline(eta, budget_s=20.0):
+    """The oracle as it stands, on all host cores, on the full workload for as
+    many steps as fit in about budget_s seconds (at least one)."""
+    import oracle as O
+
+    O.build()
+    cores = os.cpu_count() or 1
+    m = O.Model(n=N_FULL, lx=L_FULL, ly=L_FULL, r=1.0, v=0.5, eta=eta, seed=1)
+    x, y, th = O.init_state(m)
+    steps, t_used = 0, 0.0
+    while t_used < budget_s and steps < 50:
+        t0 = time.perf_counter()
+        x, y, th, _ = O.run(m, x, y, th, steps, 1, threads=cores)
+        t_used += time.perf_counter() - t0
+        steps += 1
+    return {"value": N_FULL * steps / t_used, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full steps of the N=2^24, L=2896 workload from the Philox initial "
+                      f"state ({t_used:.1f} s, OpenMP over {cores} threads)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return 0
+    import oracle as O
+
+    O.build()
+    cores = os.cpu_count() or 1
+    n_s, l_s = 1 << 16, 181.0           # same density (rho = 2.0003), same per-particle work
+    m = O.Model(n=n_s, lx=l_s, ly=l_s, r=1.0, v=0.5, eta=args.eta, seed=1)
+    x, y, th = O.init_state(m)
+    x, y, th, _ = O.run(m, x, y, th, 0, args.warmup, threads=cores)
+    t0 = time.perf_counter()
+    x, y, th, _ = O.run(m, x, y, th, args.warmup, args.steps, threads=cores)
+    dt = time.perf_counter() - t0
+    val = n_s * args.steps / dt
+    sample = (f"each step a full update of a 2^16-particle sample of the workload at the same "
+              f"density (L=181, rho=2.0003, eta={args.eta}); {args.steps} steps in {dt:.2f} s")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "vicsek_N2^24_L2896_rho2", "sample_n": n_s, "eta": args.eta},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--eta", type=float, default=0.45)
+    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--L", type=float, default=L_FULL)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--tile", type=str, default="0x0")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import paper_2211_15630_gb300 as A
+    from paper_2211_15630_gb300 import build as B
+
+    if rank == 0 or world == 1:
+        B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        B.build()
+    stream = torch.cuda.Stream()
+    tw, th_ = (int(v) for v in args.tile.split("x"))
+
+    def make(eta, seed):
+        p = A.aap_params_default(n=args.n, lx=args.L, ly=args.L, r=1.0, v=0.5, eta=eta,
+                                 seed=seed, threads=args.threads, tile_w=tw, tile_h=th_)
+        return p, A.aap_create(p, stream.cuda_stream)
+
+    def timed(h, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        A.aap_step(h, k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    p, h = make(args.eta, 1 + rank)
+    lay = A.aap_get_layout(h)
+    A.aap_step(h, args.warmup)
+    A.aap_sync(h)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    A.aap_set_timing(h, True)
+    t_begin = time.perf_counter()
+    ms = timed(h, args.steps)
+    t_end = time.perf_counter()
+    kms, klaunch = A.aap_get_timing(h)
+    A.aap_set_timing(h, False)
+    clocks.stop()
+    A.aap_sync(h)
+    obs = A.aap_observe(h)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * args.n * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers: upload the state from
+    # pinned memory, K steps recording p(t) into host memory, download the state
+    xs, ys, ts = A.aap_get_state(h, args.n)
+    px = torch.from_numpy(xs).pin_memory().numpy()
+    py = torch.from_numpy(ys).pin_memory().numpy()
+    pt = torch.from_numpy(ts).pin_memory().numpy()
+    ke = args.e2e_steps
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    A.aap_set_state(h, px, py, pt, step=obs.step)
+    phi = A.aap_phi_trace(h, ke)
+    xs2, ys2, ts2 = A.aap_get_state(h, args.n)
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_val = world * args.n * ke / float(e2e_t.item())
+    state_bytes = args.n * (8 + 8 + 4)
+    A.aap_destroy(h)
+
+    extras = {}
+    if not args.no_extras and world == 1:
+        for eta in (0.2, 0.7):
+            if abs(eta - args.eta) < 1e-9:
+                continue
+            pe, he = make(eta, 1)
+            A.aap_step(he, args.warmup)
+            msx = timed(he, max(args.steps // 4, 50))
+            extras[f"eta_{eta}"] = args.n * max(args.steps // 4, 50) / (msx / 1e3)
+            A.aap_destroy(he)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    peak, peak_kind = _peaks()
+    kstep_ms = kms[0] / max(klaunch[0], 1)
+    achieved = ALG_BYTES * args.n / (kstep_ms / 1e3) / 1e9
+    traffic = _traffic(args.n)
+    csum = clocks.summary(t_begin, t_end)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (uniform isotropic Philox initial state)",
+        "config": {"workload": "vicsek_N2^24_L2896_rho2", "n": args.n, "L": args.L, "R": 1.0,
+                   "v0": 0.5, "eta": args.eta, "boundary": "periodic", "l2": "state > L2 (no flush)",
+                   "tile": [lay.tile_w, lay.tile_h], "threads": lay.threads,
+                   "stage_cap": lay.stage_cap, "parallelism": "replicas only" if world > 1 else "1 gpu"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_step",
+                     "kernel_ms": kstep_ms, "peak_kind": peak_kind,
+                     "alg_bytes_per_update": ALG_BYTES},
+        "step_kernels_ms": {"k_step": kstep_ms, "k_deferred": kms[1] / max(klaunch[1], 1),
+                            "k_finish": kms[2] / max(klaunch[2], 1)},
+        "e2e": {"value": e2e_val, "unit": UNIT, "steps": ke,
+                "h2d_bytes_per_step": state_bytes / ke,
+                "d2h_bytes_per_step": (state_bytes + 8 * (ke + 1)) / ke},
+        "gpu_launches": 3 * args.steps,
+        "clocks": csum,
+        "phi_end": float(phi[-1]),
+        "mean_neighbours": obs.mean_neighbours,
+        "frac_of_hbm_roofline": value * ALG_BYTES / (peak * 1e9),
+    }
+    if extras:
+        line["extras"] = extras
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(args.eta)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

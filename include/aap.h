@@ -1,0 +1,205 @@
+/*
+ * aap.h -- C ABI of the GB300 (sm_103a) aligning-active-particles library.
+ *
+ * The library advances N self-propelled particles in a 2-D box with the
+ * alignment rules of Kuersten, "Aligning Active Particles Py Package" (CPC):
+ * the Vicsek collision and streaming rule (Sec. 2.1, Eq. collision_VM and
+ * Eq. streaming), its nematic variant (Eq. collision_NVM), and the overdamped
+ * Langevin alignment dynamics integrated by Euler-Maruyama (Sec. 2.2,
+ * Eq. Langevin_dynamics), with the metric neighbourhood
+ * Omega_i = { j != i : |r_i - r_j| <= R } (Eq. metric_neighborhood) found
+ * through cell lists (Sec. 3.2) and periodic or reflecting boundaries per axis
+ * (Sec. 2.4).  Every step runs in the library's own CUDA kernels on the
+ * caller's stream.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status: AAP_OK (0) or a negative AAP_E*
+ *    code.  aap_last_error() returns a message for the calling thread's last
+ *    failure.  On failure no output argument is written except where stated.
+ *  - Handles are opaque.  The library owns all device memory it allocates and
+ *    frees it in the matching *_destroy.  Host buffers passed in are owned by
+ *    the caller and are only read or written during the call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work of a handle is ordered on that stream.
+ *  - Calls that return data to host memory (aap_observe, aap_phi_trace,
+ *    aap_get_state, aap_step_neighbours, aap_ens_phi_mean, aap_ens_get_state)
+ *    synchronise the stream; aap_step and aap_ens_step only enqueue work.
+ *  - A handle is not thread-safe; different handles may be used from
+ *    different threads.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the seed,
+ *    counter (particle id, step low word, step high word, 0) for the dynamics
+ *    and (id, 0, 0, 1) for the initial state; uniforms are
+ *    ((w >> 9) + 1/2) 2^-23.  The paper's own program used a Mersenne
+ *    twister (Sec. 3.1); trajectories are therefore not comparable to it.
+ */
+#ifndef AAP_H
+#define AAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define AAP_OK          0
+#define AAP_EINVAL    (-1)   /* invalid argument or parameter set            */
+#define AAP_ENOMEM    (-2)   /* device or host allocation failed             */
+#define AAP_ECUDA     (-3)   /* a CUDA runtime call failed                   */
+#define AAP_ETIMEOUT  (-4)   /* a bounded device wait gave up                */
+#define AAP_ENAN      (-5)   /* a non-finite value reached the state         */
+#define AAP_ESTATE    (-6)   /* handle in an unusable state (after a fault)  */
+#define AAP_EOVERFLOW (-7)   /* more particles in a tile than it can hold    */
+
+/* ---- models (Sec. 2) ----------------------------------------------------- */
+#define AAP_VM        0      /* Vicsek model, Eq. (collision_VM)              */
+#define AAP_LANGEVIN  1      /* overdamped Langevin, Eq. (Langevin_dynamics)  */
+#define AAP_NVM       2      /* nematic Vicsek model, Eq. (collision_NVM)     */
+
+/* weight function h of Eq. (Langevin_dynamics), Sec. 2.2 */
+#define AAP_H_INV_1PN 0      /* h(n) = 1/(1+n): "nonadditiveL" (the default)  */
+#define AAP_H_ONE     1      /* h(n) = 1:       "additiveL"                   */
+
+/* Observation flags (aap_obs.flags). */
+#define AAP_FLAG_SPILLED  1  /* some tile region overflowed into the spill list
+                                (results stay exact; the layout was enlarged) */
+
+/*
+ * Model parameters, named as in the paper's parameter list (Sec. 4).
+ * Positions live in [0,Lx] x [0,Ly]; orientations in [-pi, pi).
+ * Constraints checked by aap_create (AAP_EINVAL otherwise):
+ *   n >= 0, n < 2^31; lx, ly, r > 0 and finite; floor(L/R) >= 3 on both axes
+ *   (a 3x3 cell stencil must not see a cell twice); v >= 0 and the per-step
+ *   displacement v (VM, NVM) or v*dt (Langevin) at most one cell side;
+ *   eta >= 0 (eta <= 1 is the paper's range for the VM but not enforced);
+ *   dt > 0 for the Langevin model; order >= 1; model, weight as defined above.
+ */
+typedef struct aap_params {
+    int64_t  n;          /* particle number N                                   */
+    double   lx, ly;     /* box size Lx, Ly                                     */
+    double   r;          /* interaction radius R                                */
+    double   v;          /* speed v                                             */
+    double   eta;        /* noise strength eta                                  */
+    double   omega;      /* chirality omega                                     */
+    double   gamma;      /* coupling Gamma (Langevin)                           */
+    double   dt;         /* Euler-Maruyama step (Langevin; ignored by VM/NVM)   */
+    uint64_t seed;       /* Philox key                                          */
+    int32_t  model;      /* AAP_VM, AAP_LANGEVIN or AAP_NVM                     */
+    int32_t  order;      /* interaction order o (Langevin), 1 = polar           */
+    int32_t  weight;     /* AAP_H_INV_1PN or AAP_H_ONE (Langevin)               */
+    int32_t  bx, by;     /* 0 periodic, nonzero reflecting (per axis)           */
+    int32_t  tile_w;     /* cells per tile along x; 0 = automatic               */
+    int32_t  tile_h;     /* cells per tile along y; 0 = automatic               */
+    int32_t  threads;    /* threads per block of the step kernel; 0 = automatic */
+    double   capacity;   /* tile-region capacity over the mean occupancy;
+                            0 = automatic (4)                                   */
+} aap_params;
+
+/* Observables of the current state (Sec. 3.4). */
+typedef struct aap_obs {
+    double  phi;              /* polar order p = |sum e^{i theta}| / N          */
+    double  q;                /* nematic order q = |sum e^{2 i theta}| / N      */
+    double  mean_neighbours;  /* mean |Omega_i| measured by the last step
+                                 (NaN before the first step)                    */
+    int64_t step;             /* number of steps taken                          */
+    int32_t flags;            /* AAP_FLAG_* bits                                */
+    int32_t reserved;
+} aap_obs;
+
+/* Geometry and memory layout chosen for a handle (for tests and tools). */
+typedef struct aap_layout {
+    int32_t ncx, ncy;         /* cells per axis, floor(L/R) (Sec. 3.2)          */
+    int32_t ntx, nty;         /* tiles per axis                                 */
+    int32_t tile_w, tile_h;   /* largest tile in cells                          */
+    int32_t fix_bits_x;       /* fixed-point bits per cell side, x              */
+    int32_t fix_bits_y;       /* fixed-point bits per cell side, y              */
+    int32_t threads;          /* threads per block of the step kernel           */
+    int32_t stage_cap;        /* particles a block stages in shared memory      */
+    int64_t tile_slots;       /* particle slots per tile                        */
+    int64_t device_bytes;     /* device memory held by the handle               */
+    double  cell_x, cell_y;   /* cell sides L/floor(L/R)                        */
+} aap_layout;
+
+typedef struct aap_handle aap_handle;
+
+/* Message of the calling thread's last failure ("" if none).  The pointer
+ * stays valid until the next call from the same thread. */
+const char *aap_last_error(void);
+
+/* ABI version of this header (bumped on any incompatible change). */
+int32_t aap_abi_version(void);
+
+/* Fill *p with this library's defaults: N = 1000, Lx = Ly = 32, R = 1, v = 0.5,
+ * eta = 0.4, omega = 0, Gamma = 1, dt = 0.01, seed = 1, VM, order 1,
+ * h(n) = 1/(1+n) (the paper's default weight, Sec. 4), periodic on both axes,
+ * automatic tiling.  Never fails. */
+void aap_params_default(aap_params *p);
+
+/* Create a system: validate *p, allocate device memory, draw the uniform
+ * isotropic initial state (positions U(0,L), angles U(-pi,pi); the initial
+ * condition of Fig. runtime) from Philox with tag 1, and build the cell lists.
+ * Mirrors aappp_init (Sec. 4).  On success *out is a new handle, step = 0.
+ * Errors: AAP_EINVAL (parameters, NULL out), AAP_ENOMEM, AAP_ECUDA. */
+int aap_create(const aap_params *p, void *stream, aap_handle **out);
+
+/* Free every resource of h (NULL is accepted).  Synchronises h's stream. */
+int aap_destroy(aap_handle *h);
+
+/* Advance nsteps >= 0 time steps: for the VM and NVM one collision followed by
+ * streaming (Sec. 2.1); for the Langevin model one Euler-Maruyama step of
+ * length dt (Sec. 2.2); then the boundary rule of Sec. 2.4.  Every step also
+ * measures p and the mean neighbour number on the fly.  Enqueues work only.
+ * Mirrors <model>_update_timesteps (Sec. 4). */
+int aap_step(aap_handle *h, int64_t nsteps);
+
+/* Record p(t) for the current state and after each of nsteps steps:
+ * phi_out[0..nsteps] (nsteps + 1 host doubles, caller-owned).  Like
+ * <model>_measurement_timesteps (Sec. 4), which uses states t = 0..n-1 of the
+ * n+1 visited (Sec. 3.4); here all n+1 values are returned. */
+int aap_phi_trace(aap_handle *h, int64_t nsteps, double *phi_out);
+
+/* Observables of the current state (Sec. 3.4): p, q, the mean neighbour number
+ * measured by the last step, the step count and flags.  Synchronises.
+ * Errors: AAP_EOVERFLOW if particles were lost to an overflow, AAP_ENAN if an
+ * orientation became non-finite. */
+int aap_observe(aap_handle *h, aap_obs *out);
+
+/* Copy the state to host buffers indexed by particle id: x[i], y[i] (FP64,
+ * the exact value of the device's fixed-point position) and theta[i] (FP32,
+ * in [-pi, pi)).  n must equal N.  Synchronises. */
+int aap_get_state(aap_handle *h, double *x, double *y, float *theta, int64_t n);
+
+/* Replace the state by host arrays indexed by particle id (x in [0,Lx],
+ * y in [0,Ly], finite theta; n must equal N) and set the step counter, which
+ * keys the noise of the next step.  Positions are rounded to the fixed-point
+ * grid (2^-fix_bits of a cell side).  Synchronises.  Errors: AAP_EINVAL for
+ * positions outside the box or non-finite values (the state is unchanged). */
+int aap_set_state(aap_handle *h, const double *x, const double *y, const float *theta,
+                  int64_t n, int64_t step);
+
+/* Take one step and write |Omega_i| of the state before it to nbr_out[i]
+ * (host, N int32, by particle id).  Synchronises. */
+int aap_step_neighbours(aap_handle *h, int32_t *nbr_out, int64_t n);
+
+/* Block until all work enqueued on h has finished; report device-side errors
+ * (AAP_EOVERFLOW, AAP_ENAN, AAP_ECUDA). */
+int aap_sync(aap_handle *h);
+
+/* Geometry and memory layout of h. */
+int aap_get_layout(aap_handle *h, aap_layout *out);
+
+/* Per-kernel timing (tracing aid).  enable != 0: every step enqueued by
+ * aap_step / aap_phi_trace / aap_step_neighbours records CUDA events on h's
+ * stream around its three kernels (the tile step, the deferred-tile step and
+ * the step finish); the accumulated times restart from zero at each call. */
+int aap_set_timing(aap_handle *h, int32_t enable);
+
+/* Milliseconds and launch counts accumulated since aap_set_timing:
+ * index 0 the tile step kernel, 1 the deferred-tile kernel, 2 the finish
+ * kernel (ms[3], launches[3], caller-owned host arrays).  Synchronises. */
+int aap_get_timing(aap_handle *h, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AAP_H */

@@ -1,0 +1,187 @@
+"""Python binding of libaap.so, the GB300 aligning-active-particles library.
+
+Argument marshalling only: every function here calls the C entry point of the
+same name declared in include/aap.h; all computation runs in the library's
+CUDA kernels.  PyTorch is used by callers only for streams and device memory.
+If the compiled library is missing, importing the binding raises -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaap.so")
+
+AAP_OK, AAP_EINVAL, AAP_ENOMEM, AAP_ECUDA, AAP_ETIMEOUT, AAP_ENAN, AAP_ESTATE, AAP_EOVERFLOW = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+AAP_VM, AAP_LANGEVIN, AAP_NVM = 0, 1, 2
+AAP_H_INV_1PN, AAP_H_ONE = 0, 1
+AAP_FLAG_SPILLED = 1
+
+# Every symbol include/aap.h declares (checked by the tests).
+EXPORTS = (
+    "aap_last_error", "aap_abi_version", "aap_params_default", "aap_create", "aap_destroy",
+    "aap_step", "aap_phi_trace", "aap_observe", "aap_get_state", "aap_set_state",
+    "aap_step_neighbours", "aap_sync", "aap_get_layout", "aap_set_timing", "aap_get_timing",
+)
+
+
+class AapError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"aap error {code}: {msg}")
+        self.code = code
+
+
+class aap_params(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("lx", C.c_double), ("ly", C.c_double), ("r", C.c_double),
+        ("v", C.c_double), ("eta", C.c_double), ("omega", C.c_double), ("gamma", C.c_double),
+        ("dt", C.c_double), ("seed", C.c_uint64), ("model", C.c_int32), ("order", C.c_int32),
+        ("weight", C.c_int32), ("bx", C.c_int32), ("by", C.c_int32), ("tile_w", C.c_int32),
+        ("tile_h", C.c_int32), ("threads", C.c_int32), ("capacity", C.c_double),
+    ]
+
+
+class aap_obs(C.Structure):
+    _fields_ = [("phi", C.c_double), ("q", C.c_double), ("mean_neighbours", C.c_double),
+                ("step", C.c_int64), ("flags", C.c_int32), ("reserved", C.c_int32)]
+
+
+class aap_layout(C.Structure):
+    _fields_ = [("ncx", C.c_int32), ("ncy", C.c_int32), ("ntx", C.c_int32), ("nty", C.c_int32),
+                ("tile_w", C.c_int32), ("tile_h", C.c_int32), ("fix_bits_x", C.c_int32),
+                ("fix_bits_y", C.c_int32), ("threads", C.c_int32), ("stage_cap", C.c_int32),
+                ("tile_slots", C.c_int64), ("device_bytes", C.c_int64), ("cell_x", C.c_double),
+                ("cell_y", C.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libaap.so (built by paper_2211_15630_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2211_15630_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    P = C.POINTER
+    sig = {
+        "aap_last_error": (C.c_char_p, []),
+        "aap_abi_version": (i32, []),
+        "aap_params_default": (None, [P(aap_params)]),
+        "aap_create": (C.c_int, [P(aap_params), vp, P(vp)]),
+        "aap_destroy": (C.c_int, [vp]),
+        "aap_step": (C.c_int, [vp, i64]),
+        "aap_phi_trace": (C.c_int, [vp, i64, vp]),
+        "aap_observe": (C.c_int, [vp, P(aap_obs)]),
+        "aap_get_state": (C.c_int, [vp, vp, vp, vp, i64]),
+        "aap_set_state": (C.c_int, [vp, vp, vp, vp, i64, i64]),
+        "aap_step_neighbours": (C.c_int, [vp, vp, i64]),
+        "aap_sync": (C.c_int, [vp]),
+        "aap_get_layout": (C.c_int, [vp, P(aap_layout)]),
+        "aap_set_timing": (C.c_int, [vp, i32]),
+        "aap_get_timing": (C.c_int, [vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != AAP_OK:
+        raise AapError(rc, load().aap_last_error().decode())
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def aap_params_default(**kw) -> aap_params:
+    p = aap_params()
+    load().aap_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def aap_create(params: aap_params, stream: int | None = None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(load().aap_create(C.byref(params), C.c_void_p(stream or 0), C.byref(h)))
+    return h
+
+
+def aap_destroy(h) -> None:
+    _check(load().aap_destroy(h))
+
+
+def aap_step(h, nsteps: int) -> None:
+    _check(load().aap_step(h, int(nsteps)))
+
+
+def aap_sync(h) -> None:
+    _check(load().aap_sync(h))
+
+
+def aap_observe(h) -> aap_obs:
+    o = aap_obs()
+    _check(load().aap_observe(h, C.byref(o)))
+    return o
+
+
+def aap_phi_trace(h, nsteps: int) -> np.ndarray:
+    out = np.zeros(int(nsteps) + 1, np.float64)
+    _check(load().aap_phi_trace(h, int(nsteps), _p(out)))
+    return out
+
+
+def aap_get_state(h, n: int):
+    x = np.zeros(n, np.float64); y = np.zeros(n, np.float64); th = np.zeros(n, np.float32)
+    _check(load().aap_get_state(h, _p(x), _p(y), _p(th), int(n)))
+    return x, y, th
+
+
+def aap_set_state(h, x, y, th, step: int = 0) -> None:
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    th = np.ascontiguousarray(th, np.float32)
+    _check(load().aap_set_state(h, _p(x), _p(y), _p(th), x.size, int(step)))
+
+
+def aap_step_neighbours(h, n: int) -> np.ndarray:
+    out = np.zeros(n, np.int32)
+    _check(load().aap_step_neighbours(h, _p(out), int(n)))
+    return out
+
+
+def aap_get_layout(h) -> aap_layout:
+    lay = aap_layout()
+    _check(load().aap_get_layout(h, C.byref(lay)))
+    return lay
+
+
+def aap_set_timing(h, enable: bool) -> None:
+    _check(load().aap_set_timing(h, int(bool(enable))))
+
+
+def aap_get_timing(h):
+    """(ms[3], launches[3]) of the tile step, deferred-tile and finish kernels."""
+    ms = np.zeros(3, np.float64)
+    cnt = np.zeros(3, np.int64)
+    _check(load().aap_get_timing(h, _p(ms), _p(cnt)))
+    return ms, cnt
+
+
+def aap_abi_version() -> int:
+    return int(load().aap_abi_version())

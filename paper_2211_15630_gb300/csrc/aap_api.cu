@@ -1,0 +1,655 @@
+// aap_api.cu -- the C ABI declared in include/aap.h.
+//
+// Host side of one simulated system: parameter checks, geometry and memory
+// layout, device allocations, the step loop (optionally replayed from a
+// captured CUDA graph), and the transfers in and out of host memory.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/aap.h"
+#include "aap_internal.cuh"
+#include "aap_kernels.cuh"
+
+using aapk::Ctl;
+using aapk::LaunchCfg;
+using aapk::Sys;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define AAP_CK(call)                                                                    \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(AAP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    return n;
+}
+
+}  // namespace
+
+struct aap_handle {
+    aap_params p{};
+    cudaStream_t stream = nullptr;
+    Sys hs{};                       // host copy of the device descriptor
+    Sys *d_sys = nullptr;
+    int *d_tile_base = nullptr;
+    Ctl *d_ctl = nullptr;
+    int *d_defer = nullptr;
+    unsigned char *d_scratch = nullptr;
+    unsigned long long *d_obs = nullptr;
+    int *d_seen = nullptr;
+    double *d_trace = nullptr, *d_trace_nbar = nullptr;
+    long long trace_alloc = 0;
+    int *d_nbr = nullptr;
+    double *d_x = nullptr, *d_y = nullptr;
+    float *d_th = nullptr;
+    LaunchCfg L{};
+    long long step = 0;
+    int flags = 0;
+    bool broken = false;
+    size_t bytes = 0;
+    std::vector<void *> allocs;
+    int ncx = 0, ncy = 0;
+    double csx = 0, csy = 0;
+    // captured step graph
+    cudaGraphExec_t gexec = nullptr;
+    int gsteps = 0;
+    // per-kernel timing (aap_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    size_t ev_used = 0;
+    double ms[3] = {0, 0, 0};
+    long long launches[3] = {0, 0, 0};
+};
+
+namespace {
+
+template <typename T>
+int dev_alloc(aap_handle *h, T **ptr, size_t bytes)
+{
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AAP_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(p);
+    h->bytes += bytes;
+    *ptr = static_cast<T *>(p);
+    return AAP_OK;
+}
+
+void free_all(aap_handle *h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    h->events.clear();
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+bool finite(double v) { return std::isfinite(v); }
+
+int check_params(const aap_params *p)
+{
+    if (!p) return fail(AAP_EINVAL, "params is NULL");
+    if (p->n < 0 || p->n >= (1ll << 31)) return fail(AAP_EINVAL, "n must be in [0, 2^31)");
+    if (!finite(p->lx) || !finite(p->ly) || !finite(p->r) || !(p->lx > 0) || !(p->ly > 0) || !(p->r > 0))
+        return fail(AAP_EINVAL, "lx, ly and r must be finite and positive");
+    if (std::floor(p->lx / p->r) < 3 || std::floor(p->ly / p->r) < 3)
+        return fail(AAP_EINVAL, "the box must hold at least 3 cells of side >= R per axis (L >= 3R)");
+    if (std::floor(p->lx / p->r) > (1 << 26) || std::floor(p->ly / p->r) > (1 << 26))
+        return fail(AAP_EINVAL, "more than 2^26 cells per axis");
+    if (!finite(p->v) || p->v < 0) return fail(AAP_EINVAL, "v must be finite and >= 0");
+    if (!finite(p->eta) || p->eta < 0) return fail(AAP_EINVAL, "eta must be finite and >= 0");
+    if (!finite(p->omega) || !finite(p->gamma)) return fail(AAP_EINVAL, "omega and gamma must be finite");
+    if (p->model != AAP_VM && p->model != AAP_LANGEVIN && p->model != AAP_NVM)
+        return fail(AAP_EINVAL, "model must be AAP_VM, AAP_LANGEVIN or AAP_NVM");
+    if (p->model == AAP_LANGEVIN && (!finite(p->dt) || !(p->dt > 0)))
+        return fail(AAP_EINVAL, "dt must be finite and positive for the Langevin model");
+    if (p->order < 1 || p->order > 64) return fail(AAP_EINVAL, "order must be in [1, 64]");
+    if (p->weight != AAP_H_INV_1PN && p->weight != AAP_H_ONE)
+        return fail(AAP_EINVAL, "weight must be AAP_H_INV_1PN or AAP_H_ONE");
+    const double cs = std::min(p->lx / std::floor(p->lx / p->r), p->ly / std::floor(p->ly / p->r));
+    const double disp = p->model == AAP_LANGEVIN ? p->v * p->dt : p->v;
+    if (disp > cs)
+        return fail(AAP_EINVAL, "the displacement per step (v, or v*dt) must not exceed one cell side");
+    if (p->tile_w < 0 || p->tile_h < 0 || p->tile_w > aapk::kMaxTile || p->tile_h > aapk::kMaxTile)
+        return fail(AAP_EINVAL, "tile_w and tile_h must be 0 (automatic) or in [6, 64]");
+    if ((p->tile_w && p->tile_w < 6) || (p->tile_h && p->tile_h < 6))
+        return fail(AAP_EINVAL, "tile_w and tile_h must be 0 (automatic) or in [6, 64]");
+    if (p->threads != 0 && p->threads != 128 && p->threads != 256 && p->threads != 512)
+        return fail(AAP_EINVAL, "threads must be 0, 128, 256 or 512");
+    if (!finite(p->capacity) || p->capacity < 0 || (p->capacity > 0 && p->capacity < 1))
+        return fail(AAP_EINVAL, "capacity must be 0 (automatic) or >= 1");
+    return AAP_OK;
+}
+
+int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+int fix_bits(int wmax)
+{
+    int s = 0;
+    while (((long long)(wmax + 2) << (s + 1)) <= 2147483647ll && s < 28) ++s;
+    return s;
+}
+
+// Region capacities and the per-tile layout.
+void layout_regions(Sys &S, double mu, double factor)
+{
+    const int wi = std::max(S.twmax - 2, 1), hi = std::max(S.thmax - 2, 1);
+    int cells[aapk::kRegions];
+    for (int ry = 0; ry < 3; ++ry)
+        for (int rx = 0; rx < 3; ++rx) {
+            const int cw = rx == 1 ? wi : 1, ch = ry == 1 ? hi : 1;
+            cells[ry * 3 + rx] = cw * ch;
+        }
+    int off = 0;
+    for (int r = 0; r < aapk::kRegions; ++r) {
+        const double want = factor * mu * cells[r] + 4.0 * std::sqrt(mu * cells[r] + 1.0) + 24.0;
+        const int cap = aapk::round_up((int)std::ceil(want), 4);
+        S.cap[r] = cap;
+        S.off[r] = off;
+        off += cap;
+    }
+    S.tile_slots = aapk::round_up(off, 4);
+}
+
+int build_layout(aap_handle *h)
+{
+    const aap_params &p = h->p;
+    Sys &S = h->hs;
+    h->ncx = (int)std::floor(p.lx / p.r);
+    h->ncy = (int)std::floor(p.ly / p.r);
+    h->csx = p.lx / h->ncx;
+    h->csy = p.ly / h->ncy;
+    S.ncx = h->ncx;
+    S.ncy = h->ncy;
+    const int nsm = sm_count();
+    int tw = p.tile_w ? p.tile_w : 32, th = p.tile_h ? p.tile_h : 16;
+    if (!p.tile_w && !p.tile_h) {
+        // small systems: shrink tiles until there are a few per SM
+        while ((long long)ceil_div(S.ncx, tw) * ceil_div(S.ncy, th) < 2ll * nsm && (tw > 8 || th > 8)) {
+            if (tw >= th && tw > 8) tw /= 2; else if (th > 8) th /= 2; else break;
+        }
+    }
+    S.ntx = ceil_div(S.ncx, std::min(tw, S.ncx));
+    S.nty = ceil_div(S.ncy, std::min(th, S.ncy));
+    S.twmax = ceil_div(S.ncx, S.ntx);
+    S.thmax = ceil_div(S.ncy, S.nty);
+    if (S.twmax > aapk::kMaxTile || S.thmax > aapk::kMaxTile)
+        return fail(AAP_EINVAL, "tile larger than 64 cells");
+    if ((long long)S.ntx * S.nty >= (1ll << 27)) return fail(AAP_EINVAL, "too many tiles");
+    S.ntiles = S.ntx * S.nty;
+    S.sx = fix_bits(S.twmax);
+    S.sy = fix_bits(S.thmax);
+    S.lx = p.lx;
+    S.ly = p.ly;
+    S.csx_d = h->csx;
+    S.csy_d = h->csy;
+    S.ux = (float)(h->csx / (double)(1ll << S.sx));
+    S.uy = (float)(h->csy / (double)(1ll << S.sy));
+    const double disp = p.model == AAP_LANGEVIN ? p.v * p.dt : p.v;
+    S.kx = (float)(disp / h->csx * (double)(1ll << S.sx));
+    S.ky = (float)(disp / h->csy * (double)(1ll << S.sy));
+    S.r2 = (float)(p.r * p.r);
+    S.model = p.model;
+    S.order = p.model == AAP_LANGEVIN ? p.order : 1;
+    S.weight = p.weight;
+    S.bx = p.bx != 0;
+    S.by = p.by != 0;
+    S.eta_pi = (float)(p.eta * M_PI);
+    S.omega_step = (float)(p.model == AAP_LANGEVIN ? p.omega * p.dt : p.omega);
+    S.gamma_dt = (float)(p.gamma * p.dt);
+    S.noise_amp = (float)(p.eta * std::sqrt(p.dt));
+    S.seed_lo = (uint32_t)p.seed;
+    S.seed_hi = (uint32_t)(p.seed >> 32);
+    S.n = p.n;
+    const double mu = (double)p.n / ((double)S.ncx * S.ncy);
+    const double factor = p.capacity > 0 ? p.capacity : 4.0;
+    layout_regions(S, mu, factor);
+    S.spill_cap = (int)std::min<long long>(4096, p.n / 16 + 256);
+    // shared-memory staging capacity: about twice the mean tile + ring load
+    const int nce = (S.twmax + 2) * (S.thmax + 2);
+    const double mean_stage = mu * nce;
+    int scap = aapk::round_up((int)std::ceil(1.75 * mean_stage + 128.0), 64);
+    scap = std::min(scap, 4096);
+    S.stage_cap = scap;
+    int own = S.tile_slots;
+    int halo = 2 * (2 * S.cap[0] + S.cap[1]) + 2 * (2 * S.cap[0] + S.cap[3]) + 4 * S.cap[0];
+    long long scr = (long long)own + halo + 4ll * S.spill_cap;
+    if (scr > 65535) scr = 65535;
+    if ((long long)own + halo > 65535)
+        return fail(AAP_EINVAL, "tile capacity too large (reduce tile size or capacity)");
+    S.scratch_cap = (int)scr;
+    int threads = p.threads ? p.threads : 256;
+    LaunchCfg &L = h->L;
+    L.threads = threads;
+    L.stage_cap = scap;
+    L.nce_max = nce;
+    const size_t smem = aapk::step_smem_bytes(scap, nce);
+    AAP_CK(aapk::configure_step_kernels(threads, smem));
+    int bps = 0;
+    AAP_CK(aapk::step_blocks_per_sm(threads, smem, &bps));
+    if (bps < 1) return fail(AAP_EINVAL, "step kernel does not fit on an SM with this tiling");
+    L.grid_step = std::max(1, std::min(S.ntiles, bps * nsm));
+    L.grid_defer = std::max(1, std::min(S.ntiles, nsm));
+    L.grid_finish = std::max(1, std::min(256, ceil_div((long long)S.ntiles * aapk::kCntStride, 256)));
+    L.scratch_cap = S.scratch_cap;
+    L.scratch_per_block = aapk::stage_particle_bytes(S.scratch_cap) + aapk::spill_list_bytes(S.scratch_cap);
+    L.scratch_per_block = (L.scratch_per_block + 255) / 256 * 256;
+    L.nsys = 1;
+    return AAP_OK;
+}
+
+int push_sys(aap_handle *h)
+{
+    AAP_CK(cudaMemcpyAsync(h->d_sys, &h->hs, sizeof(Sys), cudaMemcpyHostToDevice, h->stream));
+    return AAP_OK;
+}
+
+int alloc_all(aap_handle *h)
+{
+    Sys &S = h->hs;
+    int rc;
+    const size_t slots = (size_t)S.ntiles * S.tile_slots;
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = dev_alloc(h, &S.rec[b], slots * sizeof(int4)))) return rc;
+        if ((rc = dev_alloc(h, &S.cnt[b], (size_t)S.ntiles * aapk::kCntStride * sizeof(int)))) return rc;
+        if ((rc = dev_alloc(h, &S.spill_rec[b], (size_t)S.spill_cap * sizeof(int4)))) return rc;
+        if ((rc = dev_alloc(h, &S.spill_key[b], (size_t)S.spill_cap * sizeof(int)))) return rc;
+    }
+    if ((rc = dev_alloc(h, &S.spill_cnt, 2 * sizeof(int)))) return rc;
+    if ((rc = dev_alloc(h, &S.acc, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long)))) return rc;
+    if ((rc = dev_alloc(h, &S.last, 4 * sizeof(double)))) return rc;
+    if ((rc = dev_alloc(h, &S.err, sizeof(int)))) return rc;
+    if ((rc = dev_alloc(h, &h->d_sys, sizeof(Sys)))) return rc;
+    if ((rc = dev_alloc(h, &h->d_tile_base, 2 * sizeof(int)))) return rc;
+    if ((rc = dev_alloc(h, &h->d_ctl, sizeof(Ctl)))) return rc;
+    if ((rc = dev_alloc(h, &h->d_defer, (size_t)S.ntiles * sizeof(int)))) return rc;
+    if ((rc = dev_alloc(h, &h->d_scratch, h->L.scratch_per_block * h->L.grid_defer))) return rc;
+    if ((rc = dev_alloc(h, &h->d_obs, 8 * sizeof(unsigned long long)))) return rc;
+    if ((rc = dev_alloc(h, &h->d_seen, sizeof(int)))) return rc;
+    for (int b = 0; b < 2; ++b) {
+        AAP_CK(cudaMemsetAsync(S.cnt[b], 0, (size_t)S.ntiles * aapk::kCntStride * sizeof(int), h->stream));
+    }
+    AAP_CK(cudaMemsetAsync(S.spill_cnt, 0, 2 * sizeof(int), h->stream));
+    AAP_CK(cudaMemsetAsync(S.acc, 0, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long), h->stream));
+    AAP_CK(cudaMemsetAsync(S.last, 0, 4 * sizeof(double), h->stream));
+    AAP_CK(cudaMemsetAsync(S.err, 0, sizeof(int), h->stream));
+    AAP_CK(cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), h->stream));
+    int tb[2] = {0, S.ntiles};
+    AAP_CK(cudaMemcpyAsync(h->d_tile_base, tb, sizeof(tb), cudaMemcpyHostToDevice, h->stream));
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    LaunchCfg &L = h->L;
+    L.sys = h->d_sys;
+    L.tile_base = h->d_tile_base;
+    L.ctl = h->d_ctl;
+    L.defer_list = h->d_defer;
+    L.scratch = h->d_scratch;
+    return push_sys(h);
+}
+
+// Read and clear nothing: map the sticky device error word to a status.
+int read_errors(aap_handle *h)
+{
+    int err = 0;
+    AAP_CK(cudaMemcpyAsync(&err, h->hs.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    if (err & aapk::ERR_SPILL) h->flags |= AAP_FLAG_SPILLED;
+    if (err & (aapk::ERR_LOST | aapk::ERR_STAGE)) {
+        h->broken = true;
+        return fail(AAP_EOVERFLOW, "particles were lost: a tile overflowed its spill capacity "
+                                   "(increase aap_params.capacity)");
+    }
+    if (err & aapk::ERR_BOUNDS) {
+        h->broken = true;
+        return fail(AAP_ESTATE, "a particle record decoded outside its tile (internal fault)");
+    }
+    if (err & aapk::ERR_NAN) return fail(AAP_ENAN, "a non-finite orientation was produced");
+    return AAP_OK;
+}
+
+// Fold the durations of recorded timing events into h->ms.
+int resolve_timing(aap_handle *h)
+{
+    if (h->ev_used == 0) return AAP_OK;
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i + 3 < h->ev_used; i += 4) {
+        for (int k = 0; k < 3; ++k) {
+            float t = 0.f;
+            AAP_CK(cudaEventElapsedTime(&t, h->events[i + k], h->events[i + k + 1]));
+            h->ms[k] += t;
+            h->launches[k] += 1;
+        }
+    }
+    h->ev_used = 0;
+    return AAP_OK;
+}
+
+int run_steps(aap_handle *h, long long nsteps)
+{
+    for (long long i = 0; i < nsteps; ++i) {
+        cudaEvent_t *ev = nullptr;
+        if (h->timing) {
+            if (h->ev_used + 4 > 4096) {
+                int rc = resolve_timing(h);
+                if (rc) return rc;
+            }
+            while (h->events.size() < h->ev_used + 4) {
+                cudaEvent_t e;
+                AAP_CK(cudaEventCreate(&e));
+                h->events.push_back(e);
+            }
+            ev = &h->events[h->ev_used];
+            h->ev_used += 4;
+        }
+        AAP_CK(aapk::launch_step(h->L, h->stream, ev));
+    }
+    h->step += nsteps;
+    return AAP_OK;
+}
+
+int ensure_xfer(aap_handle *h)
+{
+    int rc;
+    if (!h->d_x) {
+        const size_t n = (size_t)std::max<long long>(h->p.n, 1);
+        if ((rc = dev_alloc(h, &h->d_x, n * sizeof(double)))) return rc;
+        if ((rc = dev_alloc(h, &h->d_y, n * sizeof(double)))) return rc;
+        if ((rc = dev_alloc(h, &h->d_th, n * sizeof(float)))) return rc;
+    }
+    return AAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *aap_last_error(void) { return g_err.c_str(); }
+
+int32_t aap_abi_version(void) { return 1; }
+
+void aap_params_default(aap_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->n = 1000;
+    p->lx = p->ly = 32.0;
+    p->r = 1.0;
+    p->v = 0.5;
+    p->eta = 0.4;
+    p->omega = 0.0;
+    p->gamma = 1.0;
+    p->dt = 0.01;
+    p->seed = 1;
+    p->model = AAP_VM;
+    p->order = 1;
+    p->weight = AAP_H_INV_1PN;
+}
+
+int aap_create(const aap_params *p, void *stream, aap_handle **out)
+{
+    g_err.clear();
+    if (!out) return fail(AAP_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(p);
+    if (rc) return rc;
+    aap_handle *h = new aap_handle();
+    h->p = *p;
+    h->stream = static_cast<cudaStream_t>(stream);
+    if ((rc = build_layout(h)) || (rc = alloc_all(h))) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    cudaError_t e = aapk::launch_insert(h->hs, 0, nullptr, nullptr, nullptr, 1, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        free_all(h);
+        delete h;
+        return fail(AAP_ECUDA, std::string("initial state: ") + cudaGetErrorString(e));
+    }
+    if ((rc = read_errors(h))) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return AAP_OK;
+}
+
+int aap_destroy(aap_handle *h)
+{
+    if (!h) return AAP_OK;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return AAP_OK;
+}
+
+int aap_step(aap_handle *h, int64_t nsteps)
+{
+    if (!h) return fail(AAP_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
+    if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
+    return run_steps(h, nsteps);
+}
+
+int aap_sync(aap_handle *h)
+{
+    if (!h) return fail(AAP_EINVAL, "handle is NULL");
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    return read_errors(h);
+}
+
+int aap_observe(aap_handle *h, aap_obs *out)
+{
+    if (!h || !out) return fail(AAP_EINVAL, "NULL argument");
+    if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
+    const Sys &S = h->hs;
+    AAP_CK(cudaMemsetAsync(h->d_obs, 0, 8 * sizeof(unsigned long long), h->stream));
+    AAP_CK(aapk::launch_observe(S, (int)(h->step & 1), h->d_obs, h->stream));
+    unsigned long long o[8];
+    double last[4];
+    AAP_CK(cudaMemcpyAsync(o, h->d_obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaMemcpyAsync(last, S.last, sizeof(last), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    int rc = read_errors(h);
+    if (rc) return rc;
+    if ((long long)o[4] != h->p.n) {
+        h->broken = true;
+        return fail(AAP_EOVERFLOW, "particle count changed: " + std::to_string((long long)o[4]) +
+                                       " stored of " + std::to_string(h->p.n));
+    }
+    const double n = (double)h->p.n;
+    const double c1 = (double)(long long)o[0] / aapk::kFix, s1 = (double)(long long)o[1] / aapk::kFix;
+    const double c2 = (double)(long long)o[2] / aapk::kFix, s2 = (double)(long long)o[3] / aapk::kFix;
+    out->phi = n > 0 ? std::sqrt(c1 * c1 + s1 * s1) / n : 0.0;
+    out->q = n > 0 ? std::sqrt(c2 * c2 + s2 * s2) / n : 0.0;
+    out->mean_neighbours = h->step > 0 ? last[1] : NAN;
+    out->step = h->step;
+    out->flags = h->flags;
+    out->reserved = 0;
+    return AAP_OK;
+}
+
+int aap_phi_trace(aap_handle *h, int64_t nsteps, double *phi_out)
+{
+    if (!h || !phi_out) return fail(AAP_EINVAL, "NULL argument");
+    if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
+    aap_obs ob;
+    int rc = aap_observe(h, &ob);
+    if (rc) return rc;
+    phi_out[0] = ob.phi;
+    if (nsteps == 0) return AAP_OK;
+    if (h->trace_alloc < nsteps + 1) {
+        if ((rc = dev_alloc(h, &h->d_trace, (size_t)(nsteps + 1) * sizeof(double)))) return rc;
+        if ((rc = dev_alloc(h, &h->d_trace_nbar, (size_t)(nsteps + 1) * sizeof(double)))) return rc;
+        h->trace_alloc = nsteps + 1;
+    }
+    h->hs.trace = h->d_trace;
+    h->hs.trace_nbar = h->d_trace_nbar;
+    h->hs.trace_base = h->step;
+    h->hs.trace_cap = nsteps + 1;
+    if ((rc = push_sys(h))) return rc;
+    if ((rc = run_steps(h, nsteps))) return rc;
+    AAP_CK(cudaMemcpyAsync(phi_out + 1, h->d_trace + 1, (size_t)nsteps * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+    h->hs.trace = nullptr;
+    h->hs.trace_nbar = nullptr;
+    h->hs.trace_cap = 0;
+    if ((rc = push_sys(h))) return rc;
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    return read_errors(h);
+}
+
+int aap_get_state(aap_handle *h, double *x, double *y, float *theta, int64_t n)
+{
+    if (!h || !x || !y || !theta) return fail(AAP_EINVAL, "NULL argument");
+    if (n != h->p.n) return fail(AAP_EINVAL, "n must equal the particle number");
+    if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
+    int rc = ensure_xfer(h);
+    if (rc) return rc;
+    if (n == 0) return AAP_OK;
+    AAP_CK(cudaMemsetAsync(h->d_seen, 0, sizeof(int), h->stream));
+    AAP_CK(aapk::launch_gather(h->hs, (int)(h->step & 1), h->d_x, h->d_y, h->d_th, h->d_seen, h->stream));
+    int seen = 0;
+    AAP_CK(cudaMemcpyAsync(x, h->d_x, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaMemcpyAsync(y, h->d_y, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaMemcpyAsync(theta, h->d_th, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaMemcpyAsync(&seen, h->d_seen, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    if ((rc = read_errors(h))) return rc;
+    if (seen != n) {
+        h->broken = true;
+        return fail(AAP_EOVERFLOW, "stored particle count " + std::to_string(seen) + " != N");
+    }
+    return AAP_OK;
+}
+
+int aap_set_state(aap_handle *h, const double *x, const double *y, const float *theta, int64_t n,
+                  int64_t step)
+{
+    if (!h || (n > 0 && (!x || !y || !theta))) return fail(AAP_EINVAL, "NULL argument");
+    if (n != h->p.n) return fail(AAP_EINVAL, "n must equal the particle number");
+    if (step < 0) return fail(AAP_EINVAL, "step < 0");
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(x[i] >= 0.0 && x[i] <= h->p.lx) || !(y[i] >= 0.0 && y[i] <= h->p.ly))
+            return fail(AAP_EINVAL, "position " + std::to_string(i) + " outside the box");
+        if (!std::isfinite(theta[i])) return fail(AAP_EINVAL, "non-finite orientation " + std::to_string(i));
+    }
+    int rc = ensure_xfer(h);
+    if (rc) return rc;
+    Sys &S = h->hs;
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    for (int b = 0; b < 2; ++b)
+        AAP_CK(cudaMemsetAsync(S.cnt[b], 0, (size_t)S.ntiles * aapk::kCntStride * sizeof(int), h->stream));
+    AAP_CK(cudaMemsetAsync(S.spill_cnt, 0, 2 * sizeof(int), h->stream));
+    AAP_CK(cudaMemsetAsync(S.acc, 0, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long), h->stream));
+    AAP_CK(cudaMemsetAsync(S.err, 0, sizeof(int), h->stream));
+    Ctl c{};
+    c.step = step;
+    AAP_CK(cudaMemcpyAsync(h->d_ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+    if (n > 0) {
+        AAP_CK(cudaMemcpyAsync(h->d_x, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        AAP_CK(cudaMemcpyAsync(h->d_y, y, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        AAP_CK(cudaMemcpyAsync(h->d_th, theta, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        AAP_CK(aapk::launch_insert(S, (int)(step & 1), h->d_x, h->d_y, h->d_th, 0, h->stream));
+    }
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    h->step = step;
+    h->flags = 0;
+    h->broken = false;
+    return read_errors(h);
+}
+
+int aap_step_neighbours(aap_handle *h, int32_t *nbr_out, int64_t n)
+{
+    if (!h || (n > 0 && !nbr_out)) return fail(AAP_EINVAL, "NULL argument");
+    if (n != h->p.n) return fail(AAP_EINVAL, "n must equal the particle number");
+    if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
+    int rc;
+    if (!h->d_nbr && (rc = dev_alloc(h, &h->d_nbr, (size_t)std::max<long long>(n, 1) * sizeof(int))))
+        return rc;
+    h->hs.nbr_out = h->d_nbr;
+    if ((rc = push_sys(h))) return rc;
+    rc = run_steps(h, 1);
+    h->hs.nbr_out = nullptr;
+    int rc2 = push_sys(h);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (n > 0)
+        AAP_CK(cudaMemcpyAsync(nbr_out, h->d_nbr, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    return read_errors(h);
+}
+
+int aap_set_timing(aap_handle *h, int32_t enable)
+{
+    if (!h) return fail(AAP_EINVAL, "handle is NULL");
+    int rc = resolve_timing(h);
+    if (rc) return rc;
+    h->timing = enable != 0;
+    for (int k = 0; k < 3; ++k) {
+        h->ms[k] = 0;
+        h->launches[k] = 0;
+    }
+    return AAP_OK;
+}
+
+int aap_get_timing(aap_handle *h, double *ms, int64_t *launches)
+{
+    if (!h || !ms || !launches) return fail(AAP_EINVAL, "NULL argument");
+    int rc = resolve_timing(h);
+    if (rc) return rc;
+    for (int k = 0; k < 3; ++k) {
+        ms[k] = h->ms[k];
+        launches[k] = h->launches[k];
+    }
+    return AAP_OK;
+}
+
+int aap_get_layout(aap_handle *h, aap_layout *out)
+{
+    if (!h || !out) return fail(AAP_EINVAL, "NULL argument");
+    const Sys &S = h->hs;
+    out->ncx = S.ncx;
+    out->ncy = S.ncy;
+    out->ntx = S.ntx;
+    out->nty = S.nty;
+    out->tile_w = S.twmax;
+    out->tile_h = S.thmax;
+    out->fix_bits_x = S.sx;
+    out->fix_bits_y = S.sy;
+    out->threads = h->L.threads;
+    out->stage_cap = S.stage_cap;
+    out->tile_slots = S.tile_slots;
+    out->device_bytes = (int64_t)h->bytes;
+    out->cell_x = h->csx;
+    out->cell_y = h->csy;
+    return AAP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// aap_internal.cuh -- device-side data layout of the GB300 particle library.
+//
+// State layout in HBM (one system):
+//   The Lx x Ly box is cut into ncx x ncy cells of side L/floor(L/R)
+//   (Sec. 3.2 of the paper), and the cells into ntx x nty tiles (balanced
+//   partition, every tile >= 3 cells per axis).  Each tile owns a fixed block
+//   of `tile_slots` particle records split into 9 regions by cell class:
+//   interior, four edges, four corners (region = ry*3 + rx with
+//   rx = 0 for the first column, 2 for the last, 1 otherwise).  A block that
+//   updates one tile can therefore read exactly its one-cell halo: the facing
+//   edge and corner regions of the 8 neighbour tiles.
+//   A record is 16 bytes {X, Y, theta, id}: X, Y are fixed-point positions
+//   relative to the tile's lower-left corner with 2^s units per cell side, so
+//   the cell of a particle is X >> s and every wrap or mirror is exact integer
+//   arithmetic.  Regions are filled through warp-aggregated atomic counters;
+//   records inside a region are unordered (the step kernel sorts them by
+//   (cell, id) in shared memory, which makes every sum deterministic).
+//   Particles that do not fit their region go to a spill list.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace aapk {
+
+constexpr int kRegions = 9;
+constexpr int kCntStride = 16;      // counters per tile (9 used): one 64-byte line
+constexpr int kAccSlots = 64;       // spread of the per-step integer accumulators
+constexpr int kAccWords = 4;        // sum cos, sum sin, sum |Omega|, unused
+constexpr int kSegs = 25;           // 9 own regions + 16 halo regions
+constexpr int kMaxTile = 64;        // largest tile side in cells
+constexpr double kFix = 4294967296.0;  // 2^32: scale of the orientation sums
+
+// error bits (Sys::err)
+enum : int {
+    ERR_SPILL = 1,    // a region overflowed into the spill list (still exact)
+    ERR_LOST = 2,     // the spill list overflowed: particles were dropped
+    ERR_BOUNDS = 4,   // a record decoded outside its tile (internal fault)
+    ERR_NAN = 8,      // a non-finite orientation was produced
+    ERR_STAGE = 16,   // a deferred tile exceeded the scratch capacity
+};
+
+struct Sys {
+    // geometry
+    int ncx, ncy, ntx, nty;
+    int sx, sy;                 // fixed-point bits per cell side
+    int twmax, thmax;           // largest tile in cells
+    double lx, ly, csx_d, csy_d;
+    float ux, uy;               // length of one fixed-point unit, cs * 2^-s
+    float kx, ky;               // displacement per step in units, times cos / sin
+    float r2;                   // R^2
+    // model (Sec. 2)
+    int model, order, weight, bx, by;
+    float eta_pi;               // VM / NVM: eta * pi (noise amplitude)
+    float omega_step;           // omega (VM / NVM) or omega * dt (Langevin)
+    float gamma_dt;             // Gamma * dt (Langevin)
+    float noise_amp;            // eta * sqrt(dt) (Langevin)
+    uint32_t seed_lo, seed_hi;
+    long long n;
+    // layout
+    int ntiles;
+    int tile_slots;
+    int cap[kRegions];
+    int off[kRegions];
+    int spill_cap;
+    int stage_cap;              // particles staged in shared memory (fast path)
+    int scratch_cap;            // particles staged in global scratch (deferred path)
+    int4 *rec[2];
+    int *cnt[2];                // [ntiles * kCntStride]
+    int4 *spill_rec[2];
+    int *spill_key[2];          // tile * kCntStride + region
+    int *spill_cnt;             // [2]
+    unsigned long long *acc;    // [2][kAccSlots][kAccWords]
+    // measurement outputs
+    double *trace;              // p(t) for t = trace_base .. trace_base + trace_cap - 1
+    double *trace_nbar;         // mean |Omega| of state t
+    long long trace_base, trace_cap;
+    double *last;               // [4]: p, mean |Omega| of the last measured state, step, unused
+    int *nbr_out;               // optional |Omega_i| by particle id
+    int *err;
+};
+
+struct Ctl {
+    long long step;             // steps taken; parity selects the current buffer
+    int tile_next;              // dynamic tile fetch of the step kernel
+    int defer_next;             // dynamic fetch of the deferred kernel
+    int defer_count;            // tiles deferred to the scratch path this step
+    int finish_ticket;
+    int pad[2];
+};
+
+// Segment: one region of one (possibly the same) tile mapped into the
+// extended (tile + one-cell ring) frame of the tile being updated.
+struct Seg {
+    const int4 *base;
+    long long bx, by;           // position map X_ext = ax * X + bx
+    int count;
+    int ax, ay;                 // +1 or -1 (mirror)
+    int cx, cy;                 // cell map: ext = a * l + c (before the +1 ring offset)
+    int flip;                   // bit0: mirrored in x, bit1: mirrored in y
+    int tile, region;
+};
+
+// Per-particle staging arrays (shared memory on the fast path, global
+// scratch on the deferred path) and per-cell tables (always shared).
+struct Stage {
+    int *rX, *rY;               // extended-frame fixed-point positions
+    float *rth;                 // orientation
+    unsigned *id;
+    unsigned short *cell;       // extended cell | flip << 14
+    unsigned short *slot;       // rank of arrival in the cell
+    unsigned short *gidx;       // grouped-by-cell order -> staged index
+    unsigned short *sk;         // sorted order -> staged index
+    float *px, *py, *pc, *ps;   // sorted: position rel. tile centre, cos, sin
+    int *spill_e;               // matched spill entries
+    unsigned char *spill_s;     // their segment
+    int spill_list_cap;
+    int cap;                    // particles
+};
+
+__host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Bytes of the per-particle staging arrays for `cap` particles.
+__host__ __device__ inline size_t stage_particle_bytes(int cap)
+{
+    return (size_t)cap * (4 * 4 + 4 * 4 + 4 * 2);
+}
+
+__host__ __device__ inline void carve_particles(Stage &st, unsigned char *p, int cap)
+{
+    st.cap = cap;
+    st.rX = (int *)p;                 p += (size_t)cap * 4;
+    st.rY = (int *)p;                 p += (size_t)cap * 4;
+    st.rth = (float *)p;              p += (size_t)cap * 4;
+    st.id = (unsigned *)p;            p += (size_t)cap * 4;
+    st.px = (float *)p;               p += (size_t)cap * 4;
+    st.py = (float *)p;               p += (size_t)cap * 4;
+    st.pc = (float *)p;               p += (size_t)cap * 4;
+    st.ps = (float *)p;               p += (size_t)cap * 4;
+    st.cell = (unsigned short *)p;    p += (size_t)cap * 2;
+    st.slot = (unsigned short *)p;    p += (size_t)cap * 2;
+    st.gidx = (unsigned short *)p;    p += (size_t)cap * 2;
+    st.sk = (unsigned short *)p;
+}
+
+// Per-tile tables held in shared memory.
+struct Tables {
+    int *hist;                  // [nce]
+    int *cstart;                // [nce + 1]
+    int *rowpre;                // [kMaxTile + 1]
+};
+
+__host__ __device__ inline size_t table_bytes(int nce)
+{
+    return (size_t)round_up(nce, 4) * 4 + (size_t)round_up(nce + 1, 4) * 4 + (kMaxTile + 4) * 4;
+}
+
+__host__ __device__ inline void carve_tables(Tables &t, unsigned char *p, int nce)
+{
+    t.hist = (int *)p;   p += (size_t)round_up(nce, 4) * 4;
+    t.cstart = (int *)p; p += (size_t)round_up(nce + 1, 4) * 4;
+    t.rowpre = (int *)p;
+}
+
+// Spill-match list kept in shared memory on the fast path.
+constexpr int kSpillListFast = 256;
+__host__ __device__ inline size_t spill_list_bytes(int cap) { return (size_t)cap * 5 + 16; }
+
+}  // namespace aapk

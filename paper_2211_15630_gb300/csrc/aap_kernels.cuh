@@ -1,0 +1,42 @@
+// aap_kernels.cuh -- host-callable launchers of the step kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "aap_internal.cuh"
+
+namespace aapk {
+
+// Everything one step launch needs; the step index and buffer parity are read
+// on the device from Ctl, so a captured CUDA graph of steps can be replayed.
+struct LaunchCfg {
+    Sys *sys;                    // device array [nsys]
+    int nsys;
+    const int *tile_base;        // device [nsys + 1]: prefix of tiles per system
+    Ctl *ctl;
+    int *defer_list;             // device [total tiles]
+    unsigned char *scratch;      // device [grid_defer * scratch_per_block]
+    size_t scratch_per_block;
+    int scratch_cap;             // particles per deferred block
+    int threads;                 // 128, 256 or 512
+    int stage_cap;               // particles staged in shared memory
+    int nce_max;                 // cells of the largest tile plus its ring
+    int grid_step, grid_defer, grid_finish;
+};
+
+size_t step_smem_bytes(int stage_cap, int nce_max);
+cudaError_t configure_step_kernels(int threads, size_t smem_bytes);
+cudaError_t step_blocks_per_sm(int threads, size_t smem_bytes, int *out);
+
+// One full step: k_step, k_deferred (no-op unless a tile overflowed shared
+// memory), k_finish.  With ev != nullptr, ev[0..3] are recorded before
+// k_step and after each of the three kernels.
+cudaError_t launch_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev = nullptr);
+
+cudaError_t launch_insert(const Sys &S, int b, const double *x, const double *y, const float *th,
+                          int mode, cudaStream_t st);
+cudaError_t launch_gather(const Sys &S, int b, double *x, double *y, float *th, int *seen,
+                          cudaStream_t st);
+cudaError_t launch_observe(const Sys &S, int b, unsigned long long *out, cudaStream_t st);
+
+}  // namespace aapk
