@@ -79,6 +79,12 @@ struct aap_handle {
     size_t ev_used = 0;
     double ms[3] = {0, 0, 0};
     long long launches[3] = {0, 0, 0};
+    // capacity management
+    double factor = 4.0;            // region slots over the mean occupancy
+    int *pinned_err = nullptr;      // error word copied after each aap_step
+    cudaEvent_t err_event = nullptr;
+    bool err_pending = false;
+    int relayouts = 0;
 };
 
 namespace {
@@ -105,6 +111,10 @@ void free_all(aap_handle *h)
     h->gexec = nullptr;
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     h->events.clear();
+    if (h->err_event) cudaEventDestroy(h->err_event);
+    h->err_event = nullptr;
+    if (h->pinned_err) cudaFreeHost(h->pinned_err);
+    h->pinned_err = nullptr;
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();
 }
@@ -176,6 +186,48 @@ void layout_regions(Sys &S, double mu, double factor)
     S.tile_slots = aapk::round_up(off, 4);
 }
 
+// Region capacities, spill list, staging capacities and launch shapes for a
+// capacity factor (slots per region over the mean occupancy).
+int set_capacity(aap_handle *h, double factor)
+{
+    const aap_params &p = h->p;
+    Sys &S = h->hs;
+    const int nsm = sm_count();
+    const double mu = (double)p.n / ((double)S.ncx * S.ncy);
+    layout_regions(S, mu, factor);
+    // every particle beyond its region's slots goes to the spill list; it is
+    // sized for an eighth of the particles so that a step never loses one
+    S.spill_cap = (int)std::max<long long>(4096, p.n / 8);
+    // shared-memory staging capacity: about twice the mean tile + ring load
+    const int nce = (S.twmax + 2) * (S.thmax + 2);
+    const double mean_stage = mu * nce;
+    int scap = aapk::round_up((int)std::ceil(1.75 * mean_stage + 128.0), 64);
+    scap = std::min(scap, 4096);
+    S.stage_cap = scap;
+    const int own = S.tile_slots;
+    const int halo = 2 * (2 * S.cap[0] + S.cap[1]) + 2 * (2 * S.cap[0] + S.cap[3]) + 4 * S.cap[0];
+    if ((long long)own + halo > 65535)
+        return fail(AAP_EINVAL, "tile capacity too large (reduce tile size or capacity)");
+    S.scratch_cap = (int)std::min<long long>(65535, (long long)own + halo + 4ll * S.spill_cap);
+    LaunchCfg &L = h->L;
+    L.threads = p.threads ? p.threads : 256;
+    L.stage_cap = scap;
+    L.nce_max = nce;
+    const size_t smem = aapk::step_smem_bytes(scap, nce);
+    AAP_CK(aapk::configure_step_kernels(L.threads, smem));
+    int bps = 0;
+    AAP_CK(aapk::step_blocks_per_sm(L.threads, smem, &bps));
+    if (bps < 1) return fail(AAP_EINVAL, "step kernel does not fit on an SM with this tiling");
+    L.grid_step = std::max(1, std::min(S.ntiles, bps * nsm));
+    L.grid_defer = std::max(1, std::min(S.ntiles, 32));
+    L.grid_finish = std::max(1, std::min(256, ceil_div((long long)S.ntiles * aapk::kCntStride, 256)));
+    L.scratch_cap = S.scratch_cap;
+    L.scratch_per_block = aapk::stage_particle_bytes(S.scratch_cap) + aapk::spill_list_bytes(S.scratch_cap);
+    L.scratch_per_block = (L.scratch_per_block + 255) / 256 * 256;
+    L.nsys = 1;
+    return AAP_OK;
+}
+
 int build_layout(aap_handle *h)
 {
     const aap_params &p = h->p;
@@ -226,41 +278,8 @@ int build_layout(aap_handle *h)
     S.seed_lo = (uint32_t)p.seed;
     S.seed_hi = (uint32_t)(p.seed >> 32);
     S.n = p.n;
-    const double mu = (double)p.n / ((double)S.ncx * S.ncy);
-    const double factor = p.capacity > 0 ? p.capacity : 4.0;
-    layout_regions(S, mu, factor);
-    S.spill_cap = (int)std::min<long long>(4096, p.n / 16 + 256);
-    // shared-memory staging capacity: about twice the mean tile + ring load
-    const int nce = (S.twmax + 2) * (S.thmax + 2);
-    const double mean_stage = mu * nce;
-    int scap = aapk::round_up((int)std::ceil(1.75 * mean_stage + 128.0), 64);
-    scap = std::min(scap, 4096);
-    S.stage_cap = scap;
-    int own = S.tile_slots;
-    int halo = 2 * (2 * S.cap[0] + S.cap[1]) + 2 * (2 * S.cap[0] + S.cap[3]) + 4 * S.cap[0];
-    long long scr = (long long)own + halo + 4ll * S.spill_cap;
-    if (scr > 65535) scr = 65535;
-    if ((long long)own + halo > 65535)
-        return fail(AAP_EINVAL, "tile capacity too large (reduce tile size or capacity)");
-    S.scratch_cap = (int)scr;
-    int threads = p.threads ? p.threads : 256;
-    LaunchCfg &L = h->L;
-    L.threads = threads;
-    L.stage_cap = scap;
-    L.nce_max = nce;
-    const size_t smem = aapk::step_smem_bytes(scap, nce);
-    AAP_CK(aapk::configure_step_kernels(threads, smem));
-    int bps = 0;
-    AAP_CK(aapk::step_blocks_per_sm(threads, smem, &bps));
-    if (bps < 1) return fail(AAP_EINVAL, "step kernel does not fit on an SM with this tiling");
-    L.grid_step = std::max(1, std::min(S.ntiles, bps * nsm));
-    L.grid_defer = std::max(1, std::min(S.ntiles, nsm));
-    L.grid_finish = std::max(1, std::min(256, ceil_div((long long)S.ntiles * aapk::kCntStride, 256)));
-    L.scratch_cap = S.scratch_cap;
-    L.scratch_per_block = aapk::stage_particle_bytes(S.scratch_cap) + aapk::spill_list_bytes(S.scratch_cap);
-    L.scratch_per_block = (L.scratch_per_block + 255) / 256 * 256;
-    L.nsys = 1;
-    return AAP_OK;
+    h->factor = p.capacity > 0 ? p.capacity : 4.0;
+    return set_capacity(h, h->factor);
 }
 
 int push_sys(aap_handle *h)
@@ -269,17 +288,72 @@ int push_sys(aap_handle *h)
     return AAP_OK;
 }
 
+int dev_free(aap_handle *h, void *p, size_t bytes)
+{
+    if (!p) return AAP_OK;
+    for (size_t i = 0; i < h->allocs.size(); ++i)
+        if (h->allocs[i] == p) {
+            h->allocs.erase(h->allocs.begin() + (long)i);
+            break;
+        }
+    h->bytes -= std::min(h->bytes, bytes);
+    AAP_CK(cudaFree(p));
+    return AAP_OK;
+}
+
+size_t region_bytes(const Sys &S) { return (size_t)S.ntiles * S.tile_slots * sizeof(int4); }
+
+// Buffers whose size depends on the capacity factor.
+int alloc_regions(aap_handle *h)
+{
+    Sys &S = h->hs;
+    int rc;
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = dev_alloc(h, &S.rec[b], region_bytes(S)))) return rc;
+        if ((rc = dev_alloc(h, &S.spill_rec[b], (size_t)S.spill_cap * sizeof(int4)))) return rc;
+        if ((rc = dev_alloc(h, &S.spill_key[b], (size_t)S.spill_cap * sizeof(int)))) return rc;
+    }
+    if ((rc = dev_alloc(h, &h->d_scratch, h->L.scratch_per_block * h->L.grid_defer))) return rc;
+    h->L.scratch = h->d_scratch;
+    return AAP_OK;
+}
+
+int free_regions(aap_handle *h)
+{
+    Sys &S = h->hs;
+    int rc;
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = dev_free(h, S.rec[b], region_bytes(S)))) return rc;
+        if ((rc = dev_free(h, S.spill_rec[b], (size_t)S.spill_cap * sizeof(int4)))) return rc;
+        if ((rc = dev_free(h, S.spill_key[b], (size_t)S.spill_cap * sizeof(int)))) return rc;
+        S.rec[b] = nullptr;
+        S.spill_rec[b] = nullptr;
+        S.spill_key[b] = nullptr;
+    }
+    rc = dev_free(h, h->d_scratch, h->L.scratch_per_block * h->L.grid_defer);
+    h->d_scratch = nullptr;
+    return rc;
+}
+
+// Clear both buffers' counters, the spill counts, the step sums and errors.
+int clear_buffers(aap_handle *h)
+{
+    Sys &S = h->hs;
+    for (int b = 0; b < 2; ++b)
+        AAP_CK(cudaMemsetAsync(S.cnt[b], 0, (size_t)S.ntiles * aapk::kCntStride * sizeof(int), h->stream));
+    AAP_CK(cudaMemsetAsync(S.spill_cnt, 0, 2 * sizeof(int), h->stream));
+    AAP_CK(cudaMemsetAsync(S.acc, 0, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long), h->stream));
+    AAP_CK(cudaMemsetAsync(S.err, 0, sizeof(int), h->stream));
+    return AAP_OK;
+}
+
 int alloc_all(aap_handle *h)
 {
     Sys &S = h->hs;
     int rc;
-    const size_t slots = (size_t)S.ntiles * S.tile_slots;
-    for (int b = 0; b < 2; ++b) {
-        if ((rc = dev_alloc(h, &S.rec[b], slots * sizeof(int4)))) return rc;
+    for (int b = 0; b < 2; ++b)
         if ((rc = dev_alloc(h, &S.cnt[b], (size_t)S.ntiles * aapk::kCntStride * sizeof(int)))) return rc;
-        if ((rc = dev_alloc(h, &S.spill_rec[b], (size_t)S.spill_cap * sizeof(int4)))) return rc;
-        if ((rc = dev_alloc(h, &S.spill_key[b], (size_t)S.spill_cap * sizeof(int)))) return rc;
-    }
+    if ((rc = alloc_regions(h))) return rc;
     if ((rc = dev_alloc(h, &S.spill_cnt, 2 * sizeof(int)))) return rc;
     if ((rc = dev_alloc(h, &S.acc, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long)))) return rc;
     if ((rc = dev_alloc(h, &S.last, 4 * sizeof(double)))) return rc;
@@ -288,16 +362,12 @@ int alloc_all(aap_handle *h)
     if ((rc = dev_alloc(h, &h->d_tile_base, 2 * sizeof(int)))) return rc;
     if ((rc = dev_alloc(h, &h->d_ctl, sizeof(Ctl)))) return rc;
     if ((rc = dev_alloc(h, &h->d_defer, (size_t)S.ntiles * sizeof(int)))) return rc;
-    if ((rc = dev_alloc(h, &h->d_scratch, h->L.scratch_per_block * h->L.grid_defer))) return rc;
     if ((rc = dev_alloc(h, &h->d_obs, 8 * sizeof(unsigned long long)))) return rc;
     if ((rc = dev_alloc(h, &h->d_seen, sizeof(int)))) return rc;
-    for (int b = 0; b < 2; ++b) {
-        AAP_CK(cudaMemsetAsync(S.cnt[b], 0, (size_t)S.ntiles * aapk::kCntStride * sizeof(int), h->stream));
-    }
-    AAP_CK(cudaMemsetAsync(S.spill_cnt, 0, 2 * sizeof(int), h->stream));
-    AAP_CK(cudaMemsetAsync(S.acc, 0, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long), h->stream));
+    AAP_CK(cudaMallocHost(&h->pinned_err, sizeof(int)));
+    AAP_CK(cudaEventCreateWithFlags(&h->err_event, cudaEventDisableTiming));
+    if ((rc = clear_buffers(h))) return rc;
     AAP_CK(cudaMemsetAsync(S.last, 0, 4 * sizeof(double), h->stream));
-    AAP_CK(cudaMemsetAsync(S.err, 0, sizeof(int), h->stream));
     AAP_CK(cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), h->stream));
     int tb[2] = {0, S.ntiles};
     AAP_CK(cudaMemcpyAsync(h->d_tile_base, tb, sizeof(tb), cudaMemcpyHostToDevice, h->stream));
@@ -307,7 +377,6 @@ int alloc_all(aap_handle *h)
     L.tile_base = h->d_tile_base;
     L.ctl = h->d_ctl;
     L.defer_list = h->d_defer;
-    L.scratch = h->d_scratch;
     return push_sys(h);
 }
 
@@ -383,6 +452,74 @@ int ensure_xfer(aap_handle *h)
     return AAP_OK;
 }
 
+// Put the particles back into freshly sized regions.  mode 0: from the flat
+// device arrays d_x, d_y, d_th; mode 1: the Philox initial state.  With an
+// automatic capacity the factor doubles until nothing spills; with an explicit
+// one spilled particles are kept (exactly) in the spill list.
+int reinsert(aap_handle *h, double factor, int mode)
+{
+    int rc;
+    for (int attempt = 0; attempt < 12; ++attempt) {
+        if ((rc = free_regions(h))) return rc;
+        if ((rc = set_capacity(h, factor))) return rc;
+        if ((rc = alloc_regions(h))) return rc;
+        if ((rc = clear_buffers(h))) return rc;
+        if ((rc = push_sys(h))) return rc;
+        AAP_CK(aapk::launch_insert(h->hs, (int)(h->step & 1), h->d_x, h->d_y, h->d_th, mode, h->stream));
+        int err = 0;
+        AAP_CK(cudaMemcpyAsync(&err, h->hs.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        AAP_CK(cudaStreamSynchronize(h->stream));
+        const bool spilled = err & (aapk::ERR_SPILL | aapk::ERR_LOST);
+        if (!spilled || (h->p.capacity > 0 && !(err & aapk::ERR_LOST))) {
+            h->factor = factor;
+            return AAP_OK;
+        }
+        if (h->p.capacity > 0) return fail(AAP_EOVERFLOW, "the particles do not fit the explicit capacity");
+        factor *= 2.0;
+    }
+    return fail(AAP_EOVERFLOW, "could not size the tile regions for this state");
+}
+
+// Gather the current state and re-insert it with a larger capacity factor;
+// the state is unchanged bit for bit (same tiles and fixed-point grid).
+int relayout(aap_handle *h, double factor)
+{
+    int rc;
+    if ((rc = ensure_xfer(h))) return rc;
+    if (h->p.n > 0) {
+        AAP_CK(cudaMemsetAsync(h->d_seen, 0, sizeof(int), h->stream));
+        AAP_CK(aapk::launch_gather(h->hs, (int)(h->step & 1), h->d_x, h->d_y, h->d_th, h->d_seen, h->stream));
+        int seen = 0;
+        AAP_CK(cudaMemcpyAsync(&seen, h->d_seen, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        AAP_CK(cudaStreamSynchronize(h->stream));
+        if (seen != h->p.n) {
+            h->broken = true;
+            return fail(AAP_EOVERFLOW, "stored particle count " + std::to_string(seen) + " != N");
+        }
+    }
+    ++h->relayouts;
+    return reinsert(h, factor, 0);
+}
+
+// At the start of aap_step: look at the error word copied after the previous
+// batch (without waiting); grow the regions if particles spilled.
+int poll_capacity(aap_handle *h)
+{
+    if (!h->err_pending) return AAP_OK;
+    const cudaError_t q = cudaEventQuery(h->err_event);
+    if (q == cudaErrorNotReady) return AAP_OK;
+    if (q != cudaSuccess) return fail(AAP_ECUDA, std::string("error event: ") + cudaGetErrorString(q));
+    h->err_pending = false;
+    const int err = *h->pinned_err;
+    if (err & aapk::ERR_SPILL) h->flags |= AAP_FLAG_SPILLED;
+    if (err & (aapk::ERR_LOST | aapk::ERR_STAGE)) {
+        h->broken = true;
+        return fail(AAP_EOVERFLOW, "particles were lost: a tile overflowed its spill capacity");
+    }
+    if ((err & aapk::ERR_SPILL) && h->p.capacity == 0) return relayout(h, h->factor * 1.5);
+    return AAP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -424,14 +561,7 @@ int aap_create(const aap_params *p, void *stream, aap_handle **out)
         delete h;
         return rc;
     }
-    cudaError_t e = aapk::launch_insert(h->hs, 0, nullptr, nullptr, nullptr, 1, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) {
-        free_all(h);
-        delete h;
-        return fail(AAP_ECUDA, std::string("initial state: ") + cudaGetErrorString(e));
-    }
-    if ((rc = read_errors(h))) {
+    if ((rc = reinsert(h, h->factor, 1)) || (rc = read_errors(h))) {
         free_all(h);
         delete h;
         return rc;
@@ -454,7 +584,13 @@ int aap_step(aap_handle *h, int64_t nsteps)
     if (!h) return fail(AAP_EINVAL, "handle is NULL");
     if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
     if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
-    return run_steps(h, nsteps);
+    int rc = poll_capacity(h);
+    if (rc) return rc;
+    if ((rc = run_steps(h, nsteps))) return rc;
+    AAP_CK(cudaMemcpyAsync(h->pinned_err, h->hs.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaEventRecord(h->err_event, h->stream));
+    h->err_pending = true;
+    return AAP_OK;
 }
 
 int aap_sync(aap_handle *h)
@@ -562,13 +698,8 @@ int aap_set_state(aap_handle *h, const double *x, const double *y, const float *
     }
     int rc = ensure_xfer(h);
     if (rc) return rc;
-    Sys &S = h->hs;
     AAP_CK(cudaStreamSynchronize(h->stream));
-    for (int b = 0; b < 2; ++b)
-        AAP_CK(cudaMemsetAsync(S.cnt[b], 0, (size_t)S.ntiles * aapk::kCntStride * sizeof(int), h->stream));
-    AAP_CK(cudaMemsetAsync(S.spill_cnt, 0, 2 * sizeof(int), h->stream));
-    AAP_CK(cudaMemsetAsync(S.acc, 0, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long), h->stream));
-    AAP_CK(cudaMemsetAsync(S.err, 0, sizeof(int), h->stream));
+    h->err_pending = false;
     Ctl c{};
     c.step = step;
     AAP_CK(cudaMemcpyAsync(h->d_ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
@@ -576,12 +707,11 @@ int aap_set_state(aap_handle *h, const double *x, const double *y, const float *
         AAP_CK(cudaMemcpyAsync(h->d_x, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         AAP_CK(cudaMemcpyAsync(h->d_y, y, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         AAP_CK(cudaMemcpyAsync(h->d_th, theta, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
-        AAP_CK(aapk::launch_insert(S, (int)(step & 1), h->d_x, h->d_y, h->d_th, 0, h->stream));
     }
-    AAP_CK(cudaStreamSynchronize(h->stream));
     h->step = step;
     h->flags = 0;
     h->broken = false;
+    if ((rc = reinsert(h, h->p.capacity > 0 ? h->p.capacity : 4.0, 0))) return rc;
     return read_errors(h);
 }
 

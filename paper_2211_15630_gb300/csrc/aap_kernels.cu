@@ -472,7 +472,7 @@ __device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long 
             }
             if (fx) { thn = AAP_PI_F - thn; cn = -cn; }
             if (fy) { thn = -thn; sn = -sn; }
-            thn -= AAP_2PI_F * floorf((thn + AAP_PI_F) * (1.0f / AAP_2PI_F));
+            if (thn >= AAP_PI_F || thn < -AAP_PI_F) thn -= AAP_2PI_F * floorf((thn + AAP_PI_F) * (1.0f / AAP_2PI_F));
             if (model == 1) sincosf(thn, &sn, &cn);
             if (!isfinite(thn)) atomicOr(S.err, ERR_NAN);
             dtile = dty * S.ntx + dtx;
@@ -697,7 +697,7 @@ __global__ void k_insert(Sys S, int b, const double *x, const double *y, const f
         const int x0 = tile_x0(S, tx), y0 = tile_y0(S, ty);
         const int X = (int)(gx - ((long long)x0 << S.sx)), Y = (int)(gy - ((long long)y0 << S.sy));
         const int tw = tile_x0(S, tx + 1) - x0, th_ = tile_y0(S, ty + 1) - y0;
-        pt -= AAP_2PI_F * floorf((pt + AAP_PI_F) * (1.0f / AAP_2PI_F));
+        if (pt >= AAP_PI_F || pt < -AAP_PI_F) pt -= AAP_2PI_F * floorf((pt + AAP_PI_F) * (1.0f / AAP_2PI_F));
         dtile = ty * S.ntx + tx;
         region = region_of(X >> S.sx, Y >> S.sy, tw, th_);
         rec = make_int4(X, Y, __float_as_int(pt), (int)i);

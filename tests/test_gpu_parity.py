@@ -228,17 +228,22 @@ def test_reflecting_mirror_extension_on_gpu(lib):
 
 
 def test_full_size_sampled(lib, oracle):
-    """N = 2^24, L = 2896 (rho = 2), R = 1, v0 = 0.5: one step in the launch
-    configuration the benchmark times, sampled particles against the oracle."""
+    """N = 2^24, L = 2896 (rho = 2), R = 1, v0 = 0.5: steps in the launch
+    configuration the benchmark times, sampled particles against the oracle.
+    On the uniform initial state the mean neighbour number is
+    (N-1) pi R^2 / L^2, and the fused on-the-fly sum equals the mean of the
+    per-particle counts."""
     n, L = 1 << 24, 2896.0
     p = params(n=n, lx=L, ly=L, eta=0.45, v=0.5, seed=1)
     h = A.aap_create(p)
     try:
-        A.aap_step(h, 2)
+        nb0 = A.aap_step_neighbours(h, n)
+        o = A.aap_observe(h)
+        assert abs(o.mean_neighbours - nb0.mean()) < 1e-9
+        assert abs(nb0.mean() - (n - 1) * np.pi / L**2) < 0.01
+        A.aap_step(h, 1)
         idx = np.random.default_rng(0).choice(n, 3000, replace=False)
         compare_one_step(oracle, p, h, idx=idx)
-        o = A.aap_observe(h)
-        assert abs(o.mean_neighbours - (n - 1) * np.pi / L**2) < 0.02
     finally:
         A.aap_destroy(h)
 
