@@ -319,12 +319,11 @@ def main():
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_step",
                      "kernel_ms": kstep_ms, "peak_kind": peak_kind,
                      "alg_bytes_per_update": ALG_BYTES},
-        "step_kernels_ms": {"k_step": kstep_ms, "k_deferred": kms[1] / max(klaunch[1], 1),
-                            "k_finish": kms[2] / max(klaunch[2], 1)},
+        "step_kernels_ms": {"k_step": kstep_ms, "k_finish": kms[1] / max(klaunch[1], 1)},
         "e2e": {"value": e2e_val, "unit": UNIT, "steps": ke,
                 "h2d_bytes_per_step": state_bytes / ke,
                 "d2h_bytes_per_step": (state_bytes + 8 * (ke + 1)) / ke},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 2 * args.steps,
         "clocks": csum,
         "phi_end": float(phi[-1]),
         "mean_neighbours": obs.mean_neighbours,

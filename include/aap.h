@@ -90,7 +90,8 @@ typedef struct aap_params {
     int32_t  bx, by;     /* 0 periodic, nonzero reflecting (per axis)           */
     int32_t  tile_w;     /* cells per tile along x; 0 = automatic               */
     int32_t  tile_h;     /* cells per tile along y; 0 = automatic               */
-    int32_t  threads;    /* threads per block of the step kernel; 0 = automatic */
+    int32_t  threads;    /* threads per block of the step kernel: 0 (automatic),
+                            256 or 512                                          */
     double   capacity;   /* tile-region capacity over the mean occupancy;
                             0 = automatic (4)                                   */
 } aap_params;
@@ -190,13 +191,13 @@ int aap_get_layout(aap_handle *h, aap_layout *out);
 
 /* Per-kernel timing (tracing aid).  enable != 0: every step enqueued by
  * aap_step / aap_phi_trace / aap_step_neighbours records CUDA events on h's
- * stream around its three kernels (the tile step, the deferred-tile step and
- * the step finish); the accumulated times restart from zero at each call. */
+ * stream around its two kernels (the tile step and the step finish); the
+ * accumulated times restart from zero at each call. */
 int aap_set_timing(aap_handle *h, int32_t enable);
 
 /* Milliseconds and launch counts accumulated since aap_set_timing:
- * index 0 the tile step kernel, 1 the deferred-tile kernel, 2 the finish
- * kernel (ms[3], launches[3], caller-owned host arrays).  Synchronises. */
+ * index 0 the tile step kernel, 1 the finish kernel, 2 reserved (0)
+ * (ms[3], launches[3], caller-owned host arrays).  Synchronises. */
 int aap_get_timing(aap_handle *h, double *ms, int64_t *launches);
 
 #ifdef __cplusplus

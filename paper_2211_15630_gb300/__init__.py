@@ -176,7 +176,7 @@ def aap_set_timing(h, enable: bool) -> None:
 
 
 def aap_get_timing(h):
-    """(ms[3], launches[3]) of the tile step, deferred-tile and finish kernels."""
+    """(ms[3], launches[3]): the tile step kernel, the finish kernel, reserved."""
     ms = np.zeros(3, np.float64)
     cnt = np.zeros(3, np.int64)
     _check(load().aap_get_timing(h, _p(ms), _p(cnt)))

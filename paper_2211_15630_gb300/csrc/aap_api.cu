@@ -53,7 +53,7 @@ struct aap_handle {
     Sys *d_sys = nullptr;
     int *d_tile_base = nullptr;
     Ctl *d_ctl = nullptr;
-    int *d_defer = nullptr;
+    int *d_x0tab = nullptr, *d_y0tab = nullptr;
     unsigned char *d_scratch = nullptr;
     unsigned long long *d_obs = nullptr;
     int *d_seen = nullptr;
@@ -149,8 +149,8 @@ int check_params(const aap_params *p)
         return fail(AAP_EINVAL, "tile_w and tile_h must be 0 (automatic) or in [6, 64]");
     if ((p->tile_w && p->tile_w < 6) || (p->tile_h && p->tile_h < 6))
         return fail(AAP_EINVAL, "tile_w and tile_h must be 0 (automatic) or in [6, 64]");
-    if (p->threads != 0 && p->threads != 128 && p->threads != 256 && p->threads != 512)
-        return fail(AAP_EINVAL, "threads must be 0, 128, 256 or 512");
+    if (p->threads != 0 && p->threads != 256 && p->threads != 512)
+        return fail(AAP_EINVAL, "threads must be 0, 256 or 512");
     if (!finite(p->capacity) || p->capacity < 0 || (p->capacity > 0 && p->capacity < 1))
         return fail(AAP_EINVAL, "capacity must be 0 (automatic) or >= 1");
     return AAP_OK;
@@ -203,26 +203,24 @@ int set_capacity(aap_handle *h, double factor)
     const double mean_stage = mu * nce;
     int scap = aapk::round_up((int)std::ceil(1.75 * mean_stage + 128.0), 64);
     scap = std::min(scap, 4096);
-    S.stage_cap = scap;
     const int own = S.tile_slots;
     const int halo = 2 * (2 * S.cap[0] + S.cap[1]) + 2 * (2 * S.cap[0] + S.cap[3]) + 4 * S.cap[0];
-    if ((long long)own + halo > 65535)
-        return fail(AAP_EINVAL, "tile capacity too large (reduce tile size or capacity)");
-    S.scratch_cap = (int)std::min<long long>(65535, (long long)own + halo + 4ll * S.spill_cap);
     LaunchCfg &L = h->L;
+    L.spill_list_cap = (int)std::min<long long>(16384, 4ll * S.spill_cap);
+    if ((long long)own + halo + L.spill_list_cap > 65472)
+        return fail(AAP_EINVAL, "tile capacity too large (reduce tile size or capacity)");
+    L.scratch_cap = aapk::round_up(own + halo + L.spill_list_cap, 64);
     L.threads = p.threads ? p.threads : 256;
+    L.model = p.model;
     L.stage_cap = scap;
     L.nce_max = nce;
     const size_t smem = aapk::step_smem_bytes(scap, nce);
-    AAP_CK(aapk::configure_step_kernels(L.threads, smem));
     int bps = 0;
-    AAP_CK(aapk::step_blocks_per_sm(L.threads, smem, &bps));
+    AAP_CK(aapk::configure_step_kernel(L.model, L.threads, smem, &bps));
     if (bps < 1) return fail(AAP_EINVAL, "step kernel does not fit on an SM with this tiling");
     L.grid_step = std::max(1, std::min(S.ntiles, bps * nsm));
-    L.grid_defer = std::max(1, std::min(S.ntiles, 32));
     L.grid_finish = std::max(1, std::min(256, ceil_div((long long)S.ntiles * aapk::kCntStride, 256)));
-    L.scratch_cap = S.scratch_cap;
-    L.scratch_per_block = aapk::stage_particle_bytes(S.scratch_cap) + aapk::spill_list_bytes(S.scratch_cap);
+    L.scratch_per_block = aapk::stage_bytes(L.scratch_cap) + aapk::spill_list_bytes(L.spill_list_cap);
     L.scratch_per_block = (L.scratch_per_block + 255) / 256 * 256;
     L.nsys = 1;
     return AAP_OK;
@@ -313,7 +311,7 @@ int alloc_regions(aap_handle *h)
         if ((rc = dev_alloc(h, &S.spill_rec[b], (size_t)S.spill_cap * sizeof(int4)))) return rc;
         if ((rc = dev_alloc(h, &S.spill_key[b], (size_t)S.spill_cap * sizeof(int)))) return rc;
     }
-    if ((rc = dev_alloc(h, &h->d_scratch, h->L.scratch_per_block * h->L.grid_defer))) return rc;
+    if ((rc = dev_alloc(h, &h->d_scratch, h->L.scratch_per_block * h->L.grid_step))) return rc;
     h->L.scratch = h->d_scratch;
     return AAP_OK;
 }
@@ -330,7 +328,7 @@ int free_regions(aap_handle *h)
         S.spill_rec[b] = nullptr;
         S.spill_key[b] = nullptr;
     }
-    rc = dev_free(h, h->d_scratch, h->L.scratch_per_block * h->L.grid_defer);
+    rc = dev_free(h, h->d_scratch, h->L.scratch_per_block * h->L.grid_step);
     h->d_scratch = nullptr;
     return rc;
 }
@@ -361,7 +359,17 @@ int alloc_all(aap_handle *h)
     if ((rc = dev_alloc(h, &h->d_sys, sizeof(Sys)))) return rc;
     if ((rc = dev_alloc(h, &h->d_tile_base, 2 * sizeof(int)))) return rc;
     if ((rc = dev_alloc(h, &h->d_ctl, sizeof(Ctl)))) return rc;
-    if ((rc = dev_alloc(h, &h->d_defer, (size_t)S.ntiles * sizeof(int)))) return rc;
+    if ((rc = dev_alloc(h, &h->d_x0tab, (size_t)(S.ntx + 1) * sizeof(int)))) return rc;
+    if ((rc = dev_alloc(h, &h->d_y0tab, (size_t)(S.nty + 1) * sizeof(int)))) return rc;
+    {
+        std::vector<int> xt(S.ntx + 1), yt(S.nty + 1);
+        for (int t = 0; t <= S.ntx; ++t) xt[t] = (int)((long long)t * S.ncx / S.ntx);
+        for (int t = 0; t <= S.nty; ++t) yt[t] = (int)((long long)t * S.ncy / S.nty);
+        AAP_CK(cudaMemcpy(h->d_x0tab, xt.data(), xt.size() * sizeof(int), cudaMemcpyHostToDevice));
+        AAP_CK(cudaMemcpy(h->d_y0tab, yt.data(), yt.size() * sizeof(int), cudaMemcpyHostToDevice));
+        S.x0tab = h->d_x0tab;
+        S.y0tab = h->d_y0tab;
+    }
     if ((rc = dev_alloc(h, &h->d_obs, 8 * sizeof(unsigned long long)))) return rc;
     if ((rc = dev_alloc(h, &h->d_seen, sizeof(int)))) return rc;
     AAP_CK(cudaMallocHost(&h->pinned_err, sizeof(int)));
@@ -376,7 +384,6 @@ int alloc_all(aap_handle *h)
     L.sys = h->d_sys;
     L.tile_base = h->d_tile_base;
     L.ctl = h->d_ctl;
-    L.defer_list = h->d_defer;
     return push_sys(h);
 }
 
@@ -405,8 +412,8 @@ int resolve_timing(aap_handle *h)
 {
     if (h->ev_used == 0) return AAP_OK;
     AAP_CK(cudaStreamSynchronize(h->stream));
-    for (size_t i = 0; i + 3 < h->ev_used; i += 4) {
-        for (int k = 0; k < 3; ++k) {
+    for (size_t i = 0; i + 2 < h->ev_used; i += 3) {
+        for (int k = 0; k < 2; ++k) {
             float t = 0.f;
             AAP_CK(cudaEventElapsedTime(&t, h->events[i + k], h->events[i + k + 1]));
             h->ms[k] += t;
@@ -422,17 +429,17 @@ int run_steps(aap_handle *h, long long nsteps)
     for (long long i = 0; i < nsteps; ++i) {
         cudaEvent_t *ev = nullptr;
         if (h->timing) {
-            if (h->ev_used + 4 > 4096) {
+            if (h->ev_used + 3 > 3072) {
                 int rc = resolve_timing(h);
                 if (rc) return rc;
             }
-            while (h->events.size() < h->ev_used + 4) {
+            while (h->events.size() < h->ev_used + 3) {
                 cudaEvent_t e;
                 AAP_CK(cudaEventCreate(&e));
                 h->events.push_back(e);
             }
             ev = &h->events[h->ev_used];
-            h->ev_used += 4;
+            h->ev_used += 3;
         }
         AAP_CK(aapk::launch_step(h->L, h->stream, ev));
     }
@@ -521,6 +528,12 @@ int poll_capacity(aap_handle *h)
 }
 
 }  // namespace
+
+#ifdef AAP_PHASE_TIMING
+namespace aapk {
+cudaError_t read_phase_times(unsigned long long *out16);
+}
+#endif
 
 extern "C" {
 
@@ -774,12 +787,21 @@ int aap_get_layout(aap_handle *h, aap_layout *out)
     out->fix_bits_x = S.sx;
     out->fix_bits_y = S.sy;
     out->threads = h->L.threads;
-    out->stage_cap = S.stage_cap;
+    out->stage_cap = h->L.stage_cap;
     out->tile_slots = S.tile_slots;
     out->device_bytes = (int64_t)h->bytes;
     out->cell_x = h->csx;
     out->cell_y = h->csy;
     return AAP_OK;
 }
+
+#ifdef AAP_PHASE_TIMING
+// Instrumented builds only: cycles per step-kernel phase summed over blocks.
+int aap_debug_phase_times(unsigned long long *out16)
+{
+    AAP_CK(aapk::read_phase_times(out16));
+    return AAP_OK;
+}
+#endif
 
 }  // extern "C"

@@ -27,9 +27,11 @@ constexpr int kRegions = 9;
 constexpr int kCntStride = 16;      // counters per tile (9 used): one 64-byte line
 constexpr int kAccSlots = 64;       // spread of the per-step integer accumulators
 constexpr int kAccWords = 4;        // sum cos, sum sin, sum |Omega|, unused
+constexpr double kFix = 4294967296.0;     // 2^32: scale of the observation sums
+constexpr float kFixStepF = 1073741824.0f;  // 2^30: scale of the per-step sums
+constexpr double kFixStep = 1073741824.0;
 constexpr int kSegs = 25;           // 9 own regions + 16 halo regions
 constexpr int kMaxTile = 64;        // largest tile side in cells
-constexpr double kFix = 4294967296.0;  // 2^32: scale of the orientation sums
 
 // error bits (Sys::err)
 enum : int {
@@ -37,12 +39,13 @@ enum : int {
     ERR_LOST = 2,     // the spill list overflowed: particles were dropped
     ERR_BOUNDS = 4,   // a record decoded outside its tile (internal fault)
     ERR_NAN = 8,      // a non-finite orientation was produced
-    ERR_STAGE = 16,   // a deferred tile exceeded the scratch capacity
+    ERR_STAGE = 16,   // a tile exceeded the scratch staging capacity
 };
 
 struct Sys {
     // geometry
     int ncx, ncy, ntx, nty;
+    const int *x0tab, *y0tab;   // first cell of every tile column / row, [ntx+1], [nty+1]
     int sx, sy;                 // fixed-point bits per cell side
     int twmax, thmax;           // largest tile in cells
     double lx, ly, csx_d, csy_d;
@@ -63,8 +66,6 @@ struct Sys {
     int cap[kRegions];
     int off[kRegions];
     int spill_cap;
-    int stage_cap;              // particles staged in shared memory (fast path)
-    int scratch_cap;            // particles staged in global scratch (deferred path)
     int4 *rec[2];
     int *cnt[2];                // [ntiles * kCntStride]
     int4 *spill_rec[2];
@@ -83,10 +84,8 @@ struct Sys {
 struct Ctl {
     long long step;             // steps taken; parity selects the current buffer
     int tile_next;              // dynamic tile fetch of the step kernel
-    int defer_next;             // dynamic fetch of the deferred kernel
-    int defer_count;            // tiles deferred to the scratch path this step
     int finish_ticket;
-    int pad[2];
+    int pad[4];
 };
 
 // Segment: one region of one (possibly the same) tile mapped into the
@@ -101,46 +100,43 @@ struct Seg {
     int tile, region;
 };
 
-// Per-particle staging arrays (shared memory on the fast path, global
-// scratch on the deferred path) and per-cell tables (always shared).
+// Per-particle staging arrays of one block: shared memory for ordinary tiles,
+// the block's slice of global scratch for tiles that do not fit.
 struct Stage {
-    int *rX, *rY;               // extended-frame fixed-point positions
+    float4 *P;                  // sorted by (cell, id): x, y rel. tile centre, cos, sin
+    int *rX, *rY;               // staged, in the tile's extended frame (fixed point)
     float *rth;                 // orientation
     unsigned *id;
     unsigned short *cell;       // extended cell | flip << 14
     unsigned short *slot;       // rank of arrival in the cell
     unsigned short *gidx;       // grouped-by-cell order -> staged index
     unsigned short *sk;         // sorted order -> staged index
-    float *px, *py, *pc, *ps;   // sorted: position rel. tile centre, cos, sin
-    int *spill_e;               // matched spill entries
-    unsigned char *spill_s;     // their segment
-    int spill_list_cap;
-    int cap;                    // particles
+    unsigned short *ownq;       // own particle o -> sorted position
+    unsigned char *segc;        // segment of staged index 32 i
+    int cap;
 };
 
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// Bytes of the per-particle staging arrays for `cap` particles.
-__host__ __device__ inline size_t stage_particle_bytes(int cap)
+__host__ __device__ inline size_t stage_bytes(int cap)
 {
-    return (size_t)cap * (4 * 4 + 4 * 4 + 4 * 2);
+    return (size_t)cap * (16 + 4 * 4 + 5 * 2) + (size_t)round_up(cap / 32 + 2, 16);
 }
 
-__host__ __device__ inline void carve_particles(Stage &st, unsigned char *p, int cap)
+__host__ __device__ inline void carve_stage(Stage &st, unsigned char *p, int cap)
 {
     st.cap = cap;
+    st.P = (float4 *)p;               p += (size_t)cap * 16;
     st.rX = (int *)p;                 p += (size_t)cap * 4;
     st.rY = (int *)p;                 p += (size_t)cap * 4;
     st.rth = (float *)p;              p += (size_t)cap * 4;
     st.id = (unsigned *)p;            p += (size_t)cap * 4;
-    st.px = (float *)p;               p += (size_t)cap * 4;
-    st.py = (float *)p;               p += (size_t)cap * 4;
-    st.pc = (float *)p;               p += (size_t)cap * 4;
-    st.ps = (float *)p;               p += (size_t)cap * 4;
     st.cell = (unsigned short *)p;    p += (size_t)cap * 2;
     st.slot = (unsigned short *)p;    p += (size_t)cap * 2;
     st.gidx = (unsigned short *)p;    p += (size_t)cap * 2;
-    st.sk = (unsigned short *)p;
+    st.sk = (unsigned short *)p;      p += (size_t)cap * 2;
+    st.ownq = (unsigned short *)p;    p += (size_t)cap * 2;
+    st.segc = p;
 }
 
 // Per-tile tables held in shared memory.
@@ -162,8 +158,7 @@ __host__ __device__ inline void carve_tables(Tables &t, unsigned char *p, int nc
     t.rowpre = (int *)p;
 }
 
-// Spill-match list kept in shared memory on the fast path.
-constexpr int kSpillListFast = 256;
-__host__ __device__ inline size_t spill_list_bytes(int cap) { return (size_t)cap * 5 + 16; }
+// Spill-match list (entry, segment) kept in the block's global scratch.
+__host__ __device__ inline size_t spill_list_bytes(int cap) { return (size_t)round_up(cap * 5 + 16, 256); }
 
 }  // namespace aapk

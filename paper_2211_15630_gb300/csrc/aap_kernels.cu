@@ -4,15 +4,16 @@
 //   k_step     per tile: stage the tile and its one-cell halo (cell lists,
 //              Sec. 3.2, with periodic or mirror images, Sec. 2.4), counting
 //              sort by cell in shared memory (block histogram + block prefix
-//              scan), sum over the 3x3 cells (Eq. collision_VM / collision_NVM
+//              scan, then id order inside each cell), sum over the 3x3
+//              cells (Eq. collision_VM / collision_NVM
 //              or the Langevin sum of Eq. Langevin_dynamics), draw Philox
 //              noise, stream (Eq. streaming or Euler-Maruyama), apply the
 //              boundary rule, and scatter the new record into the region of
 //              its new cell through a warp-aggregated atomic counter.  Also
 //              accumulates p = |sum e^{i theta}| / N (Sec. 3.4) in exact
 //              64-bit integers.
-//   k_deferred the same for tiles whose staged set overflowed shared memory,
-//              staging in global scratch instead.
+//              Tiles whose staged set does not fit shared memory are staged
+//              in the block's slice of global scratch by the same code.
 //   k_finish   turns the step's integer sums into p(t), clears the counters
 //              of the buffer just consumed and advances the step counter.
 #include <cuda_runtime.h>
@@ -21,6 +22,25 @@
 #include "aap_kernels.cuh"
 
 namespace aapk {
+
+// Optional per-phase timing of the step kernel (tracing aid, compiled out
+// unless AAP_PHASE_TIMING is defined): thread 0 of every block adds the clock
+// cycles between phase marks to g_phase[].
+#ifdef AAP_PHASE_TIMING
+__device__ unsigned long long g_phase[16];
+#define PHASE_START() long long ph_t0_ = clock64()
+#define PHASE_MARK(i)                                                         \
+    do {                                                                      \
+        if (threadIdx.x == 0) {                                               \
+            const long long t_ = clock64();                                   \
+            atomicAdd(&g_phase[i], (unsigned long long)(t_ - ph_t0_));        \
+            ph_t0_ = t_;                                                      \
+        }                                                                     \
+    } while (0)
+#else
+#define PHASE_START() do { } while (0)
+#define PHASE_MARK(i) do { } while (0)
+#endif
 
 #define AAP_PI_F 3.14159265358979f
 #define AAP_2PI_F 6.28318530717959f
@@ -50,8 +70,8 @@ __device__ __forceinline__ float u01f(uint32_t w) { return ((float)(w >> 9) + 0.
 __device__ __forceinline__ double u01d(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 // ------------------------------------------------------------ geometry ----
-__device__ __forceinline__ int tile_x0(const Sys &S, int tx) { return (int)(((long long)tx * S.ncx) / S.ntx); }
-__device__ __forceinline__ int tile_y0(const Sys &S, int ty) { return (int)(((long long)ty * S.ncy) / S.nty); }
+__device__ __forceinline__ int tile_x0(const Sys &S, int tx) { return S.x0tab[tx]; }
+__device__ __forceinline__ int tile_y0(const Sys &S, int ty) { return S.y0tab[ty]; }
 __device__ __forceinline__ int tile_of_x(const Sys &S, int cx)
 {
     return (int)((((long long)cx + 1) * S.ntx - 1) / S.ncx);
@@ -119,18 +139,18 @@ struct TileCtx {
     Sys S;
     int sysi, tile, tx, ty, tw, th, W2, H2, nce;
     int twL, twR, thD, thU;     // widths / heights of the neighbour tiles
-    int m_seg, n_spill, m, n_own, defer;
+    int m_seg, n_spill, m, n_own;
+    int next;                   // prefetched next tile index
     int segpre[kSegs + 1];
     int warp_tot[32];
     Seg seg[kSegs];
     long long red[3][32];
 };
 
-// Resolve the halo column (side -1: left, +1: right) of tile tx into a source
+// Resolve the halo column (side -1: left, +1: right) of tile t into a source
 // tile column, the region column class there, and the position / cell maps.
-__device__ __forceinline__ void resolve_axis(int side, int t, int nt, int w, int wlo, int whi,
-                                             int refl, int s, int &src, int &cls, int &a,
-                                             int &c, long long &b, int &flip)
+__device__ __forceinline__ void resolve_axis(int side, int t, int nt, int w, int wlo, int refl, int s,
+                                             int &src, int &cls, int &a, int &c, long long &b, int &flip)
 {
     if (side == 0) {
         src = t; a = 1; c = 0; b = 0; flip = 0; cls = -1;
@@ -140,53 +160,43 @@ __device__ __forceinline__ void resolve_axis(int side, int t, int nt, int w, int
         if (t > 0 || !refl) {
             src = (t > 0) ? t - 1 : nt - 1;
             cls = 2; a = 1; c = -wlo; b = -((long long)wlo << s); flip = 0;
-        } else {
+        } else {        // mirror at the wall x = 0: X -> -X, cell 0 -> -1
             src = t; cls = 0; a = -1; c = -1; b = 0; flip = 1;
         }
     } else {
         if (t < nt - 1 || !refl) {
             src = (t < nt - 1) ? t + 1 : 0;
             cls = 0; a = 1; c = w; b = (long long)w << s; flip = 0;
-        } else {
+        } else {        // mirror at the wall x = L: X -> 2 w 2^s - X, cell w-1 -> w
             src = t; cls = 2; a = -1; c = 2 * w - 1; b = 2 * ((long long)w << s); flip = 1;
         }
     }
-    (void)whi;
 }
 
+// Phase 1 of a tile: geometry, the 25 source segments (9 own regions, 16
+// halo regions with their periodic or mirror maps), spill matches, and the
+// number m of particles to stage.  Ends with the block synchronised.
 template <int NT>
-__device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long long step,
-                             Ctl *ctl, int *defer_list, int gtile, bool scratch)
+__device__ __forceinline__ void tile_setup(TileCtx &T, const Tables &tb, int cur, int nce_max,
+                                           int *spill_e, unsigned char *spill_s, int spill_list_cap)
 {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const Sys &S = T.S;
-    const int cur = (int)(step & 1), nxt = cur ^ 1;
-
-    // --- A. tile geometry ----------------------------------------------
+    const int tx = T.tile % S.ntx, ty = T.tile / S.ntx;
+    const int x0 = S.x0tab[tx], y0 = S.y0tab[ty];
+    const int tw = S.x0tab[tx + 1] - x0, th = S.y0tab[ty + 1] - y0;
+    const int txl = tx > 0 ? tx - 1 : S.ntx - 1, txr = tx < S.ntx - 1 ? tx + 1 : 0;
+    const int tyd = ty > 0 ? ty - 1 : S.nty - 1, tyu = ty < S.nty - 1 ? ty + 1 : 0;
+    const int twL = S.x0tab[txl + 1] - S.x0tab[txl], twR = S.x0tab[txr + 1] - S.x0tab[txr];
+    const int thD = S.y0tab[tyd + 1] - S.y0tab[tyd], thU = S.y0tab[tyu + 1] - S.y0tab[tyu];
     if (tid == 0) {
-        const int tx = T.tile % S.ntx, ty = T.tile / S.ntx;
-        T.tx = tx;
-        T.ty = ty;
-        const int x0 = tile_x0(S, tx), x1 = tile_x0(S, tx + 1);
-        const int y0 = tile_y0(S, ty), y1 = tile_y0(S, ty + 1);
-        T.tw = x1 - x0;
-        T.th = y1 - y0;
-        T.W2 = T.tw + 2;
-        T.H2 = T.th + 2;
-        T.nce = T.W2 * T.H2;
-        const int txl = tx > 0 ? tx - 1 : S.ntx - 1, txr = tx < S.ntx - 1 ? tx + 1 : 0;
-        const int tyd = ty > 0 ? ty - 1 : S.nty - 1, tyu = ty < S.nty - 1 ? ty + 1 : 0;
-        T.twL = tile_x0(S, txl + 1) - tile_x0(S, txl);
-        T.twR = tile_x0(S, txr + 1) - tile_x0(S, txr);
-        T.thD = tile_y0(S, tyd + 1) - tile_y0(S, tyd);
-        T.thU = tile_y0(S, tyu + 1) - tile_y0(S, tyu);
+        T.tx = tx; T.ty = ty; T.tw = tw; T.th = th;
+        T.W2 = tw + 2; T.H2 = th + 2; T.nce = (tw + 2) * (th + 2);
+        T.twL = twL; T.twR = twR; T.thD = thD; T.thU = thU;
         T.n_spill = 0;
-        T.defer = 0;
     }
-    __syncthreads();
-
-    // --- B. the 25 segments: 9 own regions, then the 16 halo regions ---
+    for (int i = tid; i < nce_max; i += NT) tb.hist[i] = 0;
     if (tid < kSegs) {
         int bxo, byo, rx = -1, ry = -1;
         if (tid < 9) {
@@ -201,8 +211,8 @@ __device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long 
         }
         int srcx, clsx, ax, cx, fx, srcy, clsy, ay, cy, fy;
         long long bxx, byy;
-        resolve_axis(bxo, T.tx, S.ntx, T.tw, T.twL, T.twR, S.bx, S.sx, srcx, clsx, ax, cx, bxx, fx);
-        resolve_axis(byo, T.ty, S.nty, T.th, T.thD, T.thU, S.by, S.sy, srcy, clsy, ay, cy, byy, fy);
+        resolve_axis(bxo, tx, S.ntx, tw, twL, S.bx, S.sx, srcx, clsx, ax, cx, bxx, fx);
+        resolve_axis(byo, ty, S.nty, th, thD, S.by, S.sy, srcy, clsy, ay, cy, byy, fy);
         if (clsx < 0) clsx = rx;
         if (clsy < 0) clsy = ry;
         Seg g;
@@ -215,6 +225,7 @@ __device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long 
         g.flip = fx | (fy << 1);
         T.seg[tid] = g;
     }
+    const int nsp = min(*((volatile int *)&S.spill_cnt[cur]), S.spill_cap);
     __syncthreads();
     if (warp == 0) {
         const int v = lane < kSegs ? T.seg[lane].count : 0;
@@ -225,60 +236,104 @@ __device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long 
             T.m_seg = incl;
         }
     }
-    // --- C. particles parked in the spill list for one of our segments ---
-    const int nsp = min(*((volatile int *)&S.spill_cnt[cur]), S.spill_cap);
-    __syncthreads();
     if (nsp > 0) {
+        // particles parked in the spill list for one of our segments
         for (int e = tid; e < nsp; e += NT) {
             const int key = S.spill_key[cur][e];
             const int et = key / kCntStride, er = key % kCntStride;
             for (int s = 0; s < kSegs; ++s) {
                 if (T.seg[s].tile == et && T.seg[s].region == er) {
                     const int j = atomicAdd(&T.n_spill, 1);
-                    if (j < A.spill_list_cap) {
-                        A.spill_e[j] = e;
-                        A.spill_s[j] = (unsigned char)s;
+                    if (j < spill_list_cap) {
+                        spill_e[j] = e;
+                        spill_s[j] = (unsigned char)s;
                     }
                 }
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
     if (tid == 0) {
+        if (T.n_spill > spill_list_cap) {
+            atomicOr(S.err, ERR_STAGE);
+            T.n_spill = spill_list_cap;
+        }
         T.m = T.m_seg + T.n_spill;
-        if (T.m > A.cap || T.n_spill > A.spill_list_cap) {
-            if (!scratch) {
-                const int d = atomicAdd(&ctl->defer_count, 1);
-                defer_list[d] = gtile;
-            } else {
-                atomicOr(S.err, ERR_STAGE | ERR_LOST);
+    }
+    __syncthreads();
+}
+
+// The 3x3-cell neighbour sum of one particle (Eq. collision_VM / NVM, or the
+// Langevin coupling sum): rows of three consecutive cells are contiguous in
+// the (cell, id) order.  The particle itself is included: it adds e^{i theta_i}
+// to the VM/NVM sum and sin 0 to the Langevin sum; cnt counts it.
+template <int MODEL>
+__device__ __forceinline__ void neighbour_sum(const float4 *__restrict__ P, const int *cstart, int ec,
+                                              int W2, float4 pi, float r2, float &sc, float &ss, int &cnt)
+{
+    sc = 0.f;
+    ss = 0.f;
+    cnt = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int c0 = ec + dy * W2 - 1;
+        const int a = cstart[c0], b = cstart[c0 + 3];
+#pragma unroll 4
+        for (int j = a; j < b; ++j) {
+            const float4 pj = P[j];
+            const float dx = pj.x - pi.x, dyy = pj.y - pi.y;
+            const float d2 = fmaf(dx, dx, dyy * dyy);
+            if (d2 <= r2) {
+                float cj = pj.z, sj = pj.w;
+                if (MODEL == 2 && fmaf(pi.z, cj, pi.w * sj) < 0.f) {
+                    cj = -cj;
+                    sj = -sj;
+                }
+                sc += cj;
+                ss += sj;
+                ++cnt;
             }
-            T.defer = 1;
         }
     }
-    __syncthreads();
-    if (T.defer) return;
+}
 
+// Phase 2 of a tile, staged in A (shared memory or the block's scratch).
+template <int NT, int MODEL>
+__device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tables &tb, long long step,
+                                          const int *spill_e, const unsigned char *spill_s)
+{
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const Sys &S = T.S;
+    const int cur = (int)(step & 1), nxt = cur ^ 1;
     const int m = T.m, m_seg = T.m_seg, W2 = T.W2, H2 = T.H2, nce = T.nce;
-    for (int i = tid; i < nce; i += NT) tb.hist[i] = 0;
+    const int tw = T.tw, th = T.th;
+    PHASE_START();
+
+    // --- segment of every 32nd staged index (chunk table) ---------------
+    for (int i = tid; i * 32 < m_seg; i += NT) {
+        const int k = i * 32;
+        int lo = 0, hi = kSegs;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (T.segpre[mid] <= k) lo = mid; else hi = mid;
+        }
+        A.segc[i] = (unsigned char)lo;
+    }
     __syncthreads();
 
-    // --- D. stage: decode, map into the extended frame, histogram by cell --
+    // --- stage: decode, map into the extended frame, histogram by cell ----
     for (int k = tid; k < m; k += NT) {
         int s;
         int4 r;
         if (k < m_seg) {
-            int lo = 0, hi = kSegs;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (T.segpre[mid] <= k) lo = mid; else hi = mid;
-            }
-            s = lo;
+            s = A.segc[k >> 5];
+            while (T.segpre[s + 1] <= k) ++s;
             r = T.seg[s].base[k - T.segpre[s]];
         } else {
             const int j = k - m_seg;
-            s = A.spill_s[j];
-            r = S.spill_rec[cur][A.spill_e[j]];
+            s = spill_s[j];
+            r = S.spill_rec[cur][spill_e[j]];
         }
         const Seg &g = T.seg[s];
         const int lx = r.x >> S.sx, ly = r.y >> S.sy;
@@ -297,8 +352,9 @@ __device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long 
         A.slot[k] = (unsigned short)atomicAdd(&tb.hist[ec], 1);
     }
     __syncthreads();
+    PHASE_MARK(0);
 
-    // --- E. block-level exclusive prefix scan of the cell histogram ------
+    // --- block-level exclusive prefix scan of the cell histogram ----------
     {
         const int per = (nce + NT - 1) / NT;
         const int b0 = min(tid * per, nce), e0 = min(b0 + per, nce);
@@ -321,16 +377,33 @@ __device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long 
         }
     }
     __syncthreads();
+    PHASE_MARK(1);
 
-    // --- F. group by cell -------------------------------------------------
+    // --- group by cell; own rows prefix ----------------------------------
     for (int k = tid; k < m; k += NT) {
         const int c = A.cell[k] & 0x3fff;
         A.gidx[tb.cstart[c] + A.slot[k]] = (unsigned short)k;
     }
+    if (warp == NT / 32 - 1) {
+        int carry = 0;
+        for (int r0 = 0; r0 < th; r0 += 32) {
+            const int r = r0 + lane;
+            int len = 0;
+            if (r < th) len = tb.cstart[(r + 1) * W2 + tw + 1] - tb.cstart[(r + 1) * W2 + 1];
+            const int incl = warp_incl_scan(len);
+            if (r < th) tb.rowpre[r] = carry + incl - len;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) {
+            tb.rowpre[th] = carry;
+            T.n_own = carry;
+        }
+    }
     __syncthreads();
+    PHASE_MARK(2);
 
-    // --- G. order each cell by particle id and lay out the sorted arrays --
-    const int xc = T.tw << (S.sx - 1), yc = T.th << (S.sy - 1);
+    // --- order each cell by particle id; sorted records; own list ---------
+    const int xc = tw << (S.sx - 1), yc = th << (S.sy - 1);
     for (int p = tid; p < m; p += NT) {
         const int k = A.gidx[p];
         const unsigned short cf = A.cell[k];
@@ -344,45 +417,27 @@ __device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long 
             rank += (id2 < myid) || (id2 == myid && k2 < k);
         }
         const int q = a + rank;
-        float th = A.rth[k];
-        if (S.model == 1 && S.order != 1) th *= (float)S.order;
+        float thv = A.rth[k];
+        if (MODEL == 1 && S.order != 1) thv *= (float)S.order;
         float sn, cs;
-        sincosf(th, &sn, &cs);
+        sincosf(thv, &sn, &cs);
         const int flip = cf >> 14;
         if (flip & 1) {
-            if (S.model != 1 || (S.order & 1)) cs = -cs; else sn = -sn;
+            if (MODEL != 1 || (S.order & 1)) cs = -cs; else sn = -sn;
         }
         if (flip & 2) sn = -sn;
-        A.px[q] = (float)(A.rX[k] - xc) * S.ux;
-        A.py[q] = (float)(A.rY[k] - yc) * S.uy;
-        A.pc[q] = cs;
-        A.ps[q] = sn;
+        A.P[q] = make_float4((float)(A.rX[k] - xc) * S.ux, (float)(A.rY[k] - yc) * S.uy, cs, sn);
         A.sk[q] = (unsigned short)k;
+        const int ey = c / W2, ex = c - ey * W2;
+        if (ey >= 1 && ey <= th && ex >= 1 && ex <= tw)
+            A.ownq[tb.rowpre[ey - 1] + q - tb.cstart[ey * W2 + 1]] = (unsigned short)q;
     }
     __syncthreads();
+    PHASE_MARK(3);
 
-    // --- H. own particles, in (cell, id) order, row by row ---------------
-    if (warp == 0) {
-        int carry = 0;
-        for (int r0 = 0; r0 < T.th; r0 += 32) {
-            const int r = r0 + lane;
-            int len = 0;
-            if (r < T.th) len = tb.cstart[(r + 1) * W2 + T.tw + 1] - tb.cstart[(r + 1) * W2 + 1];
-            const int incl = warp_incl_scan(len);
-            if (r < T.th) tb.rowpre[r] = carry + incl - len;
-            carry += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        if (lane == 0) {
-            tb.rowpre[T.th] = carry;
-            T.n_own = carry;
-        }
-    }
-    __syncthreads();
-
-    // --- I. interact, update, scatter ------------------------------------
-    const int n_own = T.n_own, th_t = T.th, tw = T.tw, th = T.th;
+    // --- interact, update, scatter ---------------------------------------
+    const int n_own = T.n_own;
     const float r2 = S.r2;
-    const int model = S.model;
     const int TWs = tw << S.sx, THs = th << S.sy;
     long long acc_c = 0, acc_s = 0, acc_n = 0;
     for (int base = 0; base < n_own; base += NT) {
@@ -391,59 +446,36 @@ __device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long 
         int4 rec = make_int4(0, 0, 0, 0);
         int dtile = 0, region = 0;
         if (act) {
-            int lo = 0, hi = th_t;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (tb.rowpre[mid] <= o) lo = mid; else hi = mid;
-            }
-            const int q = tb.cstart[(lo + 1) * W2 + 1] + (o - tb.rowpre[lo]);
+            const int q = A.ownq[o];
             const int k = A.sk[q];
             const int X = A.rX[k], Y = A.rY[k];
             const float thi = A.rth[k];
             const unsigned id = A.id[k];
-            const int ec = A.cell[k] & 0x3fff;   // clamped into the tile when staged
-            const float xi = A.px[q], yi = A.py[q], ci = A.pc[q], si = A.ps[q];
-            float sc = 0.f, ss = 0.f;
-            int cnt = 0;
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int c0 = ec + dy * W2 - 1;
-                const int a = tb.cstart[c0], b = tb.cstart[c0 + 3];
-                for (int j = a; j < b; ++j) {
-                    const float dx = A.px[j] - xi, dyy = A.py[j] - yi;
-                    const float d2 = fmaf(dx, dx, dyy * dyy);
-                    if (d2 <= r2) {
-                        float cj = A.pc[j], sj = A.ps[j];
-                        if (model == 2 && fmaf(ci, cj, si * sj) < 0.f) {
-                            cj = -cj;
-                            sj = -sj;
-                        }
-                        sc += cj;
-                        ss += sj;
-                        ++cnt;
-                    }
-                }
-            }
+            const int ec = A.cell[k] & 0x3fff;
+            const float4 pi = A.P[q];
+            float sc, ss;
+            int cnt;
+            neighbour_sum<MODEL>(A.P, tb.cstart, ec, W2, pi, r2, sc, ss, cnt);
             const int nb = cnt - 1;          // the particle itself was counted
             uint32_t c4[4] = {id, (uint32_t)step, (uint32_t)((unsigned long long)step >> 32), 0u};
             philox4x32_10(c4, S.seed_lo, S.seed_hi);
             const float u0 = u01f(c4[0]);
             float thn, cn, sn;
             int dX, dY;
-            if (model != 1) {
-                // Eq. (collision_VM) / (collision_NVM): the sum includes e^{i theta_i}.
+            if (MODEL != 1) {
+                // Eq. (collision_VM) / (collision_NVM) + noise; Eq. (streaming)
                 thn = atan2f(ss, sc) + S.omega_step + S.eta_pi * (2.0f * u0 - 1.0f);
                 sincosf(thn, &sn, &cn);
                 dX = __float2int_rn(S.kx * cn);
                 dY = __float2int_rn(S.ky * sn);
             } else {
-                // Eq. (Langevin_dynamics), Euler-Maruyama; the self term adds sin 0.
+                // Eq. (Langevin_dynamics), one Euler-Maruyama step
                 const float u1 = u01f(c4[1]);
                 const float h = S.weight ? 1.0f : 1.0f / (1.0f + (float)nb);
-                const float tsum = ci * ss - si * sc;
+                const float tsum = pi.z * ss - pi.w * sc;
                 const float gz = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
                 thn = thi + S.gamma_dt * h * tsum + S.omega_step + S.noise_amp * gz;
-                float co = ci, so = si;
+                float co = pi.z, so = pi.w;
                 if (S.order != 1) sincosf(thi, &so, &co);
                 dX = __float2int_rn(S.kx * co);
                 dY = __float2int_rn(S.ky * so);
@@ -472,20 +504,22 @@ __device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long 
             }
             if (fx) { thn = AAP_PI_F - thn; cn = -cn; }
             if (fy) { thn = -thn; sn = -sn; }
-            if (thn >= AAP_PI_F || thn < -AAP_PI_F) thn -= AAP_2PI_F * floorf((thn + AAP_PI_F) * (1.0f / AAP_2PI_F));
-            if (model == 1) sincosf(thn, &sn, &cn);
+            if (thn >= AAP_PI_F || thn < -AAP_PI_F)
+                thn -= AAP_2PI_F * floorf((thn + AAP_PI_F) * (1.0f / AAP_2PI_F));
+            if (MODEL == 1) sincosf(thn, &sn, &cn);
             if (!isfinite(thn)) atomicOr(S.err, ERR_NAN);
             dtile = dty * S.ntx + dtx;
             region = region_of(Xn >> S.sx, Yn >> S.sy, twd, thd);
             rec = make_int4(Xn, Yn, __float_as_int(thn), (int)id);
-            acc_c += __float2ll_rn(cn * 4294967296.0f);
-            acc_s += __float2ll_rn(sn * 4294967296.0f);
+            acc_c += __float2int_rn(cn * kFixStepF);
+            acc_s += __float2int_rn(sn * kFixStepF);
             acc_n += nb;
             if (S.nbr_out && id < (unsigned long long)S.n) S.nbr_out[id] = nb;
         }
         warp_insert(S, nxt, act, dtile, region, rec);
     }
-    // --- J. per-tile integer sums -> the step's accumulators -------------
+    PHASE_MARK(4);
+    // --- per-tile integer sums -> the step's accumulators ----------------
     acc_c = warp_sum_ll(acc_c);
     acc_s = warp_sum_ll(acc_s);
     acc_n = warp_sum_ll(acc_n);
@@ -501,6 +535,7 @@ __device__ void process_tile(TileCtx &T, const Stage &A, const Tables &tb, long 
         unsigned long long *slot = S.acc + ((size_t)cur * kAccSlots + (T.tile & (kAccSlots - 1))) * kAccWords;
         atomicAdd(slot + tid, (unsigned long long)v);
     }
+    PHASE_MARK(5);
 }
 
 __device__ __forceinline__ int sys_of_tile(const int *tile_base, int nsys, int g)
@@ -513,92 +548,72 @@ __device__ __forceinline__ int sys_of_tile(const int *tile_base, int nsys, int g
     return lo;
 }
 
-__device__ __forceinline__ void load_sys(TileCtx &T, const Sys *sys, int si)
-{
-    if (T.sysi == si) return;
-    __syncthreads();
-    const int words = (int)(sizeof(Sys) / 4);
-    const int *src = reinterpret_cast<const int *>(sys + si);
-    int *dst = reinterpret_cast<int *>(&T.S);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-    __syncthreads();
-    if (threadIdx.x == 0) T.sysi = si;
-    __syncthreads();
-}
-
-// Persistent blocks pull tiles (in raster order, so halos are L2-hot) from a
-// device counter.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_step(const Sys *__restrict__ sys, int nsys,
-                                             const int *__restrict__ tile_base, Ctl *ctl,
-                                             int *defer_list, int stage_cap, int nce_max)
+// Persistent blocks pull tiles in raster order (so halos are L2-hot) from a
+// device counter; the next tile index is fetched while the current one runs.
+// A tile whose staged set exceeds the shared-memory capacity is staged in the
+// block's slice of global scratch instead.  All systems of one launch share
+// the model.
+template <int NT, int MODEL>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3)
+k_step(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_base, Ctl *ctl,
+       int stage_cap, int nce_max, unsigned char *scratch, size_t scratch_per_block, int scratch_cap,
+       int spill_list_cap)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileCtx T;
-    __shared__ int s_next;
     const long long step = ctl->step;
+    const int cur = (int)(step & 1);
     const int total = tile_base[nsys];
-    Stage A;
-    carve_particles(A, smem, stage_cap);
-    unsigned char *p = smem + stage_particle_bytes(stage_cap);
+    Stage As;
+    carve_stage(As, smem, stage_cap);
     Tables tb;
-    carve_tables(tb, p, nce_max);
-    p += table_bytes(nce_max);
-    A.spill_e = (int *)p;
-    A.spill_s = (unsigned char *)(p + kSpillListFast * 4);
-    A.spill_list_cap = kSpillListFast;
-    if (threadIdx.x == 0) T.sysi = -1;
-    __syncthreads();
-    for (;;) {
-        if (threadIdx.x == 0) s_next = atomicAdd(&ctl->tile_next, 1);
-        __syncthreads();
-        const int g = s_next;
-        __syncthreads();
-        if (g >= total) break;
-        const int si = sys_of_tile(tile_base, nsys, g);
-        load_sys(T, sys, si);
-        if (threadIdx.x == 0) T.tile = g - tile_base[si];
-        __syncthreads();
-        process_tile<NT>(T, A, tb, step, ctl, defer_list, g, false);
-        __syncthreads();
-    }
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT) k_deferred(const Sys *__restrict__ sys, int nsys,
-                                                 const int *__restrict__ tile_base, Ctl *ctl,
-                                                 const int *defer_list, unsigned char *scratch,
-                                                 size_t scratch_per_block, int scratch_cap,
-                                                 int nce_max)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ TileCtx T;
-    __shared__ int s_next;
-    const int count = *((volatile int *)&ctl->defer_count);
-    if (count == 0) return;
-    const long long step = ctl->step;
-    Stage A;
+    carve_tables(tb, smem + stage_bytes(stage_cap), nce_max);
     unsigned char *mine = scratch + scratch_per_block * blockIdx.x;
-    carve_particles(A, mine, scratch_cap);
-    A.spill_e = (int *)(mine + stage_particle_bytes(scratch_cap));
-    A.spill_s = (unsigned char *)(A.spill_e + scratch_cap);
-    A.spill_list_cap = scratch_cap;
-    Tables tb;
-    carve_tables(tb, smem, nce_max);
-    if (threadIdx.x == 0) T.sysi = -1;
+    Stage Ag;
+    carve_stage(Ag, mine, scratch_cap);
+    int *spill_e = (int *)(mine + stage_bytes(scratch_cap));
+    unsigned char *spill_s = (unsigned char *)(spill_e + spill_list_cap);
+    if (threadIdx.x == 0) {
+        T.sysi = -1;
+        T.next = atomicAdd(&ctl->tile_next, 1);
+    }
     __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) s_next = atomicAdd(&ctl->defer_next, 1);
+        const int g = T.next;
+        if (g >= total) break;
+        const int si = nsys > 1 ? sys_of_tile(tile_base, nsys, g) : 0;
+        if (si != T.sysi) {
+            const int words = (int)(sizeof(Sys) / 4);
+            const int *src = reinterpret_cast<const int *>(sys + si);
+            int *dst = reinterpret_cast<int *>(&T.S);
+            for (int i = threadIdx.x; i < words; i += NT) dst[i] = src[i];
+        }
         __syncthreads();
-        const int i = s_next;
+        if (threadIdx.x == 0) {
+            T.sysi = si;
+            T.tile = g - tile_base[si];
+            T.next = atomicAdd(&ctl->tile_next, 1);
+        }
         __syncthreads();
-        if (i >= count) break;
-        const int g = defer_list[i];
-        const int si = sys_of_tile(tile_base, nsys, g);
-        load_sys(T, sys, si);
-        if (threadIdx.x == 0) T.tile = g - tile_base[si];
-        __syncthreads();
-        process_tile<NT>(T, A, tb, step, ctl, nullptr, g, true);
+#ifdef AAP_PHASE_TIMING
+        const long long ts0 = clock64();
+#endif
+        tile_setup<NT>(T, tb, cur, nce_max, spill_e, spill_s, spill_list_cap);
+#ifdef AAP_PHASE_TIMING
+        if (threadIdx.x == 0) {
+            atomicAdd(&g_phase[6], (unsigned long long)(clock64() - ts0));
+            atomicAdd(&g_phase[7], 1ull);
+            atomicAdd(&g_phase[8], (unsigned long long)T.m);
+            atomicAdd(&g_phase[9], (unsigned long long)(T.m > stage_cap));
+        }
+#endif
+        if (T.m <= stage_cap) {
+            tile_body<NT, MODEL>(T, As, tb, step, spill_e, spill_s);
+        } else if (T.m <= scratch_cap) {
+            tile_body<NT, MODEL>(T, Ag, tb, step, spill_e, spill_s);
+        } else if (threadIdx.x == 0) {
+            atomicOr(T.S.err, ERR_STAGE | ERR_LOST);
+        }
         __syncthreads();
     }
 }
@@ -638,7 +653,7 @@ __global__ void k_finish(Sys *sys, int nsys, Ctl *ctl)
             a[k * kAccWords + 2] = 0;
         }
         const double n = (double)S.n;
-        const double dc = (double)sc / kFix, ds = (double)ss / kFix;
+        const double dc = (double)sc / kFixStep, ds = (double)ss / kFixStep;
         const double phi = n > 0 ? sqrt(dc * dc + ds * ds) / n : 0.0;
         const double nbar = n > 0 ? (double)sn / n : 0.0;
         if (S.trace) {
@@ -654,8 +669,6 @@ __global__ void k_finish(Sys *sys, int nsys, Ctl *ctl)
     __syncthreads();
     if (threadIdx.x == 0) {
         ctl->tile_next = 0;
-        ctl->defer_next = 0;
-        ctl->defer_count = 0;
         ctl->finish_ticket = 0;
         ctl->step = step + 1;
     }
@@ -791,65 +804,67 @@ __global__ void k_observe(Sys S, int b, unsigned long long *out)
 }
 
 // --------------------------------------------------------------- launchers --
-template <int NT>
+size_t step_smem_bytes(int stage_cap, int nce_max) { return stage_bytes(stage_cap) + table_bytes(nce_max); }
+
+template <int NT, int MODEL>
 static cudaError_t launch_step_t(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev)
 {
     const size_t smem = step_smem_bytes(L.stage_cap, L.nce_max);
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    k_step<NT><<<L.grid_step, NT, smem, st>>>(L.sys, L.nsys, L.tile_base, L.ctl, L.defer_list,
-                                               L.stage_cap, L.nce_max);
+    k_step<NT, MODEL><<<L.grid_step, NT, smem, st>>>(L.sys, L.nsys, L.tile_base, L.ctl, L.stage_cap,
+                                                      L.nce_max, L.scratch, L.scratch_per_block,
+                                                      L.scratch_cap, L.spill_list_cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-    k_deferred<NT><<<L.grid_defer, NT, table_bytes(L.nce_max), st>>>(
-        L.sys, L.nsys, L.tile_base, L.ctl, L.defer_list, L.scratch, L.scratch_per_block,
-        L.scratch_cap, L.nce_max);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
     k_finish<<<L.grid_finish, 256, 0, st>>>(L.sys, L.nsys, L.ctl);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
-size_t step_smem_bytes(int stage_cap, int nce_max)
+template <int MODEL>
+static cudaError_t launch_step_m(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev)
 {
-    return stage_particle_bytes(stage_cap) + table_bytes(nce_max) + spill_list_bytes(kSpillListFast);
+    switch (L.threads) {
+    case 256: return launch_step_t<256, MODEL>(L, st, ev);
+    case 512: return launch_step_t<512, MODEL>(L, st, ev);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev)
 {
-    switch (L.threads) {
-    case 128: return launch_step_t<128>(L, st, ev);
-    case 256: return launch_step_t<256>(L, st, ev);
-    case 512: return launch_step_t<512>(L, st, ev);
+    switch (L.model) {
+    case 0: return launch_step_m<0>(L, st, ev);
+    case 1: return launch_step_m<1>(L, st, ev);
+    case 2: return launch_step_m<2>(L, st, ev);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t configure_step_kernels(int threads, size_t smem_bytes)
+template <int NT, int MODEL>
+static cudaError_t config_t(size_t smem, int *bps)
 {
-    cudaError_t e = cudaSuccess;
-    switch (threads) {
-    case 128: e = cudaFuncSetAttribute(k_step<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes); break;
-    case 256: e = cudaFuncSetAttribute(k_step<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes); break;
-    case 512: e = cudaFuncSetAttribute(k_step<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return e;
+    cudaError_t e = cudaFuncSetAttribute(k_step<NT, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_step<NT, MODEL>, NT, smem);
 }
 
-cudaError_t step_blocks_per_sm(int threads, size_t smem_bytes, int *out)
+cudaError_t configure_step_kernel(int model, int threads, size_t smem_bytes, int *blocks_per_sm)
 {
-    switch (threads) {
-    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step<128>, 128, smem_bytes);
-    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step<256>, 256, smem_bytes);
-    case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step<512>, 512, smem_bytes);
-    default: return cudaErrorInvalidValue;
+    if (threads == 256) {
+        if (model == 0) return config_t<256, 0>(smem_bytes, blocks_per_sm);
+        if (model == 1) return config_t<256, 1>(smem_bytes, blocks_per_sm);
+        if (model == 2) return config_t<256, 2>(smem_bytes, blocks_per_sm);
+    } else if (threads == 512) {
+        if (model == 0) return config_t<512, 0>(smem_bytes, blocks_per_sm);
+        if (model == 1) return config_t<512, 1>(smem_bytes, blocks_per_sm);
+        if (model == 2) return config_t<512, 2>(smem_bytes, blocks_per_sm);
     }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_insert(const Sys &S, int b, const double *x, const double *y, const float *th,
@@ -875,5 +890,12 @@ cudaError_t launch_observe(const Sys &S, int b, unsigned long long *out, cudaStr
     k_observe<<<1024, 256, 0, st>>>(S, b, out);
     return cudaGetLastError();
 }
+
+#ifdef AAP_PHASE_TIMING
+cudaError_t read_phase_times(unsigned long long *out16)
+{
+    return cudaMemcpyFromSymbol(out16, g_phase, sizeof(unsigned long long) * 16);
+}
+#endif
 
 }  // namespace aapk

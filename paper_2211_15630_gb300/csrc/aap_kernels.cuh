@@ -12,25 +12,26 @@ namespace aapk {
 struct LaunchCfg {
     Sys *sys;                    // device array [nsys]
     int nsys;
+    int model;                   // shared by all systems of the launch
     const int *tile_base;        // device [nsys + 1]: prefix of tiles per system
     Ctl *ctl;
-    int *defer_list;             // device [total tiles]
-    unsigned char *scratch;      // device [grid_defer * scratch_per_block]
+    unsigned char *scratch;      // device [grid_step * scratch_per_block]
     size_t scratch_per_block;
-    int scratch_cap;             // particles per deferred block
-    int threads;                 // 128, 256 or 512
+    int scratch_cap;             // particles a block can stage in global scratch
+    int spill_list_cap;          // spill matches a block can hold
+    int threads;                 // 256 or 512
     int stage_cap;               // particles staged in shared memory
     int nce_max;                 // cells of the largest tile plus its ring
-    int grid_step, grid_defer, grid_finish;
+    int grid_step, grid_finish;
 };
 
 size_t step_smem_bytes(int stage_cap, int nce_max);
-cudaError_t configure_step_kernels(int threads, size_t smem_bytes);
-cudaError_t step_blocks_per_sm(int threads, size_t smem_bytes, int *out);
+// Set the dynamic shared-memory limit of the step kernel and report how many
+// of its blocks fit on one SM.
+cudaError_t configure_step_kernel(int model, int threads, size_t smem_bytes, int *blocks_per_sm);
 
-// One full step: k_step, k_deferred (no-op unless a tile overflowed shared
-// memory), k_finish.  With ev != nullptr, ev[0..3] are recorded before
-// k_step and after each of the three kernels.
+// One full step: k_step then k_finish.  With ev != nullptr, ev[0..2] are
+// recorded before k_step, after k_step and after k_finish.
 cudaError_t launch_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev = nullptr);
 
 cudaError_t launch_insert(const Sys &S, int b, const double *x, const double *y, const float *th,
