@@ -121,7 +121,19 @@ typedef struct aap_layout {
     double  cell_x, cell_y;   /* cell sides L/floor(L/R)                        */
 } aap_layout;
 
+/* On-the-fly measurements (Sec. 3.4): moments k = 1..4 of the polar order
+ * p, the nematic order q and the mean neighbour number nbar, over the states
+ * t = t0 .. t0+n-1 of n measured steps (the last state is not used). */
+typedef struct aap_results {
+    int64_t samples;          /* number of measured states                      */
+    double  p[4];             /* <p>, <p^2>, <p^3>, <p^4>                        */
+    double  q[4];             /* <q^k>                                           */
+    double  nbar[4];          /* <nbar^k> of the ensemble-averaged neighbour number */
+    double  binder;           /* U = 1 - <p^4> / (3 <p^2>^2) (Fig. mfL caption)  */
+} aap_results;
+
 typedef struct aap_handle aap_handle;
+typedef struct aap_ens aap_ens;
 
 /* Message of the calling thread's last failure ("" if none).  The pointer
  * stays valid until the next call from the same thread. */
@@ -189,6 +201,28 @@ int aap_sync(aap_handle *h);
 /* Geometry and memory layout of h. */
 int aap_get_layout(aap_handle *h, aap_layout *out);
 
+/* Advance nsteps steps measuring on the fly (like
+ * <model>_measurement_timesteps, Sec. 4): the states t0 .. t0+nsteps-1 are
+ * added to the running sums read by aap_get_results.  Enqueues work only. */
+int aap_measure(aap_handle *h, int64_t nsteps);
+
+/* Normalised measurement results accumulated since creation or the last
+ * aap_clear_results (like aappp_get_results, Sec. 4).  Synchronises. */
+int aap_get_results(aap_handle *h, aap_results *out);
+
+/* Forget the accumulated measurements. */
+int aap_clear_results(aap_handle *h);
+
+/* Coarse-grained fields of the current state into a caller-owned DEVICE
+ * buffer dev_out of 3 * nbx * nby floats (e.g. a torch tensor's data_ptr()):
+ * plane 0 the particle density, planes 1 and 2 the polarisation density
+ * sum cos theta, sum sin theta, each per unit area of the nbx x nby bins of
+ * the box (row-major, x fastest).  Sums are exact 64-bit integer sums, so the
+ * fields are reproducible bit for bit.  Runs on h's stream without syncing.
+ * The binned density integrates to N and the binned polarisation to
+ * sum e^{i theta}, so p (Sec. 3.4) follows from the fields.  nbx, nby >= 1. */
+int aap_coarse_grain(aap_handle *h, int32_t nbx, int32_t nby, float *dev_out);
+
 /* Per-kernel timing (tracing aid).  enable != 0: every step enqueued by
  * aap_step / aap_phi_trace / aap_step_neighbours records CUDA events on h's
  * stream around its two kernels (the tile step and the step finish); the
@@ -199,6 +233,54 @@ int aap_set_timing(aap_handle *h, int32_t enable);
  * index 0 the tile step kernel, 1 the finish kernel, 2 reserved (0)
  * (ms[3], launches[3], caller-owned host arrays).  Synchronises. */
 int aap_get_timing(aap_handle *h, double *ms, int64_t *launches);
+
+/* ---- batched ensembles ---------------------------------------------------
+ * Independent replicas (a phase-diagram sweep) advanced together: every step
+ * of all replicas is one launch of the tile kernel over a shared work list of
+ * (replica, tile) plus one finish launch, replayed from a captured CUDA graph.
+ * Each replica follows exactly the trajectory a standalone handle with the
+ * same parameters (and the same tile shape) would: the results are bit for
+ * bit identical.  All replicas must use the same model. */
+
+/* Create count >= 1 replicas from params[0..count-1] on `stream`; tile shapes
+ * left at 0 follow the ensemble's tiling policy (aap_ens_autotune).
+ * Errors: AAP_EINVAL (any invalid replica, mixed models), AAP_ENOMEM,
+ * AAP_ECUDA. */
+int aap_ens_create(const aap_params *params, int32_t count, void *stream, aap_ens **out);
+
+/* Advance every replica by nsteps steps.  Enqueues work only. */
+int aap_ens_step(aap_ens *e, int64_t nsteps);
+
+/* Advance nsteps steps measuring p, q and nbar on the fly for every replica
+ * (the window convention of aap_measure).  Enqueues work only. */
+int aap_ens_measure(aap_ens *e, int64_t nsteps);
+
+/* Time-averaged polar order <p> of every replica over its measured states
+ * (out: count host doubles).  Synchronises. */
+int aap_ens_phi_mean(aap_ens *e, double *out);
+
+/* Full measurement results of replica r.  Synchronises. */
+int aap_ens_results(aap_ens *e, int32_t r, aap_results *out);
+
+/* State of replica r, as aap_get_state.  Synchronises. */
+int aap_ens_get_state(aap_ens *e, int32_t r, double *x, double *y, float *theta, int64_t n);
+
+/* Layout of replica r (its tile shape reproduces the replica standalone). */
+int aap_ens_get_layout(aap_ens *e, int32_t r, aap_layout *out);
+
+/* Autotuner of block and tile shapes: time trial_steps steps of the whole
+ * ensemble under each candidate policy (threads per block x nominal tile),
+ * keep the fastest and re-create every replica in its initial state with it.
+ * Only allowed before the first step.  *policy_out (may be NULL) receives the
+ * chosen policy index; *ms_out (may be NULL, 8 doubles) the trial times in
+ * milliseconds per step (0 for policies not tried).  Synchronises. */
+int aap_ens_autotune(aap_ens *e, int32_t trial_steps, int32_t *policy_out, double *ms_out);
+
+/* Number of replicas and the current step. */
+int aap_ens_info(aap_ens *e, int32_t *count, int64_t *step);
+
+/* Free the ensemble (NULL accepted).  Synchronises its stream. */
+int aap_ens_destroy(aap_ens *e);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,9 @@ EXPORTS = (
     "aap_last_error", "aap_abi_version", "aap_params_default", "aap_create", "aap_destroy",
     "aap_step", "aap_phi_trace", "aap_observe", "aap_get_state", "aap_set_state",
     "aap_step_neighbours", "aap_sync", "aap_get_layout", "aap_set_timing", "aap_get_timing",
+    "aap_measure", "aap_get_results", "aap_clear_results", "aap_coarse_grain",
+    "aap_ens_create", "aap_ens_step", "aap_ens_measure", "aap_ens_phi_mean", "aap_ens_results",
+    "aap_ens_get_state", "aap_ens_get_layout", "aap_ens_autotune", "aap_ens_info", "aap_ens_destroy",
 )
 
 
@@ -59,6 +62,15 @@ class aap_layout(C.Structure):
                 ("cell_y", C.c_double)]
 
 
+class aap_results(C.Structure):
+    _fields_ = [("samples", C.c_int64), ("p", C.c_double * 4), ("q", C.c_double * 4),
+                ("nbar", C.c_double * 4), ("binder", C.c_double)]
+
+
+# launch policies tried by aap_ens_autotune: (threads, nominal tile w, h)
+ENS_POLICIES = ((512, 32, 16), (256, 32, 16), (512, 16, 16), (256, 16, 16),
+                (512, 32, 32), (256, 16, 8), (512, 64, 16), (512, 16, 8))
+
 _lib = None
 
 
@@ -88,6 +100,20 @@ def load(path: str = LIB_PATH):
         "aap_get_layout": (C.c_int, [vp, P(aap_layout)]),
         "aap_set_timing": (C.c_int, [vp, i32]),
         "aap_get_timing": (C.c_int, [vp, vp, vp]),
+        "aap_measure": (C.c_int, [vp, i64]),
+        "aap_get_results": (C.c_int, [vp, P(aap_results)]),
+        "aap_clear_results": (C.c_int, [vp]),
+        "aap_coarse_grain": (C.c_int, [vp, i32, i32, vp]),
+        "aap_ens_create": (C.c_int, [vp, i32, vp, P(vp)]),
+        "aap_ens_step": (C.c_int, [vp, i64]),
+        "aap_ens_measure": (C.c_int, [vp, i64]),
+        "aap_ens_phi_mean": (C.c_int, [vp, vp]),
+        "aap_ens_results": (C.c_int, [vp, i32, P(aap_results)]),
+        "aap_ens_get_state": (C.c_int, [vp, i32, vp, vp, vp, i64]),
+        "aap_ens_get_layout": (C.c_int, [vp, i32, P(aap_layout)]),
+        "aap_ens_autotune": (C.c_int, [vp, i32, vp, vp]),
+        "aap_ens_info": (C.c_int, [vp, vp, vp]),
+        "aap_ens_destroy": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -185,3 +211,82 @@ def aap_get_timing(h):
 
 def aap_abi_version() -> int:
     return int(load().aap_abi_version())
+
+
+def aap_measure(h, nsteps: int) -> None:
+    _check(load().aap_measure(h, int(nsteps)))
+
+
+def aap_get_results(h) -> aap_results:
+    r = aap_results()
+    _check(load().aap_get_results(h, C.byref(r)))
+    return r
+
+
+def aap_clear_results(h) -> None:
+    _check(load().aap_clear_results(h))
+
+
+def aap_coarse_grain(h, nbx: int, nby: int, dev_out_ptr: int) -> None:
+    """Fields into a caller-owned device buffer of 3*nbx*nby floats (a pointer,
+    e.g. torch_tensor.data_ptr())."""
+    _check(load().aap_coarse_grain(h, int(nbx), int(nby), C.c_void_p(int(dev_out_ptr))))
+
+
+def aap_ens_create(params, stream: int | None = None) -> C.c_void_p:
+    arr = (aap_params * len(params))(*params)
+    e = C.c_void_p()
+    _check(load().aap_ens_create(arr, len(params), C.c_void_p(stream or 0), C.byref(e)))
+    return e
+
+
+def aap_ens_step(e, nsteps: int) -> None:
+    _check(load().aap_ens_step(e, int(nsteps)))
+
+
+def aap_ens_measure(e, nsteps: int) -> None:
+    _check(load().aap_ens_measure(e, int(nsteps)))
+
+
+def aap_ens_info(e):
+    cnt = C.c_int32()
+    step = C.c_int64()
+    _check(load().aap_ens_info(e, C.byref(cnt), C.byref(step)))
+    return cnt.value, step.value
+
+
+def aap_ens_phi_mean(e) -> np.ndarray:
+    cnt, _ = aap_ens_info(e)
+    out = np.zeros(cnt, np.float64)
+    _check(load().aap_ens_phi_mean(e, _p(out)))
+    return out
+
+
+def aap_ens_results(e, r: int) -> aap_results:
+    res = aap_results()
+    _check(load().aap_ens_results(e, int(r), C.byref(res)))
+    return res
+
+
+def aap_ens_get_state(e, r: int, n: int):
+    x = np.zeros(n, np.float64); y = np.zeros(n, np.float64); th = np.zeros(n, np.float32)
+    _check(load().aap_ens_get_state(e, int(r), _p(x), _p(y), _p(th), int(n)))
+    return x, y, th
+
+
+def aap_ens_get_layout(e, r: int) -> aap_layout:
+    lay = aap_layout()
+    _check(load().aap_ens_get_layout(e, int(r), C.byref(lay)))
+    return lay
+
+
+def aap_ens_autotune(e, trial_steps: int):
+    """Returns (chosen policy index, ms per step of every policy tried)."""
+    pol = C.c_int32()
+    ms = np.zeros(8, np.float64)
+    _check(load().aap_ens_autotune(e, int(trial_steps), C.byref(pol), _p(ms)))
+    return pol.value, ms
+
+
+def aap_ens_destroy(e) -> None:
+    _check(load().aap_ens_destroy(e))

@@ -3,6 +3,7 @@
 // Host side of one simulated system: parameter checks, geometry and memory
 // layout, device allocations, the step loop (optionally replayed from a
 // captured CUDA graph), and the transfers in and out of host memory.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -85,6 +86,13 @@ struct aap_handle {
     cudaEvent_t err_event = nullptr;
     bool err_pending = false;
     int relayouts = 0;
+    // ensemble membership: steps are launched by the ensemble for all members
+    bool member = false;
+    int nom_tw = 0, nom_th = 0;     // nominal tile shape actually used
+    // coarse-graining accumulator (3 * bins 64-bit sums)
+    unsigned long long *d_cg = nullptr;
+    long long cg_bins = 0;
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
 };
 
 namespace {
@@ -109,6 +117,8 @@ void free_all(aap_handle *h)
 {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     h->events.clear();
     if (h->err_event) cudaEventDestroy(h->err_event);
@@ -210,7 +220,7 @@ int set_capacity(aap_handle *h, double factor)
     if ((long long)own + halo + L.spill_list_cap > 65472)
         return fail(AAP_EINVAL, "tile capacity too large (reduce tile size or capacity)");
     L.scratch_cap = aapk::round_up(own + halo + L.spill_list_cap, 64);
-    L.threads = p.threads ? p.threads : 256;
+    L.threads = p.threads ? p.threads : 512;
     L.model = p.model;
     L.stage_cap = scap;
     L.nce_max = nce;
@@ -237,13 +247,16 @@ int build_layout(aap_handle *h)
     S.ncx = h->ncx;
     S.ncy = h->ncy;
     const int nsm = sm_count();
-    int tw = p.tile_w ? p.tile_w : 32, th = p.tile_h ? p.tile_h : 16;
-    if (!p.tile_w && !p.tile_h) {
+    int tw = p.tile_w ? p.tile_w : (h->nom_tw ? h->nom_tw : 32);
+    int th = p.tile_h ? p.tile_h : (h->nom_th ? h->nom_th : 16);
+    if (!p.tile_w && !p.tile_h && !h->member) {
         // small systems: shrink tiles until there are a few per SM
         while ((long long)ceil_div(S.ncx, tw) * ceil_div(S.ncy, th) < 2ll * nsm && (tw > 8 || th > 8)) {
             if (tw >= th && tw > 8) tw /= 2; else if (th > 8) th /= 2; else break;
         }
     }
+    h->nom_tw = tw;
+    h->nom_th = th;
     S.ntx = ceil_div(S.ncx, std::min(tw, S.ncx));
     S.nty = ceil_div(S.ncy, std::min(th, S.ncy));
     S.twmax = ceil_div(S.ncx, S.ntx);
@@ -311,8 +324,10 @@ int alloc_regions(aap_handle *h)
         if ((rc = dev_alloc(h, &S.spill_rec[b], (size_t)S.spill_cap * sizeof(int4)))) return rc;
         if ((rc = dev_alloc(h, &S.spill_key[b], (size_t)S.spill_cap * sizeof(int)))) return rc;
     }
-    if ((rc = dev_alloc(h, &h->d_scratch, h->L.scratch_per_block * h->L.grid_step))) return rc;
-    h->L.scratch = h->d_scratch;
+    if (!h->member) {
+        if ((rc = dev_alloc(h, &h->d_scratch, h->L.scratch_per_block * h->L.grid_step))) return rc;
+        h->L.scratch = h->d_scratch;
+    }
     return AAP_OK;
 }
 
@@ -328,8 +343,13 @@ int free_regions(aap_handle *h)
         S.spill_rec[b] = nullptr;
         S.spill_key[b] = nullptr;
     }
+    if (h->member) return AAP_OK;
     rc = dev_free(h, h->d_scratch, h->L.scratch_per_block * h->L.grid_step);
     h->d_scratch = nullptr;
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
     return rc;
 }
 
@@ -355,10 +375,13 @@ int alloc_all(aap_handle *h)
     if ((rc = dev_alloc(h, &S.spill_cnt, 2 * sizeof(int)))) return rc;
     if ((rc = dev_alloc(h, &S.acc, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long)))) return rc;
     if ((rc = dev_alloc(h, &S.last, 4 * sizeof(double)))) return rc;
+    if ((rc = dev_alloc(h, &S.stats, 16 * sizeof(double)))) return rc;
     if ((rc = dev_alloc(h, &S.err, sizeof(int)))) return rc;
-    if ((rc = dev_alloc(h, &h->d_sys, sizeof(Sys)))) return rc;
-    if ((rc = dev_alloc(h, &h->d_tile_base, 2 * sizeof(int)))) return rc;
-    if ((rc = dev_alloc(h, &h->d_ctl, sizeof(Ctl)))) return rc;
+    if (!h->member) {
+        if ((rc = dev_alloc(h, &h->d_sys, sizeof(Sys)))) return rc;
+        if ((rc = dev_alloc(h, &h->d_tile_base, 2 * sizeof(int)))) return rc;
+        if ((rc = dev_alloc(h, &h->d_ctl, sizeof(Ctl)))) return rc;
+    }
     if ((rc = dev_alloc(h, &h->d_x0tab, (size_t)(S.ntx + 1) * sizeof(int)))) return rc;
     if ((rc = dev_alloc(h, &h->d_y0tab, (size_t)(S.nty + 1) * sizeof(int)))) return rc;
     {
@@ -376,9 +399,13 @@ int alloc_all(aap_handle *h)
     AAP_CK(cudaEventCreateWithFlags(&h->err_event, cudaEventDisableTiming));
     if ((rc = clear_buffers(h))) return rc;
     AAP_CK(cudaMemsetAsync(S.last, 0, 4 * sizeof(double), h->stream));
-    AAP_CK(cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), h->stream));
-    int tb[2] = {0, S.ntiles};
-    AAP_CK(cudaMemcpyAsync(h->d_tile_base, tb, sizeof(tb), cudaMemcpyHostToDevice, h->stream));
+    AAP_CK(cudaMemsetAsync(S.stats, 0, 16 * sizeof(double), h->stream));
+    S.meas_until = 0;
+    if (!h->member) {
+        AAP_CK(cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), h->stream));
+        int tb[2] = {0, S.ntiles};
+        AAP_CK(cudaMemcpyAsync(h->d_tile_base, tb, sizeof(tb), cudaMemcpyHostToDevice, h->stream));
+    }
     AAP_CK(cudaStreamSynchronize(h->stream));
     LaunchCfg &L = h->L;
     L.sys = h->d_sys;
@@ -424,23 +451,67 @@ int resolve_timing(aap_handle *h)
     return AAP_OK;
 }
 
+constexpr int kGraphSteps = 32;
+
+// Capture kGraphSteps steps of L into an executable graph (on a private
+// stream, so any caller stream works, the legacy default one included).
+int capture_steps(const LaunchCfg &L, cudaStream_t &cap, cudaGraphExec_t &exec)
+{
+    if (!cap) AAP_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    AAP_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) e = aapk::launch_step(L, cap);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(AAP_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(AAP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return AAP_OK;
+}
+
+// nsteps steps of L on stream st: whole chunks replay the captured graph (the
+// step index and buffer parity live on the device, so one graph serves every
+// chunk), the rest launch directly.
+int launch_steps(const LaunchCfg &L, cudaStream_t st, long long nsteps, cudaStream_t &cap,
+                 cudaGraphExec_t &exec)
+{
+    long long done = 0;
+    if (nsteps >= kGraphSteps) {
+        if (!exec) {
+            int rc = capture_steps(L, cap, exec);
+            if (rc) return rc;
+        }
+        for (; done + kGraphSteps <= nsteps; done += kGraphSteps) AAP_CK(cudaGraphLaunch(exec, st));
+    }
+    for (; done < nsteps; ++done) AAP_CK(aapk::launch_step(L, st));
+    return AAP_OK;
+}
+
 int run_steps(aap_handle *h, long long nsteps)
 {
+    if (!h->timing) {
+        int rc = launch_steps(h->L, h->stream, nsteps, h->cap_stream, h->gexec);
+        if (rc) return rc;
+        h->step += nsteps;
+        return AAP_OK;
+    }
     for (long long i = 0; i < nsteps; ++i) {
         cudaEvent_t *ev = nullptr;
-        if (h->timing) {
-            if (h->ev_used + 3 > 3072) {
-                int rc = resolve_timing(h);
-                if (rc) return rc;
-            }
-            while (h->events.size() < h->ev_used + 3) {
-                cudaEvent_t e;
-                AAP_CK(cudaEventCreate(&e));
-                h->events.push_back(e);
-            }
-            ev = &h->events[h->ev_used];
-            h->ev_used += 3;
+        if (h->ev_used + 3 > 3072) {
+            int rc = resolve_timing(h);
+            if (rc) return rc;
         }
+        while (h->events.size() < h->ev_used + 3) {
+            cudaEvent_t e;
+            AAP_CK(cudaEventCreate(&e));
+            h->events.push_back(e);
+        }
+        ev = &h->events[h->ev_used];
+        h->ev_used += 3;
         AAP_CK(aapk::launch_step(h->L, h->stream, ev));
     }
     h->step += nsteps;
@@ -525,6 +596,211 @@ int poll_capacity(aap_handle *h)
     }
     if ((err & aapk::ERR_SPILL) && h->p.capacity == 0) return relayout(h, h->factor * 1.5);
     return AAP_OK;
+}
+
+
+// Start a measurement window of nsteps steps at the current step: the
+// current state's p and q seed last[0..1] (state t0 is the first sample).
+int begin_measure(aap_handle *h, long long nsteps)
+{
+    aap_obs ob;
+    const Sys &S = h->hs;
+    AAP_CK(cudaMemsetAsync(h->d_obs, 0, 8 * sizeof(unsigned long long), h->stream));
+    AAP_CK(aapk::launch_observe(S, (int)(h->step & 1), h->d_obs, h->stream));
+    unsigned long long o[8];
+    AAP_CK(cudaMemcpyAsync(o, h->d_obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    const double n = (double)h->p.n;
+    const double c1 = (double)(long long)o[0] / aapk::kFix, s1 = (double)(long long)o[1] / aapk::kFix;
+    const double c2 = (double)(long long)o[2] / aapk::kFix, s2 = (double)(long long)o[3] / aapk::kFix;
+    double last[2] = {n > 0 ? std::sqrt(c1 * c1 + s1 * s1) / n : 0.0, n > 0 ? std::sqrt(c2 * c2 + s2 * s2) / n : 0.0};
+    (void)ob;
+    AAP_CK(cudaMemcpyAsync(h->hs.last, last, sizeof(last), cudaMemcpyHostToDevice, h->stream));
+    h->hs.meas_until = h->step + nsteps;
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    return push_sys(h);
+}
+
+int read_results(aap_handle *h, aap_results *out)
+{
+    double st[16];
+    AAP_CK(cudaMemcpyAsync(st, h->hs.stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    const double c = st[12];
+    out->samples = (int64_t)c;
+    for (int k = 0; k < 4; ++k) {
+        out->p[k] = c > 0 ? st[k] / c : NAN;
+        out->q[k] = c > 0 ? st[4 + k] / c : NAN;
+        out->nbar[k] = c > 0 ? st[8 + k] / c : NAN;
+    }
+    out->binder = (c > 0 && out->p[1] > 0) ? 1.0 - out->p[3] / (3.0 * out->p[1] * out->p[1]) : NAN;
+    return AAP_OK;
+}
+
+
+// ------------------------------------------------------------ ensembles --
+// Candidate launch policies of the ensemble autotuner: threads per block and
+// the nominal tile shape of every replica (clipped to the replica's box).
+struct EnsPolicy {
+    int threads, tw, th;
+};
+constexpr EnsPolicy kPolicies[8] = {{512, 32, 16}, {256, 32, 16}, {512, 16, 16}, {256, 16, 16},
+                                    {512, 32, 32}, {256, 16, 8},  {512, 64, 16}, {512, 16, 8}};
+constexpr int kNumPolicies = 8;
+
+}  // namespace
+
+struct aap_ens {
+    std::vector<aap_params> params;
+    std::vector<aap_handle *> m;
+    cudaStream_t stream = nullptr;
+    Sys *d_sys = nullptr;
+    int *d_tile_base = nullptr;
+    Ctl *d_ctl = nullptr;
+    unsigned char *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    LaunchCfg L{};
+    long long step = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int policy = 0;
+    int *pinned_err = nullptr;
+    cudaEvent_t err_event = nullptr;
+    bool err_pending = false;
+};
+
+namespace {
+
+void ens_free(aap_ens *e)
+{
+    for (aap_handle *h : e->m) {
+        free_all(h);
+        delete h;
+    }
+    e->m.clear();
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    e->exec = nullptr;
+    if (e->d_sys) cudaFree(e->d_sys);
+    if (e->d_tile_base) cudaFree(e->d_tile_base);
+    if (e->d_ctl) cudaFree(e->d_ctl);
+    if (e->d_scratch) cudaFree(e->d_scratch);
+    e->d_sys = nullptr;
+    e->d_tile_base = nullptr;
+    e->d_ctl = nullptr;
+    e->d_scratch = nullptr;
+    e->scratch_bytes = 0;
+}
+
+// Combine the members' launch needs into the ensemble's launch: the largest
+// staging capacities, a shared scratch, one grid over all tiles.
+int ens_combine(aap_ens *e)
+{
+    LaunchCfg &L = e->L;
+    const EnsPolicy &pol = kPolicies[e->policy];
+    L.sys = e->d_sys;
+    L.nsys = (int)e->m.size();
+    L.model = e->params[0].model;
+    L.tile_base = e->d_tile_base;
+    L.ctl = e->d_ctl;
+    L.threads = e->params[0].threads ? e->params[0].threads : pol.threads;
+    L.stage_cap = 64;
+    L.nce_max = 9;
+    L.scratch_cap = 64;
+    L.spill_list_cap = 16;
+    long long total = 0;
+    std::vector<int> tb(e->m.size() + 1, 0);
+    for (size_t r = 0; r < e->m.size(); ++r) {
+        const aap_handle *h = e->m[r];
+        L.stage_cap = std::max(L.stage_cap, h->L.stage_cap);
+        L.nce_max = std::max(L.nce_max, h->L.nce_max);
+        L.scratch_cap = std::max(L.scratch_cap, h->L.scratch_cap);
+        L.spill_list_cap = std::max(L.spill_list_cap, h->L.spill_list_cap);
+        total += h->hs.ntiles;
+        tb[r + 1] = (int)total;
+    }
+    if (total >= (1ll << 30)) return fail(AAP_EINVAL, "too many tiles in the ensemble");
+    AAP_CK(cudaMemcpy(e->d_tile_base, tb.data(), tb.size() * sizeof(int), cudaMemcpyHostToDevice));
+    const size_t smem = aapk::step_smem_bytes(L.stage_cap, L.nce_max);
+    int bps = 0;
+    AAP_CK(aapk::configure_step_kernel(L.model, L.threads, smem, &bps));
+    if (bps < 1) return fail(AAP_EINVAL, "step kernel does not fit on an SM for this ensemble");
+    const int nsm = sm_count();
+    L.grid_step = (int)std::max<long long>(1, std::min<long long>(total, (long long)bps * nsm));
+    L.grid_finish = (int)std::max<long long>(1, std::min<long long>(256, (total * aapk::kCntStride + 255) / 256));
+    L.scratch_per_block = aapk::stage_bytes(L.scratch_cap) + aapk::spill_list_bytes(L.spill_list_cap);
+    L.scratch_per_block = (L.scratch_per_block + 255) / 256 * 256;
+    const size_t need = L.scratch_per_block * L.grid_step;
+    if (need > e->scratch_bytes) {
+        if (e->d_scratch) cudaFree(e->d_scratch);
+        e->d_scratch = nullptr;
+        e->scratch_bytes = 0;
+        if (cudaMalloc(&e->d_scratch, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(AAP_ENOMEM, "ensemble scratch allocation failed");
+        }
+        e->scratch_bytes = need;
+    }
+    L.scratch = e->d_scratch;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    e->exec = nullptr;
+    return AAP_OK;
+}
+
+// Create every replica with policy `pol`, in its Philox initial state.
+int ens_build(aap_ens *e, int pol)
+{
+    e->policy = pol;
+    const int count = (int)e->params.size();
+    if (cudaMalloc(&e->d_sys, (size_t)count * sizeof(Sys)) != cudaSuccess ||
+        cudaMalloc(&e->d_tile_base, (size_t)(count + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&e->d_ctl, sizeof(Ctl)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AAP_ENOMEM, "ensemble descriptor allocation failed");
+    }
+    AAP_CK(cudaMemset(e->d_ctl, 0, sizeof(Ctl)));
+    for (int r = 0; r < count; ++r) {
+        aap_handle *h = new aap_handle();
+        e->m.push_back(h);
+        h->member = true;
+        h->p = e->params[r];
+        h->stream = e->stream;
+        h->nom_tw = kPolicies[pol].tw;
+        h->nom_th = kPolicies[pol].th;
+        if (!h->p.threads) h->p.threads = kPolicies[pol].threads;
+        h->d_sys = e->d_sys + r;
+        h->d_ctl = e->d_ctl;
+        int rc;
+        if ((rc = build_layout(h)) || (rc = alloc_all(h)) || (rc = reinsert(h, h->factor, 1)) ||
+            (rc = read_errors(h))) {
+            g_err = "replica " + std::to_string(r) + ": " + g_err;
+            return rc;
+        }
+    }
+    e->step = 0;
+    return ens_combine(e);
+}
+
+int ens_poll(aap_ens *e)
+{
+    if (!e->err_pending) return AAP_OK;
+    const cudaError_t q = cudaEventQuery(e->err_event);
+    if (q == cudaErrorNotReady) return AAP_OK;
+    if (q != cudaSuccess) return fail(AAP_ECUDA, std::string("error event: ") + cudaGetErrorString(q));
+    e->err_pending = false;
+    bool regrow = false;
+    for (size_t r = 0; r < e->m.size(); ++r) {
+        aap_handle *h = e->m[r];
+        const int err = e->pinned_err[r];
+        if (err & aapk::ERR_SPILL) h->flags |= AAP_FLAG_SPILLED;
+        if (err & (aapk::ERR_LOST | aapk::ERR_STAGE))
+            return fail(AAP_EOVERFLOW, "replica " + std::to_string(r) + " lost particles");
+        if ((err & aapk::ERR_SPILL) && h->p.capacity == 0) {
+            int rc = relayout(h, h->factor * 1.5);
+            if (rc) return rc;
+            regrow = true;
+        }
+    }
+    return regrow ? ens_combine(e) : AAP_OK;
 }
 
 }  // namespace
@@ -637,7 +913,7 @@ int aap_observe(aap_handle *h, aap_obs *out)
     const double c2 = (double)(long long)o[2] / aapk::kFix, s2 = (double)(long long)o[3] / aapk::kFix;
     out->phi = n > 0 ? std::sqrt(c1 * c1 + s1 * s1) / n : 0.0;
     out->q = n > 0 ? std::sqrt(c2 * c2 + s2 * s2) / n : 0.0;
-    out->mean_neighbours = h->step > 0 ? last[1] : NAN;
+    out->mean_neighbours = h->step > 0 ? last[2] : NAN;
     out->step = h->step;
     out->flags = h->flags;
     out->reserved = 0;
@@ -747,6 +1023,226 @@ int aap_step_neighbours(aap_handle *h, int32_t *nbr_out, int64_t n)
         AAP_CK(cudaMemcpyAsync(nbr_out, h->d_nbr, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     AAP_CK(cudaStreamSynchronize(h->stream));
     return read_errors(h);
+}
+
+
+int aap_measure(aap_handle *h, int64_t nsteps)
+{
+    if (!h) return fail(AAP_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
+    if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
+    int rc = poll_capacity(h);
+    if (rc) return rc;
+    if ((rc = begin_measure(h, nsteps))) return rc;
+    return aap_step(h, nsteps);
+}
+
+int aap_get_results(aap_handle *h, aap_results *out)
+{
+    if (!h || !out) return fail(AAP_EINVAL, "NULL argument");
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    int rc = read_errors(h);
+    if (rc) return rc;
+    return read_results(h, out);
+}
+
+int aap_clear_results(aap_handle *h)
+{
+    if (!h) return fail(AAP_EINVAL, "handle is NULL");
+    AAP_CK(cudaMemsetAsync(h->hs.stats, 0, 16 * sizeof(double), h->stream));
+    return AAP_OK;
+}
+
+int aap_coarse_grain(aap_handle *h, int32_t nbx, int32_t nby, float *dev_out)
+{
+    if (!h || !dev_out) return fail(AAP_EINVAL, "NULL argument");
+    if (nbx < 1 || nby < 1 || (long long)nbx * nby > (1ll << 26))
+        return fail(AAP_EINVAL, "nbx, nby must be >= 1 with nbx * nby <= 2^26");
+    if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
+    const long long bins = (long long)nbx * nby;
+    if (h->cg_bins < bins) {
+        int rc;
+        if (h->d_cg && (rc = dev_free(h, h->d_cg, (size_t)h->cg_bins * 3 * sizeof(unsigned long long)))) return rc;
+        h->d_cg = nullptr;
+        if ((rc = dev_alloc(h, &h->d_cg, (size_t)bins * 3 * sizeof(unsigned long long)))) return rc;
+        h->cg_bins = bins;
+    }
+    AAP_CK(aapk::launch_coarse(h->hs, (int)(h->step & 1), nbx, nby, h->d_cg, dev_out, h->stream));
+    return AAP_OK;
+}
+
+
+int aap_ens_create(const aap_params *params, int32_t count, void *stream, aap_ens **out)
+{
+    g_err.clear();
+    if (!out || !params) return fail(AAP_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (count < 1) return fail(AAP_EINVAL, "count must be >= 1");
+    for (int r = 0; r < count; ++r) {
+        int rc = check_params(&params[r]);
+        if (rc) {
+            g_err = "replica " + std::to_string(r) + ": " + g_err;
+            return rc;
+        }
+        if (params[r].model != params[0].model) return fail(AAP_EINVAL, "all replicas must use the same model");
+        if (params[r].threads != params[0].threads) return fail(AAP_EINVAL, "all replicas must use the same threads");
+    }
+    aap_ens *e = new aap_ens();
+    e->params.assign(params, params + count);
+    e->stream = static_cast<cudaStream_t>(stream);
+    int rc = ens_build(e, 0);
+    if (rc == AAP_OK) {
+        if (cudaMallocHost(&e->pinned_err, (size_t)count * sizeof(int)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e->err_event, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(AAP_ECUDA, "ensemble host buffers");
+        }
+    }
+    if (rc) {
+        ens_free(e);
+        if (e->pinned_err) cudaFreeHost(e->pinned_err);
+        delete e;
+        return rc;
+    }
+    *out = e;
+    return AAP_OK;
+}
+
+int aap_ens_destroy(aap_ens *e)
+{
+    if (!e) return AAP_OK;
+    cudaStreamSynchronize(e->stream);
+    ens_free(e);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    if (e->err_event) cudaEventDestroy(e->err_event);
+    if (e->pinned_err) cudaFreeHost(e->pinned_err);
+    delete e;
+    return AAP_OK;
+}
+
+int aap_ens_step(aap_ens *e, int64_t nsteps)
+{
+    if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
+    if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
+    int rc = ens_poll(e);
+    if (rc) return rc;
+    if ((rc = launch_steps(e->L, e->stream, nsteps, e->cap, e->exec))) return rc;
+    e->step += nsteps;
+    for (aap_handle *h : e->m) h->step += nsteps;
+    for (size_t r = 0; r < e->m.size(); ++r)
+        AAP_CK(cudaMemcpyAsync(e->pinned_err + r, e->m[r]->hs.err, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    AAP_CK(cudaEventRecord(e->err_event, e->stream));
+    e->err_pending = true;
+    return AAP_OK;
+}
+
+int aap_ens_measure(aap_ens *e, int64_t nsteps)
+{
+    if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
+    if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
+    int rc = ens_poll(e);
+    if (rc) return rc;
+    for (aap_handle *h : e->m)
+        if ((rc = begin_measure(h, nsteps))) return rc;
+    return aap_ens_step(e, nsteps);
+}
+
+int aap_ens_phi_mean(aap_ens *e, double *out)
+{
+    if (!e || !out) return fail(AAP_EINVAL, "NULL argument");
+    AAP_CK(cudaStreamSynchronize(e->stream));
+    for (size_t r = 0; r < e->m.size(); ++r) {
+        aap_results res;
+        int rc = read_errors(e->m[r]);
+        if (rc) return rc;
+        if ((rc = read_results(e->m[r], &res))) return rc;
+        out[r] = res.p[0];
+    }
+    return AAP_OK;
+}
+
+int aap_ens_results(aap_ens *e, int32_t r, aap_results *out)
+{
+    if (!e || !out) return fail(AAP_EINVAL, "NULL argument");
+    if (r < 0 || r >= (int)e->m.size()) return fail(AAP_EINVAL, "replica index out of range");
+    return aap_get_results(e->m[r], out);
+}
+
+int aap_ens_get_state(aap_ens *e, int32_t r, double *x, double *y, float *theta, int64_t n)
+{
+    if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
+    if (r < 0 || r >= (int)e->m.size()) return fail(AAP_EINVAL, "replica index out of range");
+    AAP_CK(cudaStreamSynchronize(e->stream));
+    return aap_get_state(e->m[r], x, y, theta, n);
+}
+
+int aap_ens_get_layout(aap_ens *e, int32_t r, aap_layout *out)
+{
+    if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
+    if (r < 0 || r >= (int)e->m.size()) return fail(AAP_EINVAL, "replica index out of range");
+    int rc = aap_get_layout(e->m[r], out);
+    if (rc == AAP_OK) {
+        out->threads = e->L.threads;
+        out->stage_cap = e->L.stage_cap;
+        out->tile_w = e->m[r]->nom_tw;
+        out->tile_h = e->m[r]->nom_th;
+    }
+    return rc;
+}
+
+int aap_ens_info(aap_ens *e, int32_t *count, int64_t *step)
+{
+    if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
+    if (count) *count = (int32_t)e->m.size();
+    if (step) *step = e->step;
+    return AAP_OK;
+}
+
+int aap_ens_autotune(aap_ens *e, int32_t trial_steps, int32_t *policy_out, double *ms_out)
+{
+    if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
+    if (e->step != 0) return fail(AAP_EINVAL, "autotune is only allowed before the first step");
+    if (trial_steps < 1) return fail(AAP_EINVAL, "trial_steps must be >= 1");
+    double ms[kNumPolicies];
+    for (int k = 0; k < kNumPolicies; ++k) ms[k] = 0.0;
+    int best = -1;
+    cudaEvent_t t0, t1;
+    AAP_CK(cudaEventCreate(&t0));
+    AAP_CK(cudaEventCreate(&t1));
+    int rc = AAP_OK;
+    for (int k = 0; k < kNumPolicies && rc == AAP_OK; ++k) {
+        AAP_CK(cudaStreamSynchronize(e->stream));
+        ens_free(e);
+        if ((rc = ens_build(e, k)) != AAP_OK) {
+            if (rc == AAP_EINVAL) {     // this shape does not fit: skip it
+                g_err.clear();
+                ens_free(e);
+                rc = AAP_OK;
+            }
+            continue;
+        }
+        // warm up (captures the graph), then time
+        if ((rc = launch_steps(e->L, e->stream, 2 + 32, e->cap, e->exec))) break;
+        AAP_CK(cudaEventRecord(t0, e->stream));
+        if ((rc = launch_steps(e->L, e->stream, trial_steps, e->cap, e->exec))) break;
+        AAP_CK(cudaEventRecord(t1, e->stream));
+        AAP_CK(cudaEventSynchronize(t1));
+        float t = 0.f;
+        AAP_CK(cudaEventElapsedTime(&t, t0, t1));
+        ms[k] = t / trial_steps;
+        if (best < 0 || ms[k] < ms[best]) best = k;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    AAP_CK(cudaStreamSynchronize(e->stream));
+    ens_free(e);
+    if (rc != AAP_OK) return rc;
+    if (best < 0) return fail(AAP_EINVAL, "no launch policy fits this ensemble");
+    if ((rc = ens_build(e, best))) return rc;
+    if (policy_out) *policy_out = best;
+    if (ms_out)
+        for (int k = 0; k < kNumPolicies; ++k) ms_out[k] = ms[k];
+    return AAP_OK;
 }
 
 int aap_set_timing(aap_handle *h, int32_t enable)

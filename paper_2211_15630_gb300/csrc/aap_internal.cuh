@@ -26,7 +26,7 @@ namespace aapk {
 constexpr int kRegions = 9;
 constexpr int kCntStride = 16;      // counters per tile (9 used): one 64-byte line
 constexpr int kAccSlots = 64;       // spread of the per-step integer accumulators
-constexpr int kAccWords = 4;        // sum cos, sum sin, sum |Omega|, unused
+constexpr int kAccWords = 8;        // sum cos, sin, |Omega|, cos 2theta, sin 2theta; 3 unused
 constexpr double kFix = 4294967296.0;     // 2^32: scale of the observation sums
 constexpr float kFixStepF = 1073741824.0f;  // 2^30: scale of the per-step sums
 constexpr double kFixStep = 1073741824.0;
@@ -76,7 +76,10 @@ struct Sys {
     double *trace;              // p(t) for t = trace_base .. trace_base + trace_cap - 1
     double *trace_nbar;         // mean |Omega| of state t
     long long trace_base, trace_cap;
-    double *last;               // [4]: p, mean |Omega| of the last measured state, step, unused
+    double *last;               // [4]: p, q of the current state; mean |Omega| of the
+                                //      state before it; step
+    double *stats;              // [16]: sums of p^k, q^k, nbar^k (k = 1..4), count
+    long long meas_until;       // steps t < meas_until add state t to stats
     int *nbr_out;               // optional |Omega_i| by particle id
     int *err;
 };

@@ -16,6 +16,8 @@
 //              in the block's slice of global scratch by the same code.
 //   k_finish   turns the step's integer sums into p(t), clears the counters
 //              of the buffer just consumed and advances the step counter.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "aap_internal.cuh"
@@ -144,7 +146,7 @@ struct TileCtx {
     int segpre[kSegs + 1];
     int warp_tot[32];
     Seg seg[kSegs];
-    long long red[3][32];
+    long long red[5][32];
 };
 
 // Resolve the halo column (side -1: left, +1: right) of tile t into a source
@@ -439,7 +441,7 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
     const int n_own = T.n_own;
     const float r2 = S.r2;
     const int TWs = tw << S.sx, THs = th << S.sy;
-    long long acc_c = 0, acc_s = 0, acc_n = 0;
+    long long acc_c = 0, acc_s = 0, acc_n = 0, acc_c2 = 0, acc_s2 = 0;
     for (int base = 0; base < n_own; base += NT) {
         const int o = base + tid;
         const bool act = o < n_own;
@@ -513,6 +515,8 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             rec = make_int4(Xn, Yn, __float_as_int(thn), (int)id);
             acc_c += __float2int_rn(cn * kFixStepF);
             acc_s += __float2int_rn(sn * kFixStepF);
+            acc_c2 += __float2int_rn(fmaf(cn, cn, -sn * sn) * kFixStepF);
+            acc_s2 += __float2int_rn(2.0f * cn * sn * kFixStepF);
             acc_n += nb;
             if (S.nbr_out && id < (unsigned long long)S.n) S.nbr_out[id] = nb;
         }
@@ -523,13 +527,17 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
     acc_c = warp_sum_ll(acc_c);
     acc_s = warp_sum_ll(acc_s);
     acc_n = warp_sum_ll(acc_n);
+    acc_c2 = warp_sum_ll(acc_c2);
+    acc_s2 = warp_sum_ll(acc_s2);
     if (lane == 0) {
         T.red[0][warp] = acc_c;
         T.red[1][warp] = acc_s;
         T.red[2][warp] = acc_n;
+        T.red[3][warp] = acc_c2;
+        T.red[4][warp] = acc_s2;
     }
     __syncthreads();
-    if (tid < 3) {
+    if (tid < 5) {
         long long v = 0;
         for (int w = 0; w < NT / 32; ++w) v += T.red[tid][w];
         unsigned long long *slot = S.acc + ((size_t)cur * kAccSlots + (T.tile & (kAccSlots - 1))) * kAccWords;
@@ -643,27 +651,42 @@ __global__ void k_finish(Sys *sys, int nsys, Ctl *ctl)
     for (int si = threadIdx.x; si < nsys; si += blockDim.x) {
         Sys &S = sys[si];
         unsigned long long *a = S.acc + (size_t)cur * kAccSlots * kAccWords;
-        long long sc = 0, ss = 0, sn = 0;
-        for (int k = 0; k < kAccSlots; ++k) {
-            sc += (long long)a[k * kAccWords + 0];
-            ss += (long long)a[k * kAccWords + 1];
-            sn += (long long)a[k * kAccWords + 2];
-            a[k * kAccWords + 0] = 0;
-            a[k * kAccWords + 1] = 0;
-            a[k * kAccWords + 2] = 0;
-        }
+        long long v[5] = {0, 0, 0, 0, 0};
+        for (int k = 0; k < kAccSlots; ++k)
+            for (int w = 0; w < 5; ++w) {
+                v[w] += (long long)a[k * kAccWords + w];
+                a[k * kAccWords + w] = 0;
+            }
         const double n = (double)S.n;
-        const double dc = (double)sc / kFixStep, ds = (double)ss / kFixStep;
+        const double dc = (double)v[0] / kFixStep, ds = (double)v[1] / kFixStep;
+        const double dc2 = (double)v[3] / kFixStep, ds2 = (double)v[4] / kFixStep;
         const double phi = n > 0 ? sqrt(dc * dc + ds * ds) / n : 0.0;
-        const double nbar = n > 0 ? (double)sn / n : 0.0;
+        const double q = n > 0 ? sqrt(dc2 * dc2 + ds2 * ds2) / n : 0.0;
+        const double nbar = n > 0 ? (double)v[2] / n : 0.0;
         if (S.trace) {
             const long long i1 = step + 1 - S.trace_base, i0 = step - S.trace_base;
             if (i1 >= 0 && i1 < S.trace_cap) S.trace[i1] = phi;
             if (i0 >= 0 && i0 < S.trace_cap) S.trace_nbar[i0] = nbar;
         }
+        if (step < S.meas_until) {
+            // on-the-fly measurement (Sec. 3.4): state t contributes p(t),
+            // q(t) and the mean neighbour number measured on it
+            const double p0 = S.last[0], q0 = S.last[1];
+            double pk = 1.0, qk = 1.0, nk = 1.0;
+            for (int k = 0; k < 4; ++k) {
+                pk *= p0;
+                qk *= q0;
+                nk *= nbar;
+                S.stats[k] += pk;
+                S.stats[4 + k] += qk;
+                S.stats[8 + k] += nk;
+            }
+            S.stats[12] += 1.0;
+        }
         S.last[0] = phi;
-        S.last[1] = nbar;
-        S.last[2] = (double)(step + 1);
+        S.last[1] = q;
+        S.last[2] = nbar;
+        S.last[3] = (double)(step + 1);
         S.spill_cnt[cur] = 0;
     }
     __syncthreads();
@@ -803,6 +826,47 @@ __global__ void k_observe(Sys S, int b, unsigned long long *out)
     }
 }
 
+// ------------------------------------------------------- coarse graining --
+// Bin the particles of buffer b into nbx x nby cells of the box: counts and
+// sums of cos theta, sin theta, in exact 64-bit integers (cos scaled by 2^32)
+// so that the fields are reproducible bit for bit.  acc: [3][nbx*nby].
+__global__ void k_coarse_accumulate(Sys S, int b, int nbx, int nby, unsigned long long *acc)
+{
+    const long long total = (long long)S.ntiles * S.tile_slots + S.spill_cap;
+    const long long nb = (long long)nbx * nby;
+    const double fx = (double)nbx / S.lx, fy = (double)nby / S.ly;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        int4 r;
+        int tile;
+        if (!fetch_record(S, b, g, r, tile)) continue;
+        const int tx = tile % S.ntx, ty = tile / S.ntx;
+        const double gx = ((double)((long long)tile_x0(S, tx) << S.sx) + (double)r.x) * (S.csx_d / (double)(1ll << S.sx));
+        const double gy = ((double)((long long)tile_y0(S, ty) << S.sy) + (double)r.y) * (S.csy_d / (double)(1ll << S.sy));
+        const int ix = min(max((int)(gx * fx), 0), nbx - 1);
+        const int iy = min(max((int)(gy * fy), 0), nby - 1);
+        const long long bin = (long long)iy * nbx + ix;
+        float sn, cs;
+        sincosf(__int_as_float(r.z), &sn, &cs);
+        atomicAdd(acc + bin, 1ull);
+        atomicAdd(acc + nb + bin, (unsigned long long)__float2ll_rn(cs * 4294967296.0f));
+        atomicAdd(acc + 2 * nb + bin, (unsigned long long)__float2ll_rn(sn * 4294967296.0f));
+    }
+}
+
+// Fields per unit area: density, polarisation x, polarisation y (planes of
+// nbx*nby floats, row-major with x fastest).
+__global__ void k_coarse_finish(const unsigned long long *acc, int nbx, int nby, double inv_area, float *out)
+{
+    const long long nb = (long long)nbx * nby;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        out[i] = (float)((double)acc[i] * inv_area);
+        out[nb + i] = (float)((double)(long long)acc[nb + i] / kFix * inv_area);
+        out[2 * nb + i] = (float)((double)(long long)acc[2 * nb + i] / kFix * inv_area);
+    }
+}
+
 // --------------------------------------------------------------- launchers --
 size_t step_smem_bytes(int stage_cap, int nce_max) { return stage_bytes(stage_cap) + table_bytes(nce_max); }
 
@@ -888,6 +952,19 @@ cudaError_t launch_gather(const Sys &S, int b, double *x, double *y, float *th, 
 cudaError_t launch_observe(const Sys &S, int b, unsigned long long *out, cudaStream_t st)
 {
     k_observe<<<1024, 256, 0, st>>>(S, b, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse(const Sys &S, int b, int nbx, int nby, unsigned long long *acc, float *out,
+                          cudaStream_t st)
+{
+    const long long nb = (long long)nbx * nby;
+    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)nb * 3 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_coarse_accumulate<<<1024, 256, 0, st>>>(S, b, nbx, nby, acc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const double inv_area = (double)nbx * nby / (S.lx * S.ly);
+    k_coarse_finish<<<(unsigned)std::min<long long>((nb + 255) / 256, 4096), 256, 0, st>>>(acc, nbx, nby, inv_area, out);
     return cudaGetLastError();
 }
 

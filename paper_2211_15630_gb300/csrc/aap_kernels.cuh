@@ -39,5 +39,9 @@ cudaError_t launch_insert(const Sys &S, int b, const double *x, const double *y,
 cudaError_t launch_gather(const Sys &S, int b, double *x, double *y, float *th, int *seen,
                           cudaStream_t st);
 cudaError_t launch_observe(const Sys &S, int b, unsigned long long *out, cudaStream_t st);
+// Coarse-grained fields of buffer b into out[3][nby][nbx] (device), using
+// acc[3 * nbx * nby] (device scratch) for the integer sums.
+cudaError_t launch_coarse(const Sys &S, int b, int nbx, int nby, unsigned long long *acc, float *out,
+                          cudaStream_t st);
 
 }  // namespace aapk

@@ -1,0 +1,180 @@
+"""Batched ensembles, on-the-fly measurements, coarse-graining and graph replay
+(CUDA path through the C ABI; needs a GB300)."""
+import numpy as np
+import pytest
+
+import paper_2211_15630_gb300 as A
+from paper_2211_15630_gb300 import workloads as W
+from tests.gpu_helpers import compare_one_step, params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2211_15630_gb300 import build
+
+    build.build()
+    return A.load()
+
+
+def _standalone_like(e, r, p):
+    lay = A.aap_ens_get_layout(e, r)
+    q = A.aap_params_default()
+    for f, _ in A.aap_params._fields_:
+        setattr(q, f, getattr(p, f))
+    q.tile_w, q.tile_h = lay.tile_w, lay.tile_h
+    return q
+
+
+def test_graph_replay_equals_single_steps(lib):
+    """aap_step(h, 100) replays a captured CUDA graph of 32 steps; the
+    trajectory is bit-identical to 100 single-step calls."""
+    p = params(n=30000, lx=120.0, ly=120.0, eta=0.45, seed=3)
+    h1, h2 = A.aap_create(p), A.aap_create(p)
+    try:
+        A.aap_step(h1, 100)
+        for _ in range(100):
+            A.aap_step(h2, 1)
+        for u, v in zip(A.aap_get_state(h1, p.n), A.aap_get_state(h2, p.n)):
+            assert np.array_equal(u, v)
+    finally:
+        A.aap_destroy(h1)
+        A.aap_destroy(h2)
+
+
+def test_ensemble_replicas_bitwise_equal_standalone(lib):
+    """Every replica of the batched launch follows the standalone trajectory
+    bit for bit (same parameters, same tile shape)."""
+    ps = W.ensemble_replicas(count=12, seed=7, nmin_log2=9, nmax_log2=14)
+    e = A.aap_ens_create(ps)
+    try:
+        A.aap_ens_step(e, 40)
+        for r in (0, 3, 7, 11):
+            q = _standalone_like(e, r, ps[r])
+            h = A.aap_create(q)
+            try:
+                A.aap_step(h, 40)
+                a = A.aap_get_state(h, q.n)
+                b = A.aap_ens_get_state(e, r, q.n)
+                for u, v in zip(a, b):
+                    assert np.array_equal(u, v), f"replica {r} differs"
+            finally:
+                A.aap_destroy(h)
+    finally:
+        A.aap_ens_destroy(e)
+
+
+def test_ensemble_replica_matches_oracle(lib, oracle):
+    """One replica's next step, taken inside the ensemble, against the oracle."""
+    ps = W.ensemble_replicas(count=6, seed=11, nmin_log2=10, nmax_log2=13)
+    e = A.aap_ens_create(ps)
+    try:
+        A.aap_ens_step(e, 5)
+        r = 2
+        p = ps[r]
+        x0, y0, t0 = A.aap_ens_get_state(e, r, p.n)
+        A.aap_ens_step(e, 1)
+        x1, y1, t1 = A.aap_ens_get_state(e, r, p.n)
+        m = oracle.Model(n=p.n, lx=p.lx, ly=p.ly, r=p.r, v=p.v, eta=p.eta, seed=p.seed)
+        xo, yo, to, nbo, smag, amb = oracle.step(m, x0, y0, t0.astype(np.float64), 5)
+        ok = (amb == 0) & (smag > 0.05)
+        dth = np.abs(np.mod(t1[ok] - to[ok] + np.pi, 2 * np.pi) - np.pi)
+        assert dth.max() < 1e-5
+    finally:
+        A.aap_ens_destroy(e)
+
+
+def test_ensemble_measure_and_autotune(lib):
+    """Autotune resets to the initial state with the fastest policy; the time
+    averaged p of a replica equals its standalone measurement bit for bit."""
+    ps = W.ensemble_replicas(count=10, seed=5, nmin_log2=10, nmax_log2=14)
+    e = A.aap_ens_create(ps)
+    try:
+        pol, ms = A.aap_ens_autotune(e, 5)
+        assert 0 <= pol < 8 and ms[pol] > 0 and ms[pol] == ms[ms > 0].min()
+        A.aap_ens_step(e, 20)
+        A.aap_ens_measure(e, 30)
+        phi = A.aap_ens_phi_mean(e)
+        assert ((phi > 0) & (phi <= 1)).all()
+        r = 4
+        q = _standalone_like(e, r, ps[r])
+        q.threads = A.ENS_POLICIES[pol][0]
+        h = A.aap_create(q)
+        try:
+            A.aap_step(h, 20)
+            A.aap_measure(h, 30)
+            res = A.aap_get_results(h)
+            assert res.samples == 30
+            assert res.p[0] == phi[r]
+            er = A.aap_ens_results(e, r)
+            assert er.samples == 30 and er.binder == res.binder
+        finally:
+            A.aap_destroy(h)
+    finally:
+        A.aap_ens_destroy(e)
+
+
+def test_measurement_window_matches_trace(lib):
+    """aap_measure(n) samples the states t0 .. t0+n-1 (Sec. 3.4): its <p> and
+    <p^2> equal the moments of the p(t) trace of an identical system."""
+    p = params(n=20000, lx=100.0, ly=100.0, eta=0.3, seed=9)
+    h1, h2 = A.aap_create(p), A.aap_create(p)
+    try:
+        A.aap_step(h1, 10)
+        A.aap_step(h2, 10)
+        A.aap_measure(h1, 25)
+        res = A.aap_get_results(h1)
+        tr = A.aap_phi_trace(h2, 25)[:25]
+        assert res.samples == 25
+        assert abs(res.p[0] - tr.mean()) < 1e-12
+        assert abs(res.p[1] - (tr**2).mean()) < 1e-12
+        assert abs(res.binder - (1 - (tr**4).mean() / (3 * (tr**2).mean() ** 2))) < 1e-9
+        assert 0 < res.nbar[0] < 50 and 0 <= res.q[0] <= 1
+    finally:
+        A.aap_destroy(h1)
+        A.aap_destroy(h2)
+
+
+def test_coarse_grain_conserves(lib, oracle):
+    """Binned density integrates to N exactly, binned polarisation to
+    sum e^{i theta}, so p follows from the fields (128 x 128 bins, 4 x 4 units)."""
+    torch = pytest.importorskip("torch")
+    p = W.surrogate_training(eta=0.4, seed=10000)
+    h = A.aap_create(p)
+    try:
+        A.aap_step(h, 10)
+        out = torch.zeros(3 * 128 * 128, dtype=torch.float32, device="cuda")
+        A.aap_coarse_grain(h, 128, 128, out.data_ptr())
+        A.aap_sync(h)
+        f = out.cpu().numpy().reshape(3, 128, 128).astype(np.float64)
+        area = (p.lx / 128) * (p.ly / 128)
+        assert abs(f[0].sum() * area - p.n) < 1e-3 * 1e-3 * p.n
+        assert np.allclose(f[0] * area, np.round(f[0] * area), atol=1e-3)
+        x, y, th = A.aap_get_state(h, p.n)
+        cs = np.cos(th.astype(np.float64)).sum()
+        sn = np.sin(th.astype(np.float64)).sum()
+        assert abs(f[1].sum() * area - cs) < 1e-3 * np.sqrt(p.n)
+        assert abs(f[2].sum() * area - sn) < 1e-3 * np.sqrt(p.n)
+        ix = np.minimum((x / (p.lx / 128)).astype(int), 127)
+        iy = np.minimum((y / (p.ly / 128)).astype(int), 127)
+        counts = np.zeros((128, 128))
+        np.add.at(counts, (iy, ix), 1.0)
+        assert np.array_equal(np.round(f[0] * area), counts)
+        phi_f = np.hypot(f[1].sum(), f[2].sum()) * area / p.n
+        assert abs(phi_f - oracle.polar(th.astype(np.float64))) < 1e-6
+    finally:
+        A.aap_destroy(h)
+
+
+def test_brownian_workload_one_step(lib, oracle):
+    """The Brownian workload (N = 2^20, 724 x 724, reflecting walls, dt = 0.01):
+    sampled one-step parity in the launch configuration of the benchmark."""
+    p = W.brownian_walls(seed=3)
+    h = A.aap_create(p)
+    try:
+        A.aap_step(h, 3)
+        idx = np.random.default_rng(2).choice(p.n, 3000, replace=False)
+        compare_one_step(oracle, p, h, idx=idx)
+    finally:
+        A.aap_destroy(h)
