@@ -30,6 +30,10 @@ EXPORTS = (
     "aap_measure", "aap_get_results", "aap_clear_results", "aap_coarse_grain",
     "aap_ens_create", "aap_ens_step", "aap_ens_measure", "aap_ens_phi_mean", "aap_ens_results",
     "aap_ens_get_state", "aap_ens_get_layout", "aap_ens_autotune", "aap_ens_info", "aap_ens_destroy",
+    "aap_sur_last_error", "aap_sur_params_default", "aap_sur_create", "aap_sur_destroy",
+    "aap_sur_param_count", "aap_sur_get_params", "aap_sur_set_params", "aap_sur_get_grads",
+    "aap_sur_predict", "aap_sur_train_step", "aap_conv3x3_forward", "aap_conv3x3_backward_data",
+    "aap_conv3x3_backward_weight",
 )
 
 
@@ -65,6 +69,13 @@ class aap_layout(C.Structure):
 class aap_results(C.Structure):
     _fields_ = [("samples", C.c_int64), ("p", C.c_double * 4), ("q", C.c_double * 4),
                 ("nbar", C.c_double * 4), ("binder", C.c_double)]
+
+
+class aap_sur_params(C.Structure):
+    _fields_ = [("nbx", C.c_int32), ("nby", C.c_int32), ("max_batch", C.c_int32),
+                ("reserved", C.c_int32), ("rho0", C.c_double), ("eta_center", C.c_double),
+                ("eta_scale", C.c_double), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64)]
 
 
 # launch policies tried by aap_ens_autotune: (threads, nominal tile w, h)
@@ -114,6 +125,20 @@ def load(path: str = LIB_PATH):
         "aap_ens_autotune": (C.c_int, [vp, i32, vp, vp]),
         "aap_ens_info": (C.c_int, [vp, vp, vp]),
         "aap_ens_destroy": (C.c_int, [vp]),
+        "aap_sur_last_error": (C.c_char_p, []),
+        "aap_sur_params_default": (None, [P(aap_sur_params)]),
+        "aap_sur_create": (C.c_int, [P(aap_sur_params), vp, P(vp)]),
+        "aap_sur_destroy": (C.c_int, [vp]),
+        "aap_sur_param_count": (C.c_int, [vp, vp]),
+        "aap_sur_get_params": (C.c_int, [vp, vp, i64]),
+        "aap_sur_set_params": (C.c_int, [vp, vp, i64]),
+        "aap_sur_get_grads": (C.c_int, [vp, vp, i64]),
+        "aap_sur_predict": (C.c_int, [vp, vp, vp, i32, i32, vp]),
+        "aap_sur_train_step": (C.c_int, [vp, vp, vp, vp, i32, vp]),
+        "aap_conv3x3_forward": (C.c_int, [vp, i32, i32, i32, i32, i32, vp, vp, i32, vp, vp]),
+        "aap_conv3x3_backward_data": (C.c_int, [vp, i32, i32, i32, i32, i32, vp, vp, vp, vp]),
+        "aap_conv3x3_backward_weight": (C.c_int, [vp, vp, i32, i32, i32, i32, i32, i32, vp, i64,
+                                                  vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -290,3 +315,86 @@ def aap_ens_autotune(e, trial_steps: int):
 
 def aap_ens_destroy(e) -> None:
     _check(load().aap_ens_destroy(e))
+
+
+# ---- surrogate (include/aap_surrogate.h); device arguments are raw pointers --
+
+def _scheck(rc: int):
+    if rc != AAP_OK:
+        raise AapError(rc, load().aap_sur_last_error().decode())
+
+
+def _vp(ptr):
+    return C.c_void_p(int(ptr)) if ptr else None
+
+
+def aap_sur_params_default(**kw) -> aap_sur_params:
+    p = aap_sur_params()
+    load().aap_sur_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def aap_sur_create(params: aap_sur_params, stream: int | None = None) -> C.c_void_p:
+    s = C.c_void_p()
+    _scheck(load().aap_sur_create(C.byref(params), C.c_void_p(stream or 0), C.byref(s)))
+    return s
+
+
+def aap_sur_destroy(s) -> None:
+    _scheck(load().aap_sur_destroy(s))
+
+
+def aap_sur_param_count(s) -> int:
+    n = C.c_int64()
+    _scheck(load().aap_sur_param_count(s, C.byref(n)))
+    return n.value
+
+
+def aap_sur_get_params(s) -> np.ndarray:
+    out = np.zeros(aap_sur_param_count(s), np.float32)
+    _scheck(load().aap_sur_get_params(s, _p(out), out.size))
+    return out
+
+
+def aap_sur_set_params(s, params) -> None:
+    a = np.ascontiguousarray(params, np.float32)
+    _scheck(load().aap_sur_set_params(s, _p(a), a.size))
+
+
+def aap_sur_get_grads(s) -> np.ndarray:
+    out = np.zeros(aap_sur_param_count(s), np.float32)
+    _scheck(load().aap_sur_get_grads(s, _p(out), out.size))
+    return out
+
+
+def aap_sur_predict(s, dev_in, dev_eta, batch: int, applications: int, dev_out) -> None:
+    _scheck(load().aap_sur_predict(s, _vp(dev_in), _vp(dev_eta), int(batch), int(applications),
+                                   _vp(dev_out)))
+
+
+def aap_sur_train_step(s, dev_in, dev_target, dev_eta, batch: int) -> float:
+    loss = C.c_double()
+    _scheck(load().aap_sur_train_step(s, _vp(dev_in), _vp(dev_target), _vp(dev_eta), int(batch),
+                                      C.byref(loss)))
+    return loss.value
+
+
+def aap_conv3x3_forward(x, batch, h, w, cin, cout, wt, bias, relu, y, stream=None) -> None:
+    _scheck(load().aap_conv3x3_forward(_vp(x), batch, h, w, cin, cout, _vp(wt), _vp(bias), int(relu),
+                                       _vp(y), C.c_void_p(stream or 0)))
+
+
+def aap_conv3x3_backward_data(dy, batch, h, w, cin, cout, wt_t, mask, dx, stream=None) -> None:
+    _scheck(load().aap_conv3x3_backward_data(_vp(dy), batch, h, w, cin, cout, _vp(wt_t), _vp(mask),
+                                             _vp(dx), C.c_void_p(stream or 0)))
+
+
+def aap_conv3x3_backward_weight(x, dy, dy_stride, batch, h, w, cin, cout, part, part_floats, dw, db,
+                                stream=None) -> None:
+    _scheck(load().aap_conv3x3_backward_weight(_vp(x), _vp(dy), dy_stride, batch, h, w, cin, cout,
+                                               _vp(part), int(part_floats), _vp(dw), _vp(db),
+                                               C.c_void_p(stream or 0)))

@@ -1,0 +1,787 @@
+// aap_surrogate.cu -- coarse-grained convolutional surrogate of the particle
+// fields (density and polarisation, from aap_coarse_grain).
+//
+// Network: F(t + 10) = F(t) + Net(F(t), eta), four 3x3 convolutions with
+// circular padding, 4 (3 fields + the noise strength) -> 32 -> 32 -> 32 -> 3
+// channels, ReLU between layers.  Activations are BF16 NHWC, weights BF16,
+// every contraction accumulates in FP32; master weights and Adam moments are
+// FP32.  Channel counts are padded for the tensor-core tiles: the first
+// layer's 4 inputs to 16, the last layer's 3 outputs to 8 (the padded weights
+// start at zero and receive zero gradient, so they stay zero).
+//
+// Kernels:
+//   k_conv<CIN, COUT, MODE>   implicit-GEMM convolution on mma.sync
+//                             m16n8k16 (BF16 x BF16 -> FP32): forward with
+//                             bias + ReLU, forward with the residual update,
+//                             or the data gradient (flipped, transposed
+//                             weights) masked by the ReLU of the layer input
+//   k_conv_dw<CIN, COUT>      weight and bias gradients, FP32 FMAs over BF16
+//                             operands, one partial per block, reduced in a
+//                             fixed order (deterministic)
+//   k_adam                    Adam step on the FP32 master weights
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/aap.h"
+#include "../../include/aap_surrogate.h"
+
+namespace aaps {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kTH = 8, kTW = 16;   // output tile of one block: 8 rows x 16 columns
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+                 "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+enum { MODE_RELU = 0, MODE_RESID = 1, MODE_MASK = 2, MODE_LINEAR = 3 };
+
+// out[b, y, x, co] = sum_{tap, ci} w[tap][co][ci] * in[b, (y+dy-1) mod H, (x+dx-1) mod W, ci]
+// (tap = 3 dy + dx), then per MODE:
+//   MODE_RELU   + bias, ReLU, BF16 NHWC out
+//   MODE_LINEAR + bias, BF16 NHWC out
+//   MODE_RESID  + bias, FP32: resid_out = resid_in + value (NHWC, 8 channels)
+//   MODE_MASK   value where mask > 0 else 0, BF16 NHWC out (data gradient)
+// Block: 8 x 16 output pixels of one image, 8 warps, warp w owns tile row w.
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(256) k_conv(const bf16 *__restrict__ in, int H, int W,
+                                              const bf16 *__restrict__ wt, const float *__restrict__ bias,
+                                              bf16 *__restrict__ out, const bf16 *__restrict__ mask,
+                                              const float *__restrict__ resid_in, float *__restrict__ resid_out)
+{
+    constexpr int CS = CIN + 8;          // padded pixel stride (bank-conflict free ldmatrix)
+    constexpr int NT = COUT / 8;         // n-tiles of 8 output channels
+    __shared__ __align__(16) bf16 s_in[(kTH + 2) * (kTW + 2) * CS];
+    __shared__ __align__(16) bf16 s_w[9 * COUT * CS];
+    const int b = blockIdx.z, y0 = blockIdx.y * kTH, x0 = blockIdx.x * kTW;
+    constexpr int VEC = CIN / 8;         // 16-byte vectors per pixel
+    for (int i = threadIdx.x; i < (kTH + 2) * (kTW + 2) * VEC; i += 256) {
+        const int pix = i / VEC, v = i - pix * VEC;
+        const int hy = pix / (kTW + 2), hx = pix - hy * (kTW + 2);
+        int gy = y0 + hy - 1, gx = x0 + hx - 1;
+        gy += (gy < 0) ? H : 0;
+        gy -= (gy >= H) ? H : 0;
+        gx += (gx < 0) ? W : 0;
+        gx -= (gx >= W) ? W : 0;
+        const uint4 *src = reinterpret_cast<const uint4 *>(in + (((size_t)b * H + gy) * W + gx) * CIN) + v;
+        *reinterpret_cast<uint4 *>(s_in + pix * CS + v * 8) = *src;
+    }
+    for (int i = threadIdx.x; i < 9 * COUT * VEC; i += 256) {
+        const int row = i / VEC, v = i - row * VEC;
+        *reinterpret_cast<uint4 *>(s_w + row * CS + v * 8) =
+            *(reinterpret_cast<const uint4 *>(wt + (size_t)row * CIN) + v);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float acc[NT][4];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    const int apix = lane & 15, akoff = (lane >> 4) * 8;
+    const int brow = lane & 7, bkoff = ((lane >> 3) & 1) * 8, bnt = lane >> 4;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap - dy * 3;
+#pragma unroll
+        for (int kc = 0; kc < CIN / 16; ++kc) {
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4(a0, a1, a2, a3, s_in + ((warp + dy) * (kTW + 2) + apix + dx) * CS + kc * 16 + akoff);
+#pragma unroll
+            for (int n = 0; n + 1 < NT; n += 2) {
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4(b0, b1, b2, b3, s_w + (tap * COUT + (n + bnt) * 8 + brow) * CS + kc * 16 + bkoff);
+                mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+                mma_bf16(acc[n + 1], a0, a1, a2, a3, b2, b3);
+            }
+            if (NT & 1) {
+                uint32_t b0, b1;
+                ldsm_x2(b0, b1, s_w + (tap * COUT + (NT - 1) * 8 + brow) * CS + kc * 16 + bkoff);
+                mma_bf16(acc[NT - 1], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    // epilogue: acc[n][0,1] -> pixel g, channels 2t, 2t+1; acc[n][2,3] -> pixel g + 8
+    const int g = lane >> 2, t = lane & 3;
+    const int y = y0 + warp;
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+        const int co = n * 8 + 2 * t;
+#pragma unroll
+        for (int hp = 0; hp < 2; ++hp) {
+            const int x = x0 + g + hp * 8;
+            const size_t pix = ((size_t)b * H + y) * W + x;
+            float v0 = acc[n][2 * hp], v1 = acc[n][2 * hp + 1];
+            if (MODE != MODE_MASK) {
+                v0 += bias[co];
+                v1 += bias[co + 1];
+            }
+            if (MODE == MODE_RELU) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            if (MODE == MODE_MASK) {
+                const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * COUT + co);
+                if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
+                if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
+            }
+            if (MODE == MODE_RESID) {
+                resid_out[pix * 8 + co] = resid_in[pix * 8 + co] + v0;
+                resid_out[pix * 8 + co + 1] = resid_in[pix * 8 + co + 1] + v1;
+            } else {
+                *reinterpret_cast<__nv_bfloat162 *>(out + pix * COUT + co) = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
+}
+
+// Weight / bias gradient: dw[co][tap][ci] = sum_p dy[p][co] x[p + tap - 1][ci],
+// db[co] = sum_p dy[p][co], over a band of `rows` image rows per block (dy
+// holds dy_stride channels per pixel, of which the first COUT are used).
+// part[block][COUT * 9 * CIN + COUT] receives the block's partial sums.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_conv_dw(const bf16 *__restrict__ x, const bf16 *__restrict__ dy,
+                                                 int dy_stride, int H, int W, int rows, float *__restrict__ part)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    bf16 *s_x = reinterpret_cast<bf16 *>(smem_raw);                 // (rows+2) x (W+2) x CIN
+    bf16 *s_dy = s_x + (size_t)(rows + 2) * (W + 2) * CIN;          // rows x W x COUT
+    const int b = blockIdx.y, r0 = blockIdx.x * rows;
+    constexpr int VX = CIN / 8, VD = COUT / 8;
+    for (int i = threadIdx.x; i < (rows + 2) * (W + 2) * VX; i += 256) {
+        const int pix = i / VX, v = i - pix * VX;
+        const int hy = pix / (W + 2), hx = pix - hy * (W + 2);
+        int gy = r0 + hy - 1, gx = hx - 1;
+        gy += (gy < 0) ? H : 0;
+        gy -= (gy >= H) ? H : 0;
+        gx += (gx < 0) ? W : 0;
+        gx -= (gx >= W) ? W : 0;
+        *reinterpret_cast<uint4 *>(s_x + (size_t)pix * CIN + v * 8) =
+            *(reinterpret_cast<const uint4 *>(x + (((size_t)b * H + gy) * W + gx) * CIN) + v);
+    }
+    for (int i = threadIdx.x; i < rows * W * VD; i += 256) {
+        const int pix = i / VD, v = i - pix * VD;
+        const int yy = pix / W, xx = pix - yy * W;
+        *reinterpret_cast<uint4 *>(s_dy + (size_t)pix * COUT + v * 8) =
+            *(reinterpret_cast<const uint4 *>(dy + (((size_t)b * H + r0 + yy) * W + xx) * dy_stride) + v);
+    }
+    __syncthreads();
+    constexpr int TPC = 256 / COUT;      // threads per output channel
+    constexpr int CPT = CIN / TPC;       // input channels per thread
+    static_assert(CPT >= 1 && CIN % TPC == 0, "channel split");
+    const int co = threadIdx.x / TPC, cb = (threadIdx.x % TPC) * CPT;
+    float acc[9][CPT];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) acc[k][j] = 0.f;
+    float accb = 0.f;
+    for (int yy = 0; yy < rows; ++yy) {
+        for (int xx = 0; xx < W; ++xx) {
+            const float d = __bfloat162float(s_dy[((size_t)yy * W + xx) * COUT + co]);
+            accb += d;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int ty = tap / 3, tx = tap - ty * 3;
+                const bf16 *px = s_x + ((size_t)(yy + ty) * (W + 2) + xx + tx) * CIN + cb;
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) acc[tap][j] = fmaf(d, __bfloat162float(px[j]), acc[tap][j]);
+            }
+        }
+    }
+    float *pb = part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (COUT * 9 * CIN + COUT);
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) pb[((size_t)co * 9 + tap) * CIN + cb + j] = acc[tap][j];
+    if (threadIdx.x % TPC == 0) pb[COUT * 9 * CIN + co] = accb;
+}
+
+// out[i] = sum_k part[k][i] in a fixed order (deterministic).
+__global__ void k_reduce_parts(const float *__restrict__ part, int nparts, int len, float *__restrict__ w_out,
+                               int wlen, float *__restrict__ b_out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < nparts; ++k) s += part[(size_t)k * len + i];
+        if (i < wlen) w_out[i] = s; else b_out[i - wlen] = s;
+    }
+}
+
+// Fields in (FP32 planes [B][3][H][W]) -> normalised residual state (FP32 NHWC 8)
+// and the BF16 network input (NHWC 16: 3 fields, the noise strength, zeros).
+__global__ void k_fields_in(const float *__restrict__ f, const float *__restrict__ eta, int B, int H, int W,
+                            float rho0, float eta_c, float eta_s, float *__restrict__ state, bf16 *__restrict__ x0)
+{
+    const long long n = (long long)B * H * W;
+    const long long plane = (long long)H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / plane, p = i - b * plane;
+        const float u0 = f[(b * 3 + 0) * plane + p] / rho0 - 1.f;
+        const float u1 = f[(b * 3 + 1) * plane + p] / rho0;
+        const float u2 = f[(b * 3 + 2) * plane + p] / rho0;
+        float *s = state + i * 8;
+        s[0] = u0; s[1] = u1; s[2] = u2;
+        s[3] = s[4] = s[5] = s[6] = s[7] = 0.f;
+        const float e = (eta[b] - eta_c) / eta_s;
+        __nv_bfloat162 *xb = reinterpret_cast<__nv_bfloat162 *>(x0 + i * 16);
+        xb[0] = __floats2bfloat162_rn(u0, u1);
+        xb[1] = __floats2bfloat162_rn(u2, e);
+        for (int k = 2; k < 8; ++k) xb[k] = __floats2bfloat162_rn(0.f, 0.f);
+    }
+}
+
+// Residual state -> the next network input (after one application).
+__global__ void k_state_to_input(const float *__restrict__ state, const float *__restrict__ eta, int B, int H,
+                                 int W, float eta_c, float eta_s, bf16 *__restrict__ x0)
+{
+    const long long n = (long long)B * H * W;
+    const long long plane = (long long)H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / plane;
+        const float *s = state + i * 8;
+        const float e = (eta[b] - eta_c) / eta_s;
+        __nv_bfloat162 *xb = reinterpret_cast<__nv_bfloat162 *>(x0 + i * 16);
+        xb[0] = __floats2bfloat162_rn(s[0], s[1]);
+        xb[1] = __floats2bfloat162_rn(s[2], e);
+        for (int k = 2; k < 8; ++k) xb[k] = __floats2bfloat162_rn(0.f, 0.f);
+    }
+}
+
+// Normalised state -> fields (FP32 planes).
+__global__ void k_fields_out(const float *__restrict__ state, int B, int H, int W, float rho0, float *__restrict__ f)
+{
+    const long long n = (long long)B * H * W;
+    const long long plane = (long long)H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / plane, p = i - b * plane;
+        const float *s = state + i * 8;
+        f[(b * 3 + 0) * plane + p] = rho0 * (s[0] + 1.f);
+        f[(b * 3 + 1) * plane + p] = rho0 * s[1];
+        f[(b * 3 + 2) * plane + p] = rho0 * s[2];
+    }
+}
+
+// Mean squared error over the 3 field channels of pred vs target (both
+// normalised FP32 NHWC 8), per-block partial sums; dout = d loss / d pred in
+// BF16 NHWC 16 (channels >= 3 zero).
+__global__ void k_mse(const float *__restrict__ pred, const float *__restrict__ target, long long npix,
+                      float scale, float *__restrict__ part, bf16 *__restrict__ dout)
+{
+    __shared__ float red[256];
+    float s = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
+        float d[3];
+        for (int c = 0; c < 3; ++c) {
+            d[c] = pred[i * 8 + c] - target[i * 8 + c];
+            s += d[c] * d[c];
+        }
+        __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(dout + i * 16);
+        o[0] = __floats2bfloat162_rn(2.f * scale * d[0], 2.f * scale * d[1]);
+        o[1] = __floats2bfloat162_rn(2.f * scale * d[2], 0.f);
+        for (int k = 2; k < 8; ++k) o[k] = __floats2bfloat162_rn(0.f, 0.f);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// Adam (Kingma & Ba) on the FP32 master parameters.
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// Master weights [co][tap][ci] -> BF16 forward layout [tap][co][ci] and the
+// data-gradient layout [tap'][ci][cob] with tap' = 8 - tap the flipped tap and
+// cob >= cout output channels (zero beyond cout; the buffer is cleared first).
+__global__ void k_pack(const float *__restrict__ w, int cout, int cin, bf16 *__restrict__ wf, bf16 *__restrict__ wb,
+                       int cob)
+{
+    const int n = cout * 9 * cin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int co = i / (9 * cin), r = i - co * 9 * cin, tap = r / cin, ci = r - tap * cin;
+        const bf16 v = __float2bfloat16_rn(w[i]);
+        wf[((size_t)tap * cout + co) * cin + ci] = v;
+        if (wb) wb[((size_t)(8 - tap) * cin + ci) * cob + co] = v;
+    }
+}
+
+}  // namespace aaps
+
+using namespace aaps;
+
+// ------------------------------------------------------------------ host --
+namespace {
+
+thread_local std::string s_err;
+
+int sfail(int code, const std::string &m)
+{
+    s_err = m;
+    return code;
+}
+
+#define SCK(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return sfail(AAP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+template <int CIN, int COUT, int MODE>
+cudaError_t conv(const bf16 *in, int B, int H, int W, const bf16 *w, const float *bias, bf16 *out, const bf16 *mask,
+                 const float *rin, float *rout, cudaStream_t st)
+{
+    dim3 grid(W / kTW, H / kTH, B);
+    k_conv<CIN, COUT, MODE><<<grid, 256, 0, st>>>(in, H, W, w, bias, out, mask, rin, rout);
+    return cudaGetLastError();
+}
+
+int dw_rows(int H) { return H % 4 == 0 ? 4 : (H % 2 == 0 ? 2 : 1); }
+
+template <int CIN, int COUT>
+size_t dw_smem(int H, int W)
+{
+    const int rows = dw_rows(H);
+    return (size_t)(rows + 2) * (W + 2) * CIN * 2 + (size_t)rows * W * COUT * 2;
+}
+
+template <int CIN, int COUT>
+cudaError_t conv_dw(const bf16 *x, const bf16 *dy, int dy_stride, int B, int H, int W, float *part, float *dw,
+                    float *db, cudaStream_t st)
+{
+    const int rows = dw_rows(H);
+    const size_t smem = dw_smem<CIN, COUT>(H, W);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_dw<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(H / rows, B);
+    k_conv_dw<CIN, COUT><<<grid, 256, smem, st>>>(x, dy, dy_stride, H, W, rows, part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int len = COUT * 9 * CIN + COUT;
+    k_reduce_parts<<<std::max(1, (len + 255) / 256), 256, 0, st>>>(part, (int)(grid.x * grid.y), len, dw,
+                                                                      COUT * 9 * CIN, db);
+    return cudaGetLastError();
+}
+
+bool valid_shape(int H, int W) { return H >= 8 && W >= 16 && H % 8 == 0 && W % 16 == 0 && H <= 4096 && W <= 4096; }
+
+}  // namespace
+
+// Layer table: (cin, cout) padded.
+static const int kLayerCin[4] = {16, 32, 32, 32};
+static const int kLayerCout[4] = {32, 32, 32, 8};
+
+struct aap_sur {
+    aap_sur_params p{};
+    cudaStream_t stream = nullptr;
+    int H = 0, W = 0, maxb = 0;
+    long long nparam = 0;
+    long long woff[4], boff[4];
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;       // FP32 master, grad, Adam moments
+    bf16 *wf[4] = {}, *wb[4] = {};                                     // packed BF16 weights
+    bf16 *x0 = nullptr, *a[3] = {}, *d[3] = {}, *dout = nullptr;       // activations and gradients
+    float *state = nullptr, *state2 = nullptr, *target = nullptr, *eta = nullptr;
+    float *part = nullptr, *loss_part = nullptr;
+    size_t part_floats = 0;
+    int loss_blocks = 0;
+    long long t = 0;                                                   // Adam step
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+template <typename T>
+int salloc(aap_sur *s, T **p, size_t bytes)
+{
+    void *q = nullptr;
+    if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(AAP_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    s->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return AAP_OK;
+}
+
+void sfree(aap_sur *s)
+{
+    for (void *q : s->allocs) cudaFree(q);
+    s->allocs.clear();
+}
+
+// Output channels of the data-gradient weight layout of layer l (the last
+// layer's 8 are padded to 16, the smallest input width of k_conv).
+int cob_of(int l) { return std::max(kLayerCout[l], 16); }
+
+int pack_all(aap_sur *s)
+{
+    for (int l = 0; l < 4; ++l) {
+        const int n = kLayerCout[l] * 9 * kLayerCin[l];
+        if (l > 0) SCK(cudaMemsetAsync(s->wb[l], 0, (size_t)cob_of(l) * 9 * kLayerCin[l] * 2, s->stream));
+        k_pack<<<(n + 255) / 256, 256, 0, s->stream>>>(s->w + s->woff[l], kLayerCout[l], kLayerCin[l], s->wf[l],
+                                                       l > 0 ? s->wb[l] : nullptr, cob_of(l));
+        SCK(cudaGetLastError());
+    }
+    return AAP_OK;
+}
+
+// Forward of `batch` samples from s->x0; the result (normalised state after
+// one application) goes to s->state2 from s->state.
+int forward(aap_sur *s, int batch)
+{
+    const int H = s->H, W = s->W;
+    cudaStream_t st = s->stream;
+    SCK((conv<16, 32, MODE_RELU>(s->x0, batch, H, W, s->wf[0], s->w + s->boff[0], s->a[0], nullptr, nullptr, nullptr, st)));
+    SCK((conv<32, 32, MODE_RELU>(s->a[0], batch, H, W, s->wf[1], s->w + s->boff[1], s->a[1], nullptr, nullptr, nullptr, st)));
+    SCK((conv<32, 32, MODE_RELU>(s->a[1], batch, H, W, s->wf[2], s->w + s->boff[2], s->a[2], nullptr, nullptr, nullptr, st)));
+    SCK((conv<32, 8, MODE_RESID>(s->a[2], batch, H, W, s->wf[3], s->w + s->boff[3], nullptr, nullptr, s->state, s->state2, st)));
+    return AAP_OK;
+}
+
+unsigned long long splitmix(unsigned long long &x)
+{
+    unsigned long long z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *aap_sur_last_error(void) { return s_err.c_str(); }
+
+void aap_sur_params_default(aap_sur_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->nbx = p->nby = 128;
+    p->max_batch = 32;
+    p->rho0 = 2.0;
+    p->eta_center = 0.4;
+    p->eta_scale = 0.1;
+    p->lr = 1e-3;
+    p->beta1 = 0.9;
+    p->beta2 = 0.999;
+    p->eps = 1e-8;
+    p->seed = 1;
+}
+
+int aap_sur_create(const aap_sur_params *p, void *stream, aap_sur **out)
+{
+    s_err.clear();
+    if (!p || !out) return sfail(AAP_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (!valid_shape(p->nby, p->nbx)) return sfail(AAP_EINVAL, "nby must be a multiple of 8 and nbx of 16 (<= 4096)");
+    if (p->max_batch < 1 || p->max_batch > 4096) return sfail(AAP_EINVAL, "max_batch must be in [1, 4096]");
+    if (!(p->rho0 > 0) || !(p->eta_scale > 0) || !(p->lr > 0) || !(p->eps > 0))
+        return sfail(AAP_EINVAL, "rho0, eta_scale, lr and eps must be positive");
+    aap_sur *s = new aap_sur();
+    s->p = *p;
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->H = p->nby;
+    s->W = p->nbx;
+    s->maxb = p->max_batch;
+    long long off = 0;
+    for (int l = 0; l < 4; ++l) {
+        s->woff[l] = off;
+        off += (long long)kLayerCout[l] * 9 * kLayerCin[l];
+        s->boff[l] = off;
+        off += kLayerCout[l];
+    }
+    s->nparam = off;
+    const size_t pix = (size_t)s->maxb * s->H * s->W;
+    int rc = AAP_OK;
+    auto A = [&](auto **ptr, size_t bytes) {
+        if (rc == AAP_OK) rc = salloc(s, ptr, bytes);
+    };
+    A(&s->w, off * 4);
+    A(&s->g, off * 4);
+    A(&s->m, off * 4);
+    A(&s->v, off * 4);
+    for (int l = 0; l < 4; ++l) {
+        A(&s->wf[l], (size_t)kLayerCout[l] * 9 * kLayerCin[l] * 2);
+        A(&s->wb[l], (size_t)std::max(kLayerCout[l], 16) * 9 * kLayerCin[l] * 2);
+    }
+    A(&s->x0, pix * 16 * 2);
+    for (int l = 0; l < 3; ++l) {
+        A(&s->a[l], pix * 32 * 2);
+        A(&s->d[l], pix * 32 * 2);
+    }
+    A(&s->dout, pix * 16 * 2);
+    A(&s->state, pix * 8 * 4);
+    A(&s->state2, pix * 8 * 4);
+    A(&s->target, pix * 8 * 4);
+    A(&s->eta, (size_t)s->maxb * 4);
+    // weight-gradient partials: one per (row band, sample)
+    const size_t nblk = (size_t)(s->H / dw_rows(s->H)) * s->maxb;
+    s->part_floats = nblk * (32 * 9 * 32 + 32);
+    A(&s->part, s->part_floats * 4);
+    s->loss_blocks = 256;
+    A(&s->loss_part, (size_t)s->loss_blocks * 4);
+    if (rc) {
+        sfree(s);
+        delete s;
+        return rc;
+    }
+    // He-uniform initial weights (splitmix64 stream from the seed); the last
+    // layer starts small so that the residual map starts near the identity;
+    // padded inputs / outputs are zero.
+    std::vector<float> hw((size_t)off, 0.f);
+    unsigned long long st = p->seed;
+    for (int l = 0; l < 4; ++l) {
+        const int cin_real = l == 0 ? 4 : 32, cout_real = l == 3 ? 3 : 32;
+        const double bound = std::sqrt(6.0 / (9.0 * cin_real)) * (l == 3 ? 0.1 : 1.0);
+        for (int co = 0; co < kLayerCout[l]; ++co)
+            for (int tap = 0; tap < 9; ++tap)
+                for (int ci = 0; ci < kLayerCin[l]; ++ci) {
+                    const double u = (double)(splitmix(st) >> 11) * (1.0 / 9007199254740992.0);
+                    if (co < cout_real && ci < cin_real)
+                        hw[(size_t)s->woff[l] + ((size_t)co * 9 + tap) * kLayerCin[l] + ci] = (float)((2.0 * u - 1.0) * bound);
+                }
+    }
+    if (cudaMemcpy(s->w, hw.data(), (size_t)off * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(s->m, 0, (size_t)off * 4) != cudaSuccess || cudaMemset(s->v, 0, (size_t)off * 4) != cudaSuccess ||
+        cudaMemset(s->g, 0, (size_t)off * 4) != cudaSuccess) {
+        sfree(s);
+        delete s;
+        return sfail(AAP_ECUDA, "surrogate initialisation");
+    }
+    if ((rc = pack_all(s)) || cudaStreamSynchronize(s->stream) != cudaSuccess) {
+        sfree(s);
+        delete s;
+        return rc ? rc : sfail(AAP_ECUDA, "surrogate initialisation");
+    }
+    *out = s;
+    return AAP_OK;
+}
+
+int aap_sur_destroy(aap_sur *s)
+{
+    if (!s) return AAP_OK;
+    cudaStreamSynchronize(s->stream);
+    sfree(s);
+    delete s;
+    return AAP_OK;
+}
+
+int aap_sur_param_count(aap_sur *s, int64_t *count)
+{
+    if (!s || !count) return sfail(AAP_EINVAL, "NULL argument");
+    *count = s->nparam;
+    return AAP_OK;
+}
+
+int aap_sur_get_params(aap_sur *s, float *host, int64_t count)
+{
+    if (!s || !host || count != s->nparam) return sfail(AAP_EINVAL, "bad arguments");
+    SCK(cudaMemcpyAsync(host, s->w, (size_t)count * 4, cudaMemcpyDeviceToHost, s->stream));
+    SCK(cudaStreamSynchronize(s->stream));
+    return AAP_OK;
+}
+
+int aap_sur_set_params(aap_sur *s, const float *host, int64_t count)
+{
+    if (!s || !host || count != s->nparam) return sfail(AAP_EINVAL, "bad arguments");
+    SCK(cudaMemcpyAsync(s->w, host, (size_t)count * 4, cudaMemcpyHostToDevice, s->stream));
+    SCK(cudaMemsetAsync(s->m, 0, (size_t)count * 4, s->stream));
+    SCK(cudaMemsetAsync(s->v, 0, (size_t)count * 4, s->stream));
+    s->t = 0;
+    int rc = pack_all(s);
+    if (rc) return rc;
+    SCK(cudaStreamSynchronize(s->stream));
+    return AAP_OK;
+}
+
+int aap_sur_predict(aap_sur *s, const float *dev_in, const float *dev_eta, int32_t batch, int32_t applications,
+                    float *dev_out)
+{
+    if (!s || !dev_in || !dev_eta || !dev_out) return sfail(AAP_EINVAL, "NULL argument");
+    if (batch < 1 || batch > s->maxb || applications < 0) return sfail(AAP_EINVAL, "bad batch or applications");
+    const int H = s->H, W = s->W;
+    const int grid = 1024;
+    SCK(cudaMemcpyAsync(s->eta, dev_eta, (size_t)batch * 4, cudaMemcpyDeviceToDevice, s->stream));
+    k_fields_in<<<grid, 256, 0, s->stream>>>(dev_in, s->eta, batch, H, W, (float)s->p.rho0, (float)s->p.eta_center,
+                                             (float)s->p.eta_scale, s->state, s->x0);
+    SCK(cudaGetLastError());
+    for (int k = 0; k < applications; ++k) {
+        if (k > 0) {
+            k_state_to_input<<<grid, 256, 0, s->stream>>>(s->state, s->eta, batch, H, W, (float)s->p.eta_center,
+                                                          (float)s->p.eta_scale, s->x0);
+            SCK(cudaGetLastError());
+        }
+        int rc = forward(s, batch);
+        if (rc) return rc;
+        std::swap(s->state, s->state2);
+    }
+    k_fields_out<<<grid, 256, 0, s->stream>>>(s->state, batch, H, W, (float)s->p.rho0, dev_out);
+    SCK(cudaGetLastError());
+    return AAP_OK;
+}
+
+int aap_sur_train_step(aap_sur *s, const float *dev_in, const float *dev_target, const float *dev_eta, int32_t batch,
+                       double *loss_out)
+{
+    if (!s || !dev_in || !dev_target || !dev_eta) return sfail(AAP_EINVAL, "NULL argument");
+    if (batch < 1 || batch > s->maxb) return sfail(AAP_EINVAL, "bad batch");
+    const int H = s->H, W = s->W;
+    cudaStream_t st = s->stream;
+    const int grid = 1024;
+    SCK(cudaMemcpyAsync(s->eta, dev_eta, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st));
+    // targets: normalised through the same path (x0 is overwritten below)
+    k_fields_in<<<grid, 256, 0, st>>>(dev_target, s->eta, batch, H, W, (float)s->p.rho0, (float)s->p.eta_center,
+                                      (float)s->p.eta_scale, s->target, s->x0);
+    k_fields_in<<<grid, 256, 0, st>>>(dev_in, s->eta, batch, H, W, (float)s->p.rho0, (float)s->p.eta_center,
+                                      (float)s->p.eta_scale, s->state, s->x0);
+    SCK(cudaGetLastError());
+    int rc = forward(s, batch);
+    if (rc) return rc;
+    const long long npix = (long long)batch * H * W;
+    k_mse<<<s->loss_blocks, 256, 0, st>>>(s->state2, s->target, npix, (float)(1.0 / (3.0 * (double)npix)),
+                                          s->loss_part, s->dout);
+    SCK(cudaGetLastError());
+    float *g = s->g;
+    const float *bias_none = nullptr;
+    (void)bias_none;
+    // layer 4: weight gradient from a[2] and dout (16-channel pixels, 8 used);
+    // data gradient through the flipped weights, masked by ReLU(a[2]) > 0
+    SCK((conv_dw<32, 8>(s->a[2], s->dout, 16, batch, H, W, s->part, g + s->woff[3], g + s->boff[3], st)));
+    SCK((conv<16, 32, MODE_MASK>(s->dout, batch, H, W, s->wb[3], nullptr, s->d[2], s->a[2], nullptr, nullptr, st)));
+    // layer 3
+    SCK((conv_dw<32, 32>(s->a[1], s->d[2], 32, batch, H, W, s->part, g + s->woff[2], g + s->boff[2], st)));
+    SCK((conv<32, 32, MODE_MASK>(s->d[2], batch, H, W, s->wb[2], nullptr, s->d[1], s->a[1], nullptr, nullptr, st)));
+    // layer 2
+    SCK((conv_dw<32, 32>(s->a[0], s->d[1], 32, batch, H, W, s->part, g + s->woff[1], g + s->boff[1], st)));
+    SCK((conv<32, 32, MODE_MASK>(s->d[1], batch, H, W, s->wb[1], nullptr, s->d[0], s->a[0], nullptr, nullptr, st)));
+    // layer 1 (its input needs no gradient)
+    SCK((conv_dw<16, 32>(s->x0, s->d[0], 32, batch, H, W, s->part, g + s->woff[0], g + s->boff[0], st)));
+    // Adam step and the BF16 copies
+    s->t += 1;
+    const double c1 = 1.0 - std::pow(s->p.beta1, (double)s->t), c2 = 1.0 - std::pow(s->p.beta2, (double)s->t);
+    k_adam<<<(int)std::min<long long>(1024, (s->nparam + 255) / 256), 256, 0, st>>>(
+        s->w, s->g, s->m, s->v, (int)s->nparam, (float)s->p.lr, (float)s->p.beta1, (float)s->p.beta2,
+        (float)s->p.eps, (float)c1, (float)c2);
+    SCK(cudaGetLastError());
+    if ((rc = pack_all(s))) return rc;
+    if (loss_out) {
+        std::vector<float> lp(s->loss_blocks);
+        SCK(cudaMemcpyAsync(lp.data(), s->loss_part, lp.size() * 4, cudaMemcpyDeviceToHost, st));
+        SCK(cudaStreamSynchronize(st));
+        double tot = 0.0;
+        for (float v : lp) tot += v;
+        *loss_out = tot / (3.0 * (double)npix);
+    }
+    return AAP_OK;
+}
+
+// Gradient of the last train step (FP32, the layout of aap_sur_get_params).
+int aap_sur_get_grads(aap_sur *s, float *host, int64_t count)
+{
+    if (!s || !host || count != s->nparam) return sfail(AAP_EINVAL, "bad arguments");
+    SCK(cudaMemcpyAsync(host, s->g, (size_t)count * 4, cudaMemcpyDeviceToHost, s->stream));
+    SCK(cudaStreamSynchronize(s->stream));
+    return AAP_OK;
+}
+
+// ---- the convolution kernels alone (device buffers, BF16 as raw 16-bit) ----
+int aap_conv3x3_forward(const uint16_t *x, int32_t batch, int32_t h, int32_t w, int32_t cin, int32_t cout,
+                        const uint16_t *wt, const float *bias, int32_t relu, uint16_t *y, void *stream)
+{
+    if (!x || !wt || !bias || !y || batch < 1 || !valid_shape(h, w)) return sfail(AAP_EINVAL, "bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bf16 *X = reinterpret_cast<const bf16 *>(x), *Wt = reinterpret_cast<const bf16 *>(wt);
+    bf16 *Y = reinterpret_cast<bf16 *>(y);
+    cudaError_t e;
+    if (cin == 16 && cout == 32) e = relu ? conv<16, 32, MODE_RELU>(X, batch, h, w, Wt, bias, Y, nullptr, nullptr, nullptr, st)
+                                          : conv<16, 32, MODE_LINEAR>(X, batch, h, w, Wt, bias, Y, nullptr, nullptr, nullptr, st);
+    else if (cin == 32 && cout == 32) e = relu ? conv<32, 32, MODE_RELU>(X, batch, h, w, Wt, bias, Y, nullptr, nullptr, nullptr, st)
+                                               : conv<32, 32, MODE_LINEAR>(X, batch, h, w, Wt, bias, Y, nullptr, nullptr, nullptr, st);
+    else if (cin == 32 && cout == 8) e = relu ? conv<32, 8, MODE_RELU>(X, batch, h, w, Wt, bias, Y, nullptr, nullptr, nullptr, st)
+                                              : conv<32, 8, MODE_LINEAR>(X, batch, h, w, Wt, bias, Y, nullptr, nullptr, nullptr, st);
+    else if (cin == 16 && cout == 8) e = relu ? conv<16, 8, MODE_RELU>(X, batch, h, w, Wt, bias, Y, nullptr, nullptr, nullptr, st)
+                                              : conv<16, 8, MODE_LINEAR>(X, batch, h, w, Wt, bias, Y, nullptr, nullptr, nullptr, st);
+    else return sfail(AAP_EINVAL, "supported (cin, cout): (16, 32), (32, 32), (32, 8), (16, 8)");
+    if (e != cudaSuccess) return sfail(AAP_ECUDA, cudaGetErrorString(e));
+    return AAP_OK;
+}
+
+int aap_conv3x3_backward_data(const uint16_t *dy, int32_t batch, int32_t h, int32_t w, int32_t cin, int32_t cout,
+                              const uint16_t *wt_t, const uint16_t *mask, uint16_t *dx, void *stream)
+{
+    // dx[., ci] = sum_{tap', co} wt_t[tap'][ci][co] dy[p + tap' - 1][co], zeroed where mask <= 0
+    if (!dy || !wt_t || !mask || !dx || batch < 1 || !valid_shape(h, w)) return sfail(AAP_EINVAL, "bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bf16 *D = reinterpret_cast<const bf16 *>(dy), *Wt = reinterpret_cast<const bf16 *>(wt_t);
+    const bf16 *M = reinterpret_cast<const bf16 *>(mask);
+    bf16 *X = reinterpret_cast<bf16 *>(dx);
+    cudaError_t e;
+    if (cout == 32 && cin == 32) e = conv<32, 32, MODE_MASK>(D, batch, h, w, Wt, nullptr, X, M, nullptr, nullptr, st);
+    else if (cout == 16 && cin == 32) e = conv<16, 32, MODE_MASK>(D, batch, h, w, Wt, nullptr, X, M, nullptr, nullptr, st);
+    else return sfail(AAP_EINVAL, "supported (cout, cin): (32, 32), (16, 32)");
+    if (e != cudaSuccess) return sfail(AAP_ECUDA, cudaGetErrorString(e));
+    return AAP_OK;
+}
+
+int aap_conv3x3_backward_weight(const uint16_t *x, const uint16_t *dy, int32_t dy_stride, int32_t batch, int32_t h,
+                                int32_t w, int32_t cin, int32_t cout, float *part, int64_t part_floats, float *dw,
+                                float *db, void *stream)
+{
+    if (!x || !dy || !part || !dw || !db || batch < 1 || !valid_shape(h, w)) return sfail(AAP_EINVAL, "bad arguments");
+    const long long need = (long long)(h / dw_rows(h)) * batch * (cout * 9 * cin + cout);
+    if (part_floats < need) return sfail(AAP_EINVAL, "part buffer too small: need " + std::to_string(need) + " floats");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bf16 *X = reinterpret_cast<const bf16 *>(x), *D = reinterpret_cast<const bf16 *>(dy);
+    cudaError_t e;
+    if (cin == 32 && cout == 32) e = conv_dw<32, 32>(X, D, dy_stride, batch, h, w, part, dw, db, st);
+    else if (cin == 16 && cout == 32) e = conv_dw<16, 32>(X, D, dy_stride, batch, h, w, part, dw, db, st);
+    else if (cin == 32 && cout == 8) e = conv_dw<32, 8>(X, D, dy_stride, batch, h, w, part, dw, db, st);
+    else return sfail(AAP_EINVAL, "supported (cin, cout): (32, 32), (16, 32), (32, 8)");
+    if (e != cudaSuccess) return sfail(AAP_ECUDA, cudaGetErrorString(e));
+    return AAP_OK;
+}
+
+}  // extern "C"

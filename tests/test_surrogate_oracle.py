@@ -1,0 +1,90 @@
+"""Pins of the surrogate oracle (no GPU): scipy's wrap-boundary correlation for
+the forward pass, central finite differences for both gradients and for the
+whole network, closed forms of Adam and of BF16 rounding."""
+import numpy as np
+import pytest
+
+from oracle import surrogate as S
+
+signal = pytest.importorskip("scipy.signal")
+
+
+def test_forward_matches_scipy_correlate2d():
+    g = np.random.default_rng(0)
+    x = g.normal(size=(2, 8, 16, 3))
+    w = g.normal(size=(4, 9, 3))
+    b = g.normal(size=4)
+    y = S.conv_forward(x, w, b)
+    for n in range(2):
+        for co in range(4):
+            ref = np.full((8, 16), b[co])
+            for ci in range(3):
+                k = w[co, :, ci].reshape(3, 3)
+                ref += signal.correlate2d(x[n, :, :, ci], k, mode="same", boundary="wrap")
+            assert np.allclose(y[n, :, :, co], ref, atol=1e-12)
+
+
+def _fd(f, a, idx, h=1e-6):
+    a = a.copy()
+    a[idx] += h
+    fp = f(a)
+    a[idx] -= 2 * h
+    fm = f(a)
+    return (fp - fm) / (2 * h)
+
+
+def test_backward_data_and_weight_finite_differences():
+    g = np.random.default_rng(1)
+    x = g.normal(size=(2, 8, 16, 5))
+    w = g.normal(size=(3, 9, 5))
+    b = g.normal(size=3)
+    c = g.normal(size=(2, 8, 16, 3))      # L = sum(c * y)
+    L = lambda xx=x, ww=w, bb=b: float((c * S.conv_forward(xx, ww, bb)).sum())
+    dx = S.conv_backward_data(c, w)
+    dw, db = S.conv_backward_weight(x, c)
+    for idx in [(0, 0, 0, 0), (1, 7, 15, 4), (0, 3, 9, 2), (1, 0, 15, 1)]:
+        assert abs(_fd(lambda a: L(xx=a), x, idx) - dx[idx]) < 1e-6
+    for idx in [(0, 0, 0), (2, 8, 4), (1, 4, 2)]:
+        assert abs(_fd(lambda a: L(ww=a), w, idx) - dw[idx]) < 1e-6
+    for k in range(3):
+        assert abs(_fd(lambda a: L(bb=a), b, k) - db[k]) < 1e-6
+
+
+def test_network_gradient_finite_differences():
+    g = np.random.default_rng(2)
+    n = sum(co * 9 * ci + co for ci, co in S.LAYERS)
+    params = g.normal(size=n) * 0.2
+    # keep the padding at zero like the library
+    layers = S.unpack(params.copy())
+    layers[0][0][:, :, 4:] = 0
+    layers[3][0][3:] = 0
+    layers[3][1][3:] = 0
+    params = S.pack(layers)
+    fields = np.abs(g.normal(size=(2, 3, 8, 16))) + 1.0
+    target = fields + 0.1 * g.normal(size=fields.shape)
+    st, x0 = S.normalise(fields, [0.35, 0.45], 2.0, 0.4, 0.1)
+    tg, _ = S.normalise(target, [0.35, 0.45], 2.0, 0.4, 0.1)
+    loss, grad = S.loss_and_grad(params, st, x0, tg)
+    f = lambda p: S.loss_and_grad(p, st, x0, tg)[0]
+    nz = np.nonzero(grad)[0]
+    for i in np.random.default_rng(3).choice(nz, 12, replace=False):
+        assert abs(_fd(f, params, i, 1e-6) - grad[i]) < 1e-7 + 1e-5 * abs(grad[i])
+    # padded weights get no gradient
+    gl = S.unpack(grad)
+    assert not gl[0][0][:, :, 4:].any() and not gl[3][0][3:].any() and not gl[3][1][3:].any()
+
+
+def test_adam_first_step_closed_form():
+    """First Adam step moves every parameter by lr * sign(grad) (bias-corrected)."""
+    p = np.array([1.0, -2.0, 0.5])
+    gr = np.array([0.3, -4.0, 1e-3])
+    p1, m, v = S.adam(p, gr, np.zeros(3), np.zeros(3), 1, lr=0.01, eps=0.0)
+    assert np.allclose(p1, p - 0.01 * np.sign(gr), atol=1e-15)
+
+
+def test_bf16_rounding():
+    vals = np.array([1.0, 1.00390625, 1.005859375, -3.0e-5, 65280.0, 1.0 + 2 ** -9])
+    r = S.bf16_round(vals)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0078125
+    assert r[5] == 1.0   # tie to even
+    assert np.array_equal(S.from_bf16_bits(S.bf16_bits(vals)), r)
