@@ -223,6 +223,27 @@ int aap_clear_results(aap_handle *h);
  * sum e^{i theta}, so p (Sec. 3.4) follows from the fields.  nbx, nby >= 1. */
 int aap_coarse_grain(aap_handle *h, int32_t nbx, int32_t nby, float *dev_out);
 
+/* Coarse-graining without any device allocation, for callers that cannot
+ * allocate: code whose device memory all belongs to a pool or arena, callers
+ * that must not call cudaMalloc (it may synchronise the device and is not
+ * allowed during stream capture), fixed-budget embedded users.  The paper has
+ * no counterpart; this is a library convenience.
+ * Same fields as aap_coarse_grain, from caller-owned DEVICE arrays x, y
+ * (FP64, in [0,lx] x [0,ly]) and theta (FP32) of n particles, into the
+ * caller-owned DEVICE buffer dev_out (3 * nbx * nby floats), on `stream`.
+ * The integer sums live in a fixed file-scope device array of 3 x 65,536
+ * 64-bit words (1.5 MiB, held by every device that loads the library until
+ * the process exits): nbx * nby must not exceed 65,536 (AAP_EINVAL
+ * otherwise).  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * share the array, which keeps the last call's sums and is cleared at the
+ * start of each call: calls whose work overlaps on the GPU (other streams or
+ * threads) race; calls ordered on one stream are safe.  Calls no cudaMalloc
+ * or cudaFree.  Messages: aap_noalloc_last_error(). */
+int aap_coarse_grain_noalloc(const double *x, const double *y, const float *theta, int64_t n, double lx, double ly,
+                             int32_t nbx, int32_t nby, float *dev_out, void *stream);
+const char *aap_noalloc_last_error(void);
+
 /* Per-kernel timing (tracing aid).  enable != 0: every step enqueued by
  * aap_step / aap_phi_trace / aap_step_neighbours records CUDA events on h's
  * stream around its two kernels (the tile step and the step finish); the

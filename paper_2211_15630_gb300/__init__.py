@@ -33,7 +33,7 @@ EXPORTS = (
     "aap_sur_last_error", "aap_sur_params_default", "aap_sur_create", "aap_sur_destroy",
     "aap_sur_param_count", "aap_sur_get_params", "aap_sur_set_params", "aap_sur_get_grads",
     "aap_sur_predict", "aap_sur_train_step", "aap_conv3x3_forward", "aap_conv3x3_backward_data",
-    "aap_conv3x3_backward_weight",
+    "aap_conv3x3_backward_weight", "aap_coarse_grain_noalloc", "aap_noalloc_last_error",
 )
 
 
@@ -139,6 +139,9 @@ def load(path: str = LIB_PATH):
         "aap_conv3x3_backward_data": (C.c_int, [vp, i32, i32, i32, i32, i32, vp, vp, vp, vp]),
         "aap_conv3x3_backward_weight": (C.c_int, [vp, vp, i32, i32, i32, i32, i32, i32, vp, i64,
                                                   vp, vp, vp]),
+        "aap_coarse_grain_noalloc": (C.c_int, [vp, vp, vp, i64, C.c_double, C.c_double, i32, i32, vp,
+                                               vp]),
+        "aap_noalloc_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -398,3 +401,14 @@ def aap_conv3x3_backward_weight(x, dy, dy_stride, batch, h, w, cin, cout, part, 
     _scheck(load().aap_conv3x3_backward_weight(_vp(x), _vp(dy), dy_stride, batch, h, w, cin, cout,
                                                _vp(part), int(part_floats), _vp(dw), _vp(db),
                                                C.c_void_p(stream or 0)))
+
+
+def aap_coarse_grain_noalloc(x_ptr, y_ptr, th_ptr, n: int, lx: float, ly: float, nbx: int, nby: int,
+                             dev_out_ptr, stream: int | None = None) -> None:
+    """Fields of caller-owned device arrays into a caller-owned device buffer,
+    with no device allocation (fixed internal scratch of 65,536 bins)."""
+    rc = load().aap_coarse_grain_noalloc(_vp(x_ptr), _vp(y_ptr), _vp(th_ptr), int(n), float(lx),
+                                         float(ly), int(nbx), int(nby), _vp(dev_out_ptr),
+                                         C.c_void_p(stream or 0))
+    if rc != AAP_OK:
+        raise AapError(rc, load().aap_noalloc_last_error().decode())
