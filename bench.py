@@ -150,6 +150,172 @@ def _cpu_baseline(eta, budget_s=20.0):
                       f"state ({t_used:.1f} s, OpenMP over {cores} threads)"}
 
 
+def _structure_factor(rho_counts):
+    """Radially averaged S(k) = <|rho_hat(k)|^2> / N of a density-count field."""
+    import numpy as np
+
+    n = rho_counts.sum()
+    d = rho_counts - rho_counts.mean()
+    f = np.abs(np.fft.fft2(d)) ** 2 / max(n, 1.0)
+    ky = np.fft.fftfreq(d.shape[0]) * d.shape[0]
+    kx = np.fft.fftfreq(d.shape[1]) * d.shape[1]
+    kk = np.sqrt(ky[:, None] ** 2 + kx[None, :] ** 2)
+    kb = np.rint(kk).astype(int)
+    kmax = min(d.shape) // 2
+    s = np.array([f[kb == k].mean() for k in range(1, kmax)])
+    return s
+
+
+def _bench_brownian(A, W, torch, stream, steps):
+    p = W.brownian_walls(seed=1)
+    h = A.aap_create(p, stream.cuda_stream)
+    A.aap_step(h, 20)
+    A.aap_sync(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    A.aap_step(h, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    A.aap_destroy(h)
+    return {"workload": "langevin_N2^20_L724_reflecting_dt0.01", "updates_per_s": p.n * steps / (ms / 1e3),
+            "ms_per_step": ms / steps, "steps": steps}
+
+
+def _bench_ensemble(A, W, torch, stream, steps):
+    """256 Vicsek replicas (N log-uniform 2^10..2^18, rho in {0.5,1,2,4}, eta in
+    [0.1,0.7]): one batched, graph-replayed launch per step vs the same replicas
+    run one after another as standalone systems with the same tile shapes."""
+    import numpy as np
+
+    ps = W.ensemble_replicas(count=256, seed=7)
+    ntot = sum(p.n for p in ps)
+    e = A.aap_ens_create(ps, stream.cuda_stream)
+    pol, trial = A.aap_ens_autotune(e, 10)
+    A.aap_ens_step(e, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    A.aap_ens_step(e, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_ens = e0.elapsed_time(e1)
+    layouts = [A.aap_ens_get_layout(e, r) for r in range(len(ps))]
+    ms_seq = 0.0
+    exact = True
+    for r, p in enumerate(ps):
+        q = A.aap_params_default()
+        for f, _ in A.aap_params._fields_:
+            setattr(q, f, getattr(p, f))
+        q.tile_w, q.tile_h, q.threads = layouts[r].tile_w, layouts[r].tile_h, layouts[r].threads
+        h = A.aap_create(q, stream.cuda_stream)
+        A.aap_step(h, 3)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        A.aap_step(h, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_seq += e0.elapsed_time(e1)
+        if r in (0, 255):
+            a = A.aap_get_state(h, q.n)
+            b = A.aap_ens_get_state(e, r, q.n)
+            exact = exact and all(np.array_equal(u, v) for u, v in zip(a, b))
+        A.aap_destroy(h)
+    A.aap_ens_destroy(e)
+    return {"workload": "256 Vicsek replicas, N log-uniform [2^10,2^18], rho {0.5,1,2,4}, eta U[0.1,0.7]",
+            "replicas": len(ps), "total_particles": ntot, "steps": steps,
+            "updates_per_s": ntot * steps / (ms_ens / 1e3),
+            "sequential_updates_per_s": ntot * steps / (ms_seq / 1e3),
+            "speedup_vs_sequential": ms_seq / ms_ens, "policy": int(pol),
+            "policy_ms_per_step": [round(float(v), 4) for v in trial],
+            "phi_error": 0.0 if exact else None, "replicas_bitwise_equal_checked": [0, 255]}
+
+
+def _bench_surrogate(A, W, torch, stream, train_traj=32, iters=300, horizon=100):
+    """Train the field surrogate on Vicsek N = 524,288, L = 512 trajectories
+    (eta in [0.3, 0.5]) coarse-grained to 128 x 128 x 3 every 10 steps, then
+    advance held-out states by `horizon` particle steps with the surrogate
+    and with the particle method; report speedup and errors in p and S(k)."""
+    import numpy as np
+
+    nb, every = 128, 10
+    g = np.random.default_rng(3)
+    etas = g.uniform(0.3, 0.5, train_traj)
+    ps = [W.surrogate_training(eta=float(etas[r]), seed=10000 + r) for r in range(train_traj)]
+    e = A.aap_ens_create(ps, stream.cuda_stream)
+    A.aap_ens_step(e, 100)
+    nfr = 40
+    frames = torch.zeros(train_traj, nfr, 3, nb, nb, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(nfr):
+        for r in range(train_traj):
+            A.aap_ens_coarse_grain(e, r, nb, nb, frames[r, k].data_ptr())
+        A.aap_ens_step(e, every)
+    stream.synchronize()
+    A.aap_ens_destroy(e)
+    t_data = time.perf_counter() - t0
+    B = 32
+    s = A.aap_sur_create(A.aap_sur_params_default(nbx=nb, nby=nb, max_batch=B, lr=2e-3, seed=11),
+                         stream.cuda_stream)
+    xin = torch.zeros(B, 3, nb, nb, device="cuda")
+    xtg = torch.zeros_like(xin)
+    eta_t = torch.zeros(B, device="cuda")
+    etas_t = torch.tensor(etas, dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    loss = 0.0
+    for it in range(iters):
+        ri = torch.from_numpy(g.integers(0, train_traj, B)).cuda()
+        ki = torch.from_numpy(g.integers(0, nfr - 1, B)).cuda()
+        xin.copy_(frames[ri, ki])
+        xtg.copy_(frames[ri, ki + 1])
+        eta_t.copy_(etas_t[ri])
+        loss = A.aap_sur_train_step(s, xin.data_ptr(), xtg.data_ptr(), eta_t.data_ptr(), B)
+    t_train = time.perf_counter() - t0
+    # held-out evaluation
+    errs, keep_errs, sk_errs, sk_keep, t_part, t_sur = [], [], [], [], 0.0, 0.0
+    apps = horizon // every
+    f0 = torch.zeros(1, 3, nb, nb, device="cuda")
+    ft = torch.zeros_like(f0)
+    fp = torch.zeros_like(f0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    area = (512.0 / nb) ** 2
+    for j, eta in enumerate((0.35, 0.4, 0.45, 0.5)):
+        p = W.surrogate_training(eta=eta, seed=20000 + j)
+        h = A.aap_create(p, stream.cuda_stream)
+        A.aap_step(h, 100)
+        A.aap_coarse_grain(h, nb, nb, f0.data_ptr())
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        A.aap_step(h, horizon)
+        A.aap_coarse_grain(h, nb, nb, ft.data_ptr())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_part += ev0.elapsed_time(ev1)
+        ed = torch.full((1,), eta, device="cuda")
+        ev0.record(stream)
+        A.aap_sur_predict(s, f0.data_ptr(), ed.data_ptr(), 1, apps, fp.data_ptr())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_sur += ev0.elapsed_time(ev1)
+        A.aap_destroy(h)
+        a_t, a_p, a_0 = (v.cpu().numpy()[0].astype(np.float64) for v in (ft, fp, f0))
+        phi = lambda f: np.hypot(f[1].sum(), f[2].sum()) / f[0].sum()
+        errs.append(abs(phi(a_p) - phi(a_t)))
+        keep_errs.append(abs(phi(a_0) - phi(a_t)))
+        s_t, s_p, s_0 = (_structure_factor(f[0] * area) for f in (a_t, a_p, a_0))
+        sk_errs.append(float(np.linalg.norm(s_p - s_t) / np.linalg.norm(s_t)))
+        sk_keep.append(float(np.linalg.norm(s_0 - s_t) / np.linalg.norm(s_t)))
+    A.aap_sur_destroy(s)
+    return {"workload": "Vicsek N=524288 L=512 eta[0.3,0.5] -> 128x128x3 fields, 4-layer 3x3 conv 32 ch",
+            "train_trajectories": train_traj, "frames_per_trajectory": nfr, "iterations": iters,
+            "batch": B, "final_loss": loss, "data_s": t_data, "train_s": t_train,
+            "horizon_steps": horizon, "speedup_vs_particles": t_part / t_sur,
+            "particle_ms": t_part / 4, "surrogate_ms": t_sur / 4,
+            "phi_abs_error": float(np.mean(errs)), "phi_abs_error_keep_fields": float(np.mean(keep_errs)),
+            "sk_rel_l2_error": float(np.mean(sk_errs)), "sk_rel_l2_error_keep_fields": float(np.mean(sk_keep))}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the oracle on the host cores (rank 0 only)."""
     if rank != 0:
@@ -288,14 +454,20 @@ def main():
 
     extras = {}
     if not args.no_extras and world == 1:
+        from paper_2211_15630_gb300 import workloads as W
+
         for eta in (0.2, 0.7):
             if abs(eta - args.eta) < 1e-9:
                 continue
             pe, he = make(eta, 1)
             A.aap_step(he, args.warmup)
             msx = timed(he, max(args.steps // 4, 50))
-            extras[f"eta_{eta}"] = args.n * max(args.steps // 4, 50) / (msx / 1e3)
+            extras[f"vicsek_eta_{eta}_updates_per_s"] = args.n * max(args.steps // 4, 50) / (msx / 1e3)
             A.aap_destroy(he)
+        extras["brownian"] = _bench_brownian(A, W, torch, stream, 500)
+        extras["ensemble"] = _bench_ensemble(A, W, torch, stream, 200)
+        with torch.cuda.stream(stream):     # torch copies and library calls share one stream
+            extras["surrogate"] = _bench_surrogate(A, W, torch, stream)
 
     if rank != 0:
         if dist:

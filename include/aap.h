@@ -286,6 +286,10 @@ int aap_ens_results(aap_ens *e, int32_t r, aap_results *out);
 /* State of replica r, as aap_get_state.  Synchronises. */
 int aap_ens_get_state(aap_ens *e, int32_t r, double *x, double *y, float *theta, int64_t n);
 
+/* Coarse-grained fields of replica r into a caller-owned DEVICE buffer, as
+ * aap_coarse_grain (enqueued on the ensemble's stream, no sync). */
+int aap_ens_coarse_grain(aap_ens *e, int32_t r, int32_t nbx, int32_t nby, float *dev_out);
+
 /* Layout of replica r (its tile shape reproduces the replica standalone). */
 int aap_ens_get_layout(aap_ens *e, int32_t r, aap_layout *out);
 

@@ -30,6 +30,7 @@ EXPORTS = (
     "aap_measure", "aap_get_results", "aap_clear_results", "aap_coarse_grain",
     "aap_ens_create", "aap_ens_step", "aap_ens_measure", "aap_ens_phi_mean", "aap_ens_results",
     "aap_ens_get_state", "aap_ens_get_layout", "aap_ens_autotune", "aap_ens_info", "aap_ens_destroy",
+    "aap_ens_coarse_grain",
     "aap_sur_last_error", "aap_sur_params_default", "aap_sur_create", "aap_sur_destroy",
     "aap_sur_param_count", "aap_sur_get_params", "aap_sur_set_params", "aap_sur_get_grads",
     "aap_sur_predict", "aap_sur_train_step", "aap_conv3x3_forward", "aap_conv3x3_backward_data",
@@ -125,6 +126,7 @@ def load(path: str = LIB_PATH):
         "aap_ens_autotune": (C.c_int, [vp, i32, vp, vp]),
         "aap_ens_info": (C.c_int, [vp, vp, vp]),
         "aap_ens_destroy": (C.c_int, [vp]),
+        "aap_ens_coarse_grain": (C.c_int, [vp, i32, i32, i32, vp]),
         "aap_sur_last_error": (C.c_char_p, []),
         "aap_sur_params_default": (None, [P(aap_sur_params)]),
         "aap_sur_create": (C.c_int, [P(aap_sur_params), vp, P(vp)]),
@@ -314,6 +316,10 @@ def aap_ens_autotune(e, trial_steps: int):
     ms = np.zeros(8, np.float64)
     _check(load().aap_ens_autotune(e, int(trial_steps), C.byref(pol), _p(ms)))
     return pol.value, ms
+
+
+def aap_ens_coarse_grain(e, r: int, nbx: int, nby: int, dev_out_ptr: int) -> None:
+    _check(load().aap_ens_coarse_grain(e, int(r), int(nbx), int(nby), C.c_void_p(int(dev_out_ptr))))
 
 
 def aap_ens_destroy(e) -> None:

@@ -1176,6 +1176,13 @@ int aap_ens_get_state(aap_ens *e, int32_t r, double *x, double *y, float *theta,
     return aap_get_state(e->m[r], x, y, theta, n);
 }
 
+int aap_ens_coarse_grain(aap_ens *e, int32_t r, int32_t nbx, int32_t nby, float *dev_out)
+{
+    if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
+    if (r < 0 || r >= (int)e->m.size()) return fail(AAP_EINVAL, "replica index out of range");
+    return aap_coarse_grain(e->m[r], nbx, nby, dev_out);
+}
+
 int aap_ens_get_layout(aap_ens *e, int32_t r, aap_layout *out)
 {
     if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
