@@ -96,7 +96,9 @@ __device__ __forceinline__ void warp_insert(const Sys &S, int b, bool act, int d
 {
     const int lane = threadIdx.x & 31;
     const int key = act ? dtile * kCntStride + region : -1 - lane;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    // most warps send every lane to one region: skip the match in that case
+    const bool same = __all_sync(0xffffffffu, key == __shfl_sync(0xffffffffu, key, 0));
+    const unsigned peers = same ? 0xffffffffu : __match_any_sync(0xffffffffu, key);
     const int leader = __ffs(peers) - 1;
     int base = 0;
     if (act && lane == leader) base = atomicAdd(&S.cnt[b][key], __popc(peers));
@@ -420,9 +422,14 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
         }
         const int q = a + rank;
         float thv = A.rth[k];
-        if (MODEL == 1 && S.order != 1) thv *= (float)S.order;
         float sn, cs;
-        sincosf(thv, &sn, &cs);
+        if (MODEL == 1 && S.order != 1) {
+            thv *= (float)S.order;
+            sincosf(thv, &sn, &cs);
+        } else {
+            // |theta| <= pi: the hardware sine/cosine is within 2^-21.4 absolute
+            __sincosf(thv, &sn, &cs);
+        }
         const int flip = cf >> 14;
         if (flip & 1) {
             if (MODEL != 1 || (S.order & 1)) cs = -cs; else sn = -sn;
@@ -467,7 +474,7 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             if (MODEL != 1) {
                 // Eq. (collision_VM) / (collision_NVM) + noise; Eq. (streaming)
                 thn = atan2f(ss, sc) + S.omega_step + S.eta_pi * (2.0f * u0 - 1.0f);
-                sincosf(thn, &sn, &cn);
+                __sincosf(thn, &sn, &cn);
                 dX = __float2int_rn(S.kx * cn);
                 dY = __float2int_rn(S.ky * sn);
             } else {
@@ -508,7 +515,7 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             if (fy) { thn = -thn; sn = -sn; }
             if (thn >= AAP_PI_F || thn < -AAP_PI_F)
                 thn -= AAP_2PI_F * floorf((thn + AAP_PI_F) * (1.0f / AAP_2PI_F));
-            if (MODEL == 1) sincosf(thn, &sn, &cn);
+            if (MODEL == 1) __sincosf(thn, &sn, &cn);
             if (!isfinite(thn)) atomicOr(S.err, ERR_NAN);
             dtile = dty * S.ntx + dtx;
             region = region_of(Xn >> S.sx, Yn >> S.sy, twd, thd);
@@ -615,6 +622,9 @@ k_step(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_base,
             atomicAdd(&g_phase[9], (unsigned long long)(T.m > stage_cap));
         }
 #endif
+#ifdef AAP_PHASE_TIMING
+        const long long tb0 = clock64();
+#endif
         if (T.m <= stage_cap) {
             tile_body<NT, MODEL>(T, As, tb, step, spill_e, spill_s);
         } else if (T.m <= scratch_cap) {
@@ -622,6 +632,10 @@ k_step(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_base,
         } else if (threadIdx.x == 0) {
             atomicOr(T.S.err, ERR_STAGE | ERR_LOST);
         }
+#ifdef AAP_PHASE_TIMING
+        if (threadIdx.x == 0)
+            atomicAdd(&g_phase[T.m <= stage_cap ? 10 : 11], (unsigned long long)(clock64() - tb0));
+#endif
         __syncthreads();
     }
 }
