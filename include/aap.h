@@ -50,6 +50,7 @@ extern "C" {
 #define AAP_ENAN      (-5)   /* a non-finite value reached the state         */
 #define AAP_ESTATE    (-6)   /* handle in an unusable state (after a fault)  */
 #define AAP_EOVERFLOW (-7)   /* more particles in a tile than it can hold    */
+#define AAP_EIO       (-8)   /* a saved-state file could not be written/read */
 
 /* ---- models (Sec. 2) ----------------------------------------------------- */
 #define AAP_VM        0      /* Vicsek model, Eq. (collision_VM)              */
@@ -94,6 +95,11 @@ typedef struct aap_params {
                             256 or 512                                          */
     double   capacity;   /* tile-region capacity over the mean occupancy;
                             0 = automatic (4)                                   */
+    int32_t  binnum_theta;      /* bins of the orientation histogram over
+                                   [-pi, pi) (Sec. 3.4); 0 = 100, at most 512     */
+    int32_t  binnum_neighbors;  /* bins 0..binnum_neighbors-1 of the neighbour-
+                                   number histogram, the last collecting all
+                                   larger |Omega_i|; 0 = 100, at most 512         */
 } aap_params;
 
 /* Observables of the current state (Sec. 3.4). */
@@ -140,7 +146,7 @@ typedef struct aap_ens aap_ens;
 const char *aap_last_error(void);
 
 /* ABI version of this header (bumped on any incompatible change). */
-int32_t aap_abi_version(void);
+int32_t aap_abi_version(void);   /* 2 */
 
 /* Fill *p with this library's defaults: N = 1000, Lx = Ly = 32, R = 1, v = 0.5,
  * eta = 0.4, omega = 0, Gamma = 1, dt = 0.01, seed = 1, VM, order 1,
@@ -210,8 +216,30 @@ int aap_measure(aap_handle *h, int64_t nsteps);
  * aap_clear_results (like aappp_get_results, Sec. 4).  Synchronises. */
 int aap_get_results(aap_handle *h, aap_results *out);
 
-/* Forget the accumulated measurements. */
+/* Forget the accumulated measurements (moments and histograms). */
 int aap_clear_results(aap_handle *h);
+
+/* Normalised histograms of the measured states (Sec. 3.4): theta_hist[k] is the
+ * fraction of (particle, state) samples with theta in bin k of [-pi, pi)
+ * (nt must equal binnum_theta); nbr_hist[k] the fraction with |Omega_i| = k
+ * (the last bin: >= nn-1; nn must equal binnum_neighbors).  Either pointer may
+ * be NULL.  Synchronises. */
+int aap_get_histograms(aap_handle *h, double *theta_hist, int32_t nt, double *nbr_hist, int32_t nn);
+
+/* Save the system to a binary file (Sec. 4: the paper's program can save a
+ * simulation and load it later): parameters, step counter, state by particle
+ * id and the accumulated measurements (moments and histograms).  Little-endian
+ * layout: "AAPSAVE1", u32 version 1, u32 sizeof(aap_params), aap_params,
+ * i64 step, i64 N, x[N] f64, y[N] f64, theta[N] f32, 16 f64 sums, i32 bins
+ * theta, i32 bins |Omega|, u64 counts.  Synchronises.  AAP_EIO when the file
+ * cannot be written. */
+int aap_save(aap_handle *h, const char *path);
+
+/* Create a handle from a file written by aap_save, on `stream`: continuing it
+ * reproduces the trajectory of the saved handle bit for bit, and aap_get_results
+ * / aap_get_histograms keep the saved measurements.  AAP_EIO for a missing,
+ * foreign or truncated file; no handle is returned on error. */
+int aap_load(const char *path, void *stream, aap_handle **out);
 
 /* Coarse-grained fields of the current state into a caller-owned DEVICE
  * buffer dev_out of 3 * nbx * nby floats (e.g. a torch tensor's data_ptr()):

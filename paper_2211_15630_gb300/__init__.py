@@ -16,8 +16,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libaap.so")
 
-AAP_OK, AAP_EINVAL, AAP_ENOMEM, AAP_ECUDA, AAP_ETIMEOUT, AAP_ENAN, AAP_ESTATE, AAP_EOVERFLOW = (
-    0, -1, -2, -3, -4, -5, -6, -7)
+AAP_OK, AAP_EINVAL, AAP_ENOMEM, AAP_ECUDA, AAP_ETIMEOUT, AAP_ENAN, AAP_ESTATE, AAP_EOVERFLOW, AAP_EIO = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
 AAP_VM, AAP_LANGEVIN, AAP_NVM = 0, 1, 2
 AAP_H_INV_1PN, AAP_H_ONE = 0, 1
 AAP_FLAG_SPILLED = 1
@@ -27,7 +27,8 @@ EXPORTS = (
     "aap_last_error", "aap_abi_version", "aap_params_default", "aap_create", "aap_destroy",
     "aap_step", "aap_phi_trace", "aap_observe", "aap_get_state", "aap_set_state",
     "aap_step_neighbours", "aap_sync", "aap_get_layout", "aap_set_timing", "aap_get_timing",
-    "aap_measure", "aap_get_results", "aap_clear_results", "aap_coarse_grain",
+    "aap_measure", "aap_get_results", "aap_clear_results", "aap_coarse_grain", "aap_get_histograms",
+    "aap_save", "aap_load",
     "aap_ens_create", "aap_ens_step", "aap_ens_measure", "aap_ens_phi_mean", "aap_ens_results",
     "aap_ens_get_state", "aap_ens_get_layout", "aap_ens_autotune", "aap_ens_info", "aap_ens_destroy",
     "aap_ens_coarse_grain",
@@ -51,6 +52,7 @@ class aap_params(C.Structure):
         ("dt", C.c_double), ("seed", C.c_uint64), ("model", C.c_int32), ("order", C.c_int32),
         ("weight", C.c_int32), ("bx", C.c_int32), ("by", C.c_int32), ("tile_w", C.c_int32),
         ("tile_h", C.c_int32), ("threads", C.c_int32), ("capacity", C.c_double),
+        ("binnum_theta", C.c_int32), ("binnum_neighbors", C.c_int32),
     ]
 
 
@@ -115,6 +117,9 @@ def load(path: str = LIB_PATH):
         "aap_measure": (C.c_int, [vp, i64]),
         "aap_get_results": (C.c_int, [vp, P(aap_results)]),
         "aap_clear_results": (C.c_int, [vp]),
+        "aap_get_histograms": (C.c_int, [vp, vp, i32, vp, i32]),
+        "aap_save": (C.c_int, [vp, C.c_char_p]),
+        "aap_load": (C.c_int, [C.c_char_p, vp, P(vp)]),
         "aap_coarse_grain": (C.c_int, [vp, i32, i32, vp]),
         "aap_ens_create": (C.c_int, [vp, i32, vp, P(vp)]),
         "aap_ens_step": (C.c_int, [vp, i64]),
@@ -175,6 +180,18 @@ def aap_params_default(**kw) -> aap_params:
 def aap_create(params: aap_params, stream: int | None = None) -> C.c_void_p:
     h = C.c_void_p()
     _check(load().aap_create(C.byref(params), C.c_void_p(stream or 0), C.byref(h)))
+    return h
+
+
+def aap_save(h, path: str) -> None:
+    """Write the system (parameters, step, state, measurements) to `path`."""
+    _check(load().aap_save(h, os.fsencode(path)))
+
+
+def aap_load(path: str, stream: int | None = None) -> C.c_void_p:
+    """A new handle continuing the system saved in `path`."""
+    h = C.c_void_p()
+    _check(load().aap_load(os.fsencode(path), C.c_void_p(stream or 0), C.byref(h)))
     return h
 
 
@@ -251,6 +268,14 @@ def aap_get_results(h) -> aap_results:
     r = aap_results()
     _check(load().aap_get_results(h, C.byref(r)))
     return r
+
+
+def aap_get_histograms(h, nt: int, nn: int):
+    """Normalised (theta histogram [nt], |Omega| histogram [nn]) of the measured states."""
+    th = np.zeros(nt, np.float64)
+    nb = np.zeros(nn, np.float64)
+    _check(load().aap_get_histograms(h, _p(th), int(nt), _p(nb), int(nn)))
+    return th, nb
 
 
 def aap_clear_results(h) -> None:

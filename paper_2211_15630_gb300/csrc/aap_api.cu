@@ -163,6 +163,9 @@ int check_params(const aap_params *p)
         return fail(AAP_EINVAL, "threads must be 0, 256 or 512");
     if (!finite(p->capacity) || p->capacity < 0 || (p->capacity > 0 && p->capacity < 1))
         return fail(AAP_EINVAL, "capacity must be 0 (automatic) or >= 1");
+    if (p->binnum_theta < 0 || p->binnum_theta > aapk::kMaxBins || p->binnum_neighbors < 0 ||
+        p->binnum_neighbors > aapk::kMaxBins)
+        return fail(AAP_EINVAL, "binnum_theta and binnum_neighbors must be in [0, 512]");
     return AAP_OK;
 }
 
@@ -224,7 +227,8 @@ int set_capacity(aap_handle *h, double factor)
     L.model = p.model;
     L.stage_cap = scap;
     L.nce_max = nce;
-    const size_t smem = aapk::step_smem_bytes(scap, nce);
+    L.hist_words = (p.binnum_theta ? p.binnum_theta : 100) + (p.binnum_neighbors ? p.binnum_neighbors : 100);
+    const size_t smem = aapk::step_smem_bytes(scap, nce, L.hist_words);
     int bps = 0;
     AAP_CK(aapk::configure_step_kernel(L.model, L.threads, smem, &bps));
     if (bps < 1) return fail(AAP_EINVAL, "step kernel does not fit on an SM with this tiling");
@@ -376,6 +380,9 @@ int alloc_all(aap_handle *h)
     if ((rc = dev_alloc(h, &S.acc, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long)))) return rc;
     if ((rc = dev_alloc(h, &S.last, 4 * sizeof(double)))) return rc;
     if ((rc = dev_alloc(h, &S.stats, 16 * sizeof(double)))) return rc;
+    S.bins_theta = h->p.binnum_theta ? h->p.binnum_theta : 100;     // theta + |Omega| bins = L.hist_words
+    S.bins_nbr = h->p.binnum_neighbors ? h->p.binnum_neighbors : 100;
+    if ((rc = dev_alloc(h, &S.hist, (size_t)(S.bins_theta + S.bins_nbr) * sizeof(unsigned long long)))) return rc;
     if ((rc = dev_alloc(h, &S.err, sizeof(int)))) return rc;
     if (!h->member) {
         if ((rc = dev_alloc(h, &h->d_sys, sizeof(Sys)))) return rc;
@@ -400,6 +407,7 @@ int alloc_all(aap_handle *h)
     if ((rc = clear_buffers(h))) return rc;
     AAP_CK(cudaMemsetAsync(S.last, 0, 4 * sizeof(double), h->stream));
     AAP_CK(cudaMemsetAsync(S.stats, 0, 16 * sizeof(double), h->stream));
+    AAP_CK(cudaMemsetAsync(S.hist, 0, (size_t)(S.bins_theta + S.bins_nbr) * sizeof(unsigned long long), h->stream));
     S.meas_until = 0;
     if (!h->member) {
         AAP_CK(cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), h->stream));
@@ -705,6 +713,7 @@ int ens_combine(aap_ens *e)
     L.threads = e->params[0].threads ? e->params[0].threads : pol.threads;
     L.stage_cap = 64;
     L.nce_max = 9;
+    L.hist_words = 0;
     L.scratch_cap = 64;
     L.spill_list_cap = 16;
     long long total = 0;
@@ -713,6 +722,7 @@ int ens_combine(aap_ens *e)
         const aap_handle *h = e->m[r];
         L.stage_cap = std::max(L.stage_cap, h->L.stage_cap);
         L.nce_max = std::max(L.nce_max, h->L.nce_max);
+        L.hist_words = std::max(L.hist_words, h->L.hist_words);
         L.scratch_cap = std::max(L.scratch_cap, h->L.scratch_cap);
         L.spill_list_cap = std::max(L.spill_list_cap, h->L.spill_list_cap);
         total += h->hs.ntiles;
@@ -720,7 +730,7 @@ int ens_combine(aap_ens *e)
     }
     if (total >= (1ll << 30)) return fail(AAP_EINVAL, "too many tiles in the ensemble");
     AAP_CK(cudaMemcpy(e->d_tile_base, tb.data(), tb.size() * sizeof(int), cudaMemcpyHostToDevice));
-    const size_t smem = aapk::step_smem_bytes(L.stage_cap, L.nce_max);
+    const size_t smem = aapk::step_smem_bytes(L.stage_cap, L.nce_max, L.hist_words);
     int bps = 0;
     AAP_CK(aapk::configure_step_kernel(L.model, L.threads, smem, &bps));
     if (bps < 1) return fail(AAP_EINVAL, "step kernel does not fit on an SM for this ensemble");
@@ -811,11 +821,36 @@ cudaError_t read_phase_times(unsigned long long *out16);
 }
 #endif
 
+namespace {
+constexpr char kSaveMagic[8] = {'A', 'A', 'P', 'S', 'A', 'V', 'E', '1'};
+constexpr uint32_t kSaveVersion = 1;
+
+struct FileCloser {
+    FILE *f;
+    ~FileCloser()
+    {
+        if (f) std::fclose(f);
+    }
+};
+
+template <class T>
+bool put(FILE *f, const T *v, size_t n)
+{
+    return n == 0 || std::fwrite(v, sizeof(T), n, f) == n;
+}
+
+template <class T>
+bool get(FILE *f, T *v, size_t n)
+{
+    return n == 0 || std::fread(v, sizeof(T), n, f) == n;
+}
+}  // namespace
+
 extern "C" {
 
 const char *aap_last_error(void) { return g_err.c_str(); }
 
-int32_t aap_abi_version(void) { return 1; }
+int32_t aap_abi_version(void) { return 2; }
 
 void aap_params_default(aap_params *p)
 {
@@ -1050,6 +1085,115 @@ int aap_clear_results(aap_handle *h)
 {
     if (!h) return fail(AAP_EINVAL, "handle is NULL");
     AAP_CK(cudaMemsetAsync(h->hs.stats, 0, 16 * sizeof(double), h->stream));
+    AAP_CK(cudaMemsetAsync(h->hs.hist, 0, (size_t)(h->hs.bins_theta + h->hs.bins_nbr) * sizeof(unsigned long long),
+                           h->stream));
+    return AAP_OK;
+}
+
+int aap_get_histograms(aap_handle *h, double *theta_hist, int32_t nt, double *nbr_hist, int32_t nn)
+{
+    if (!h) return fail(AAP_EINVAL, "handle is NULL");
+    const Sys &S = h->hs;
+    if ((theta_hist && nt != S.bins_theta) || (nbr_hist && nn != S.bins_nbr))
+        return fail(AAP_EINVAL, "bin counts must equal binnum_theta / binnum_neighbors");
+    std::vector<unsigned long long> v((size_t)(S.bins_theta + S.bins_nbr));
+    AAP_CK(cudaMemcpyAsync(v.data(), S.hist, v.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    int rc = read_errors(h);
+    if (rc) return rc;
+    double tt = 0, tn = 0;
+    for (int k = 0; k < S.bins_theta; ++k) tt += (double)v[k];
+    for (int k = 0; k < S.bins_nbr; ++k) tn += (double)v[S.bins_theta + k];
+    if (theta_hist)
+        for (int k = 0; k < S.bins_theta; ++k) theta_hist[k] = tt > 0 ? (double)v[k] / tt : 0.0;
+    if (nbr_hist)
+        for (int k = 0; k < S.bins_nbr; ++k) nbr_hist[k] = tn > 0 ? (double)v[S.bins_theta + k] / tn : 0.0;
+    return AAP_OK;
+}
+
+// Saved-state file (little-endian): "AAPSAVE1", u32 version, u32 sizeof(aap_params),
+// aap_params, i64 step, i64 n, x[n] f64, y[n] f64, theta[n] f32, stats[16] f64,
+// i32 bins_theta, i32 bins_nbr, hist[bins_theta + bins_nbr] u64.
+
+int aap_save(aap_handle *h, const char *path)
+{
+    if (!h || !path) return fail(AAP_EINVAL, "NULL argument");
+    if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
+    const int64_t n = h->p.n;
+    std::vector<double> x((size_t)n), y((size_t)n);
+    std::vector<float> th((size_t)n);
+    int rc = aap_get_state(h, x.data(), y.data(), th.data(), n);
+    if (rc) return rc;
+    const Sys &S = h->hs;
+    double st[16];
+    std::vector<unsigned long long> hist((size_t)(S.bins_theta + S.bins_nbr));
+    AAP_CK(cudaMemcpyAsync(st, S.stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaMemcpyAsync(hist.data(), S.hist, hist.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           h->stream));
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    FileCloser fc{std::fopen(path, "wb")};
+    if (!fc.f) return fail(AAP_EIO, std::string("cannot open ") + path + " for writing");
+    const uint32_t ver = kSaveVersion, psz = (uint32_t)sizeof(aap_params);
+    const int64_t step = h->step;
+    const int32_t bins[2] = {S.bins_theta, S.bins_nbr};
+    bool ok = put(fc.f, kSaveMagic, 8) && put(fc.f, &ver, 1) && put(fc.f, &psz, 1) && put(fc.f, &h->p, 1) &&
+              put(fc.f, &step, 1) && put(fc.f, &n, 1) && put(fc.f, x.data(), x.size()) &&
+              put(fc.f, y.data(), y.size()) && put(fc.f, th.data(), th.size()) && put(fc.f, st, 16) &&
+              put(fc.f, bins, 2) && put(fc.f, hist.data(), hist.size());
+    ok = (std::fclose(fc.f) == 0) && ok;
+    fc.f = nullptr;
+    if (!ok) return fail(AAP_EIO, std::string("write to ") + path + " failed");
+    return AAP_OK;
+}
+
+int aap_load(const char *path, void *stream, aap_handle **out)
+{
+    if (!path || !out) return fail(AAP_EINVAL, "NULL argument");
+    *out = nullptr;
+    FileCloser fc{std::fopen(path, "rb")};
+    if (!fc.f) return fail(AAP_EIO, std::string("cannot open ") + path);
+    char magic[8];
+    uint32_t ver = 0, psz = 0;
+    aap_params p;
+    int64_t step = 0, n = 0;
+    if (!get(fc.f, magic, 8) || std::memcmp(magic, kSaveMagic, 8) != 0)
+        return fail(AAP_EIO, std::string(path) + " is not a saved state");
+    if (!get(fc.f, &ver, 1) || ver != kSaveVersion || !get(fc.f, &psz, 1) || psz != sizeof(aap_params))
+        return fail(AAP_EIO, std::string(path) + ": unsupported version or parameter layout");
+    if (!get(fc.f, &p, 1) || !get(fc.f, &step, 1) || !get(fc.f, &n, 1) || n != p.n || n < 0 || step < 0)
+        return fail(AAP_EIO, std::string(path) + ": truncated or inconsistent header");
+    std::vector<double> x((size_t)n), y((size_t)n);
+    std::vector<float> th((size_t)n);
+    double st[16];
+    int32_t bins[2];
+    if (!get(fc.f, x.data(), x.size()) || !get(fc.f, y.data(), y.size()) || !get(fc.f, th.data(), th.size()) ||
+        !get(fc.f, st, 16) || !get(fc.f, bins, 2))
+        return fail(AAP_EIO, std::string(path) + ": truncated");
+    if (bins[0] < 1 || bins[0] > aapk::kMaxBins || bins[1] < 1 || bins[1] > aapk::kMaxBins)
+        return fail(AAP_EIO, std::string(path) + ": bad histogram size");
+    std::vector<unsigned long long> hist((size_t)(bins[0] + bins[1]));
+    if (!get(fc.f, hist.data(), hist.size())) return fail(AAP_EIO, std::string(path) + ": truncated");
+    aap_handle *h = nullptr;
+    int rc = aap_create(&p, stream, &h);
+    if (rc) return rc;
+    if (h->hs.bins_theta != bins[0] || h->hs.bins_nbr != bins[1]) {
+        aap_destroy(h);
+        return fail(AAP_EIO, std::string(path) + ": histogram size does not match its parameters");
+    }
+    if ((rc = aap_set_state(h, x.data(), y.data(), th.data(), n, step))) {
+        aap_destroy(h);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->hs.stats, st, sizeof(st), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->hs.hist, hist.data(), hist.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        aap_destroy(h);
+        return fail(AAP_ECUDA, std::string("restoring measurements: ") + cudaGetErrorString(e));
+    }
+    *out = h;
     return AAP_OK;
 }
 

@@ -32,6 +32,7 @@ constexpr float kFixStepF = 1073741824.0f;  // 2^30: scale of the per-step sums
 constexpr double kFixStep = 1073741824.0;
 constexpr int kSegs = 25;           // 9 own regions + 16 halo regions
 constexpr int kMaxTile = 64;        // largest tile side in cells
+constexpr int kMaxBins = 512;       // histogram bins (each of theta and |Omega|)
 
 // error bits (Sys::err)
 enum : int {
@@ -80,6 +81,8 @@ struct Sys {
                                 //      state before it; step
     double *stats;              // [16]: sums of p^k, q^k, nbar^k (k = 1..4), count
     long long meas_until;       // steps t < meas_until add state t to stats
+    unsigned long long *hist;   // [bins_theta + bins_nbr] measured histograms
+    int bins_theta, bins_nbr;
     int *nbr_out;               // optional |Omega_i| by particle id
     int *err;
 };
@@ -147,18 +150,22 @@ struct Tables {
     int *hist;                  // [nce]
     int *cstart;                // [nce + 1]
     int *rowpre;                // [kMaxTile + 1]
+    int *mhist;                 // [bins_theta + bins_nbr] measured theta / |Omega| counts of the tile
 };
 
-__host__ __device__ inline size_t table_bytes(int nce)
+// hist_words: bins_theta + bins_nbr of the widest system run by the launch.
+__host__ __device__ inline size_t table_bytes(int nce, int hist_words)
 {
-    return (size_t)round_up(nce, 4) * 4 + (size_t)round_up(nce + 1, 4) * 4 + (kMaxTile + 4) * 4;
+    return (size_t)round_up(nce, 4) * 4 + (size_t)round_up(nce + 1, 4) * 4 + (kMaxTile + 4) * 4 +
+           (size_t)round_up(hist_words, 4) * 4;
 }
 
 __host__ __device__ inline void carve_tables(Tables &t, unsigned char *p, int nce)
 {
     t.hist = (int *)p;   p += (size_t)round_up(nce, 4) * 4;
     t.cstart = (int *)p; p += (size_t)round_up(nce + 1, 4) * 4;
-    t.rowpre = (int *)p;
+    t.rowpre = (int *)p; p += (kMaxTile + 4) * 4;
+    t.mhist = (int *)p;
 }
 
 // Spill-match list (entry, segment) kept in the block's global scratch.

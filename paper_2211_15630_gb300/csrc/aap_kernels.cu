@@ -201,6 +201,8 @@ __device__ __forceinline__ void tile_setup(TileCtx &T, const Tables &tb, int cur
         T.n_spill = 0;
     }
     for (int i = tid; i < nce_max; i += NT) tb.hist[i] = 0;
+    if (T.S.meas_until > 0)
+        for (int i = tid; i < S.bins_theta + S.bins_nbr; i += NT) tb.mhist[i] = 0;
     if (tid < kSegs) {
         int bxo, byo, rx = -1, ry = -1;
         if (tid < 9) {
@@ -448,6 +450,7 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
     const int n_own = T.n_own;
     const float r2 = S.r2;
     const int TWs = tw << S.sx, THs = th << S.sy;
+    const bool measure = step < S.meas_until;   // on-the-fly histograms (Sec. 3.4)
     long long acc_c = 0, acc_s = 0, acc_n = 0, acc_c2 = 0, acc_s2 = 0;
     for (int base = 0; base < n_own; base += NT) {
         const int o = base + tid;
@@ -466,6 +469,12 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             int cnt;
             neighbour_sum<MODEL>(A.P, tb.cstart, ec, W2, pi, r2, sc, ss, cnt);
             const int nb = cnt - 1;          // the particle itself was counted
+            if (measure) {
+                int bt = (int)floorf((thi + AAP_PI_F) * ((float)S.bins_theta * (1.0f / AAP_2PI_F)));
+                bt = min(max(bt, 0), S.bins_theta - 1);
+                atomicAdd(&tb.mhist[bt], 1);
+                atomicAdd(&tb.mhist[S.bins_theta + min(nb, S.bins_nbr - 1)], 1);
+            }
             uint32_t c4[4] = {id, (uint32_t)step, (uint32_t)((unsigned long long)step >> 32), 0u};
             philox4x32_10(c4, S.seed_lo, S.seed_hi);
             const float u0 = u01f(c4[0]);
@@ -549,6 +558,10 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
         for (int w = 0; w < NT / 32; ++w) v += T.red[tid][w];
         unsigned long long *slot = S.acc + ((size_t)cur * kAccSlots + (T.tile & (kAccSlots - 1))) * kAccWords;
         atomicAdd(slot + tid, (unsigned long long)v);
+    }
+    if (measure) {
+        for (int i = tid; i < S.bins_theta + S.bins_nbr; i += NT)
+            if (tb.mhist[i]) atomicAdd(S.hist + i, (unsigned long long)tb.mhist[i]);
     }
     PHASE_MARK(5);
 }
@@ -882,12 +895,15 @@ __global__ void k_coarse_finish(const unsigned long long *acc, int nbx, int nby,
 }
 
 // --------------------------------------------------------------- launchers --
-size_t step_smem_bytes(int stage_cap, int nce_max) { return stage_bytes(stage_cap) + table_bytes(nce_max); }
+size_t step_smem_bytes(int stage_cap, int nce_max, int hist_words)
+{
+    return stage_bytes(stage_cap) + table_bytes(nce_max, hist_words);
+}
 
 template <int NT, int MODEL>
 static cudaError_t launch_step_t(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev)
 {
-    const size_t smem = step_smem_bytes(L.stage_cap, L.nce_max);
+    const size_t smem = step_smem_bytes(L.stage_cap, L.nce_max, L.hist_words);
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
     k_step<NT, MODEL><<<L.grid_step, NT, smem, st>>>(L.sys, L.nsys, L.tile_base, L.ctl, L.stage_cap,

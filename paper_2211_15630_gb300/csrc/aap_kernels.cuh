@@ -22,10 +22,11 @@ struct LaunchCfg {
     int threads;                 // 256 or 512
     int stage_cap;               // particles staged in shared memory
     int nce_max;                 // cells of the largest tile plus its ring
+    int hist_words;              // histogram bins (theta + |Omega|) of the widest system
     int grid_step, grid_finish;
 };
 
-size_t step_smem_bytes(int stage_cap, int nce_max);
+size_t step_smem_bytes(int stage_cap, int nce_max, int hist_words);
 // Set the dynamic shared-memory limit of the step kernel and report how many
 // of its blocks fit on one SM.
 cudaError_t configure_step_kernel(int model, int threads, size_t smem_bytes, int *blocks_per_sm);

@@ -685,8 +685,6 @@ int aap_sur_train_step(aap_sur *s, const float *dev_in, const float *dev_target,
                                           s->loss_part, s->dout);
     SCK(cudaGetLastError());
     float *g = s->g;
-    const float *bias_none = nullptr;
-    (void)bias_none;
     // layer 4: weight gradient from a[2] and dout (16-channel pixels, 8 used);
     // data gradient through the flipped weights, masked by ReLU(a[2]) > 0
     SCK((conv_dw<32, 8>(s->a[2], s->dout, 16, batch, H, W, s->part, g + s->woff[3], g + s->boff[3], st)));

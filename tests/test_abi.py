@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_defaults(lib):
-    assert A.aap_abi_version() == 1
+    assert A.aap_abi_version() == 2
     p = A.aap_params_default()
     assert (p.n, p.lx, p.ly, p.r, p.v, p.eta, p.model, p.order, p.weight) == (
         1000, 32.0, 32.0, 1.0, 0.5, 0.4, A.AAP_VM, 1, A.AAP_H_INV_1PN)
@@ -49,6 +49,7 @@ def test_abi_version_and_defaults(lib):
     (dict(model=9), "model"), (dict(eta=-0.1), "eta"), (dict(model=1, dt=-1.0), "dt"),
     (dict(order=0), "order"), (dict(weight=5), "weight"), (dict(threads=96), "threads"),
     (dict(tile_w=4), "tile_w"), (dict(capacity=0.5), "capacity"), (dict(r=float("inf")), "finite"),
+    (dict(binnum_theta=513), "binnum"), (dict(binnum_neighbors=-1), "binnum"),
 ])
 def test_invalid_parameters(lib, kw, frag):
     with pytest.raises(A.AapError) as e:
@@ -66,3 +67,19 @@ def test_null_arguments(lib):
     assert lib.aap_destroy(None) == A.AAP_OK
     assert b"NULL" in lib.aap_last_error() or lib.aap_last_error() == b""
     del C
+
+
+def test_load_rejects_missing_and_foreign_files(lib, tmp_path):
+    with pytest.raises(A.AapError) as e:
+        A.aap_load(str(tmp_path / "absent.aap"))
+    assert e.value.code == A.AAP_EIO
+    junk = tmp_path / "junk.aap"
+    junk.write_bytes(b"not a state file at all")
+    with pytest.raises(A.AapError) as e:
+        A.aap_load(str(junk))
+    assert e.value.code == A.AAP_EIO and "not a saved state" in str(e.value)
+    trunc = tmp_path / "trunc.aap"
+    trunc.write_bytes(b"AAPSAVE1" + (1).to_bytes(4, "little"))
+    with pytest.raises(A.AapError) as e:
+        A.aap_load(str(trunc))
+    assert e.value.code == A.AAP_EIO

@@ -5,7 +5,7 @@ import pytest
 
 import paper_2211_15630_gb300 as A
 from paper_2211_15630_gb300 import workloads as W
-from tests.gpu_helpers import compare_one_step, params
+from tests.gpu_helpers import compare_one_step, oracle_model, params
 
 pytestmark = pytest.mark.gpu
 
@@ -176,5 +176,89 @@ def test_brownian_workload_one_step(lib, oracle):
         A.aap_step(h, 3)
         idx = np.random.default_rng(2).choice(p.n, 3000, replace=False)
         compare_one_step(oracle, p, h, idx=idx)
+    finally:
+        A.aap_destroy(h)
+
+
+def _theta_bins(th, bins):
+    """Bin of theta in [-pi, pi) with the kernel's FP32 operations (an integer
+    decided by floating point is decided in the same precision on both sides)."""
+    t = th.astype(np.float32)
+    k = np.float32(bins) * (np.float32(1.0) / np.float32(6.28318530717959))
+    b = np.floor((t + np.float32(3.14159265358979)) * k).astype(np.int64)
+    return np.clip(b, 0, bins - 1)
+
+
+@pytest.mark.parametrize("bins_nbr", [64, 5])
+def test_histograms_match_sampled_states(lib, oracle, bins_nbr):
+    """Histograms of theta and of |Omega_i| over the measured states t0 ..
+    t0+n-1 (Sec. 3.4) equal those of the same states read back one by one:
+    theta bins exactly, neighbour numbers against the oracle's counts up to
+    pairs within 1e-5 of the radius; the last neighbour bin collects the rest."""
+    p = params(n=12000, lx=80.0, ly=80.0, eta=0.35, seed=17)
+    p.binnum_theta, p.binnum_neighbors = 36, bins_nbr
+    m = oracle_model(oracle, p)
+    h1, h2 = A.aap_create(p), A.aap_create(p)
+    nmeas = 6
+    try:
+        A.aap_step(h1, 9)
+        A.aap_step(h2, 9)
+        A.aap_measure(h1, nmeas)
+        th_h, nb_h = A.aap_get_histograms(h1, 36, bins_nbr)
+        res = A.aap_get_results(h1)
+        ct = np.zeros(36, np.int64)
+        cn = np.zeros(bins_nbr, np.int64)
+        amb_total = 0
+        for _ in range(nmeas):
+            x, y, th = A.aap_get_state(h2, p.n)
+            step = A.aap_observe(h2).step
+            ct += np.bincount(_theta_bins(th, 36), minlength=36)
+            _, _, _, nb, _, amb = oracle.step(m, x, y, th.astype(np.float64), step)
+            amb_total += int((amb != 0).sum())
+            cn += np.bincount(np.minimum(nb, bins_nbr - 1), minlength=bins_nbr)
+            A.aap_step(h2, 1)
+        total = p.n * nmeas
+        assert np.array_equal(np.rint(th_h * total).astype(np.int64), ct)
+        assert abs(th_h.sum() - 1) < 1e-12 and abs(nb_h.sum() - 1) < 1e-12
+        got = np.rint(nb_h * total).astype(np.int64)
+        assert np.abs(got - cn).sum() <= 2 * amb_total
+        if bins_nbr == 64 and cn[-1] == 0:
+            # unclipped: the histogram's mean is the measured mean neighbour number
+            assert abs((np.arange(bins_nbr) * nb_h).sum() - res.nbar[0]) < 1e-9
+        A.aap_clear_results(h1)
+        th0, nb0 = A.aap_get_histograms(h1, 36, bins_nbr)
+        assert not th0.any() and not nb0.any()
+        with pytest.raises(A.AapError):
+            A.aap_get_histograms(h1, 35, bins_nbr)
+    finally:
+        A.aap_destroy(h1)
+        A.aap_destroy(h2)
+
+
+def test_save_load_continues_bitwise(lib, tmp_path):
+    """A system saved after a measurement and loaded into a new handle carries
+    on bit for bit, with the saved moments and histograms."""
+    p = params(n=25000, lx=110.0, ly=110.0, eta=0.3, seed=23, model=A.AAP_LANGEVIN, dt=0.1, v=0.5)
+    p.binnum_theta, p.binnum_neighbors = 24, 40
+    h = A.aap_create(p)
+    path = str(tmp_path / "sys.aap")
+    try:
+        A.aap_step(h, 7)
+        A.aap_measure(h, 5)
+        A.aap_save(h, path)
+        h2 = A.aap_load(path)
+        try:
+            r1, r2 = A.aap_get_results(h), A.aap_get_results(h2)
+            assert r1.samples == r2.samples == 5 and list(r1.p) == list(r2.p) and list(r1.nbar) == list(r2.nbar)
+            for u, v in zip(A.aap_get_histograms(h, 24, 40), A.aap_get_histograms(h2, 24, 40)):
+                assert np.array_equal(u, v)
+            assert A.aap_observe(h2).step == A.aap_observe(h).step == 12
+            A.aap_step(h, 9)
+            A.aap_step(h2, 9)
+            for u, v in zip(A.aap_get_state(h, p.n), A.aap_get_state(h2, p.n)):
+                assert np.array_equal(u, v)
+            assert A.aap_observe(h).phi == A.aap_observe(h2).phi
+        finally:
+            A.aap_destroy(h2)
     finally:
         A.aap_destroy(h)
