@@ -46,7 +46,7 @@ class Params(C.Structure):
         ("v", C.c_double), ("eta", C.c_double), ("omega", C.c_double),
         ("gamma", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64),
         ("model", C.c_int32), ("order", C.c_int32), ("weight", C.c_int32),
-        ("bx", C.c_int32), ("by", C.c_int32), ("self_image", C.c_int32),
+        ("bx", C.c_int32), ("by", C.c_int32), ("self_image", C.c_int32), ("kn", C.c_int32),
     ]
 
 
@@ -70,11 +70,12 @@ class Model:
     bx: int = 0
     by: int = 0
     self_image: int = 1
+    kn: int = 0
 
     def c(self) -> Params:
         return Params(self.n, self.lx, self.ly, self.r, self.v, self.eta, self.omega,
                       self.gamma, self.dt, self.seed, self.model, self.order, self.weight,
-                      self.bx, self.by, self.self_image)
+                      self.bx, self.by, self.self_image, self.kn)
 
 
 _lib = None
@@ -97,6 +98,7 @@ def lib():
             "orc_geometry": (C.c_int, [P(Params), vp, vp, vp, vp]),
             "orc_neighbours_brute": (i64, [P(Params), vp, vp, i64, vp, vp, i64]),
             "orc_counts_brute": (None, [P(Params), vp, vp, vp]),
+            "orc_knn": (i64, [P(Params), vp, vp, i64, i64, vp, vp, vp]),
             "orc_counts_cell": (C.c_int, [P(Params), vp, vp, vp]),
             "orc_step_subset": (C.c_int, [P(Params), vp, vp, vp, u64, vp, i64, vp, vp, vp,
                                           vp, vp, vp, d]),
@@ -163,6 +165,18 @@ def neighbours_brute(m: Model, x, y, i: int, cap: int = 4096):
     cnt = lib().orc_neighbours_brute(C.byref(p), _p(x), _p(y), i, _p(j), _p(img), cap)
     k = min(cnt, cap)
     return cnt, j[:k].copy(), img[:k].copy()
+
+
+def knn(m: Model, x, y, i: int, k: int):
+    """The k nearest candidates of particle i (Sec. 2.3): (j, image code, distance),
+    ascending; image = (ix+1) + 3 (iy+1)."""
+    x = np.ascontiguousarray(x, np.float64); y = np.ascontiguousarray(y, np.float64)
+    j = np.zeros(k, np.int64); img = np.zeros(k, np.int32); d = np.zeros(k)
+    p = m.c()
+    cnt = lib().orc_knn(C.byref(p), _p(x), _p(y), int(i), int(k), _p(j), _p(img), _p(d))
+    if cnt < 0:
+        raise MemoryError("orc_knn")
+    return j[:cnt].copy(), img[:cnt].copy(), d[:cnt].copy()
 
 
 def counts_brute(m: Model, x, y) -> np.ndarray:

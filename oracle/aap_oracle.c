@@ -239,6 +239,128 @@ typedef struct {
     int     amb;        /* a candidate within `band` of R                      */
 } accum;
 
+/* One neighbour with (image) orientation tj joins the sums of particle i. */
+static void add_neighbour(const orc_params *p, double ti, double tj, accum *a)
+{
+    a->n++;
+    if (p->model == 0) {                 /* Eq. (collision_VM) */
+        a->sx += cos(tj);
+        a->sy += sin(tj);
+    } else if (p->model == 2) {          /* Eq. (collision_NVM), sign(0) = +1 */
+        double sgn = cos(ti - tj) >= 0.0 ? 1.0 : -1.0;
+        double tn = tj + 0.5 * ORC_PI * (1.0 - sgn);
+        a->sx += cos(tn);
+        a->sy += sin(tn);
+    } else {                             /* Eq. (Langevin_dynamics) */
+        a->t += sin((double)p->order * (tj - ti));
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Metric-free neighbourhoods (Sec. 2.3): the k nearest particles.  This is
+ * the definition written out by brute force over every particle and image;
+ * the cell rings the paper describes (Sec. 3.3) only make it faster.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double  d2;
+    int64_t j;
+    int32_t img;
+} knn_cand;
+
+static int cand_less(double d2, int64_t j, int32_t img, const knn_cand *b)
+{
+    if (d2 != b->d2) return d2 < b->d2;
+    if (j != b->j) return j < b->j;
+    return img < b->img;
+}
+
+/* Image codes of particle j along one axis: the nearest periodic copy, or
+ * all three copies at a reflecting axis. */
+static int axis_codes(double ci, double cj, double L, int reflecting, int codes[3])
+{
+    if (reflecting) {
+        codes[0] = -1; codes[1] = 0; codes[2] = 1;
+        return 3;
+    }
+    int best = 0;
+    double bd = fabs(ci - cj);
+    if (fabs(ci - (cj - L)) < bd) { best = -1; bd = fabs(ci - (cj - L)); }
+    if (fabs(ci - (cj + L)) < bd) { best = 1; }
+    codes[0] = best;
+    return 1;
+}
+
+static int64_t knn_collect(const orc_params *p, const double *x, const double *y, int64_t i,
+                           int64_t m, knn_cand *out)
+{
+    int64_t cnt = 0;
+    if (m <= 0) return 0;
+    for (int64_t j = 0; j < p->n; ++j) {
+        int cx[3], cy[3];
+        int nx = axis_codes(x[i], x[j], p->lx, p->bx, cx);
+        int ny = axis_codes(y[i], y[j], p->ly, p->by, cy);
+        for (int b = 0; b < ny; ++b) {
+            for (int a = 0; a < nx; ++a) {
+                int ix = cx[a], iy = cy[b];
+                if (j == i && ix == 0 && iy == 0) continue;
+                if (j == i && !p->self_image) continue;
+                double dx = x[i] - image_coord(x[j], ix, p->lx, p->bx);
+                double dy = y[i] - image_coord(y[j], iy, p->ly, p->by);
+                double d2 = dx * dx + dy * dy;
+                int32_t img = (ix + 1) + 3 * (iy + 1);
+                if (cnt == m && !cand_less(d2, j, img, &out[m - 1])) continue;
+                int64_t s = cnt < m ? cnt++ : m - 1;
+                while (s > 0 && cand_less(d2, j, img, &out[s - 1])) {
+                    out[s] = out[s - 1];
+                    --s;
+                }
+                out[s].d2 = d2;
+                out[s].j = j;
+                out[s].img = img;
+            }
+        }
+    }
+    return cnt;
+}
+
+int64_t orc_knn(const orc_params *p, const double *x, const double *y, int64_t i, int64_t m,
+                int64_t *j_out, int32_t *img_out, double *d_out)
+{
+    if (m <= 0) return 0;
+    knn_cand *c = (knn_cand *)malloc((size_t)m * sizeof(knn_cand));
+    if (!c) return -1;
+    int64_t cnt = knn_collect(p, x, y, i, m, c);
+    for (int64_t s = 0; s < cnt; ++s) {
+        if (j_out) j_out[s] = c[s].j;
+        if (img_out) img_out[s] = c[s].img;
+        if (d_out) d_out[s] = sqrt(c[s].d2);
+    }
+    free(c);
+    return cnt;
+}
+
+/* Sums over the k nearest (h = 1 is applied by the caller, Sec. 2.3). */
+static void gather_knn(const orc_params *p, const double *x, const double *y, const double *th,
+                       int64_t i, double band, accum *a)
+{
+    const double ti = th[i];
+    a->n = 0;
+    a->sx = cos(ti);
+    a->sy = sin(ti);
+    a->t = 0.0;
+    a->amb = 0;
+    const int64_t k = p->kn;
+    knn_cand *c = (knn_cand *)malloc((size_t)(k + 1) * sizeof(knn_cand));
+    if (!c) { a->amb = 1; return; }
+    int64_t cnt = knn_collect(p, x, y, i, k + 1, c);
+    if (cnt > k && sqrt(c[k].d2) - sqrt(c[k - 1].d2) < band) a->amb = 1;
+    for (int64_t s = 0; s < cnt && s < k; ++s) {
+        int ix = c[s].img % 3 - 1, iy = c[s].img / 3 - 1;
+        add_neighbour(p, ti, image_theta(th[c[s].j], ix, iy, p), a);
+    }
+    free(c);
+}
+
 static void gather(const orc_params *p, const cell_list *cl, const double *x, const double *y,
                    const double *th, int64_t i, double band, accum *a)
 {
@@ -268,19 +390,7 @@ static void gather(const orc_params *p, const cell_list *cl, const double *x, co
                 double d2 = dx * dx + dy * dy;
                 if (fabs(sqrt(d2) - p->r) < band) a->amb = 1;
                 if (d2 > r2) continue;
-                double tj = image_theta(th[j], ix, iy, p);
-                a->n++;
-                if (p->model == 0) {                 /* Eq. (collision_VM) */
-                    a->sx += cos(tj);
-                    a->sy += sin(tj);
-                } else if (p->model == 2) {          /* Eq. (collision_NVM), sign(0) = +1 */
-                    double sgn = cos(ti - tj) >= 0.0 ? 1.0 : -1.0;
-                    double tn = tj + 0.5 * ORC_PI * (1.0 - sgn);
-                    a->sx += cos(tn);
-                    a->sy += sin(tn);
-                } else {                             /* Eq. (Langevin_dynamics) */
-                    a->t += sin((double)p->order * (tj - ti));
-                }
+                add_neighbour(p, ti, image_theta(th[j], ix, iy, p), a);
             }
         }
     }
@@ -315,7 +425,8 @@ static void update_one(const orc_params *p, const cell_list *cl, const double *x
                        double *xo, double *yo, double *to, int32_t *nb, double *smag, int32_t *amb)
 {
     accum a;
-    gather(p, cl, x, y, th, i, band, &a);
+    if (p->kn > 0) gather_knn(p, x, y, th, i, band, &a);
+    else gather(p, cl, x, y, th, i, band, &a);
     uint32_t w[4];
     orc_draw(p, (uint32_t)i, step, 0, w);
     double u0 = orc_u01(w[0]), u1 = orc_u01(w[1]);
@@ -327,7 +438,8 @@ static void update_one(const orc_params *p, const cell_list *cl, const double *x
         xn = x[i] + p->v * cos(tn);
         yn = y[i] + p->v * sin(tn);
     } else {
-        double h = (p->weight == 0) ? 1.0 / (1.0 + (double)a.n) : 1.0;
+        /* metric-free: h = 1 (Sec. 2.3, the weight is absorbed in Gamma) */
+        double h = (p->weight == 0 && p->kn == 0) ? 1.0 / (1.0 + (double)a.n) : 1.0;
         /* Box-Muller Gaussian (Sec. 3.1). */
         double g = sqrt(-2.0 * log(u0)) * cos(2.0 * ORC_PI * u1);
         tn = th[i] + p->dt * (p->gamma * h * a.t + p->omega) + p->eta * sqrt(p->dt) * g;
@@ -361,9 +473,12 @@ int orc_step_subset(const orc_params *p, const double *x, const double *y, const
                     double *x_out, double *y_out, double *th_out,
                     int32_t *nb, double *smag, int32_t *amb, double band)
 {
-    cell_list cl;
-    int rc = build_cells(p, x, y, &cl);
-    if (rc) return rc;
+    cell_list cl = {0, 0, 0.0, 0.0, NULL, NULL};
+    if (p->kn < 0) return -1;
+    if (p->kn == 0) {
+        int rc = build_cells(p, x, y, &cl);
+        if (rc) return rc;
+    }
     if (!idx && m != p->n) { free_cells(&cl); return -1; }
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 256) num_threads(g_threads)

@@ -17,6 +17,7 @@
  *   Langevin   dtheta = [Gamma h(|Omega_i|) sum sin(o (theta_j - theta_i)) + omega] dt
  *                       + eta dW,  dx = v cos theta dt  (Euler-Maruyama)  Eq. (Langevin_dynamics), Sec. 2.2
  *   Omega_i    { j != i : |r_i - r_j| <= R }                           Eq. (metric_neighborhood)
+ *              or the k nearest j != i (metric-free, h = 1)            Sec. 2.3
  *   boundaries periodic or reflecting per axis, with image particles   Sec. 2.4
  *   cell lists side L/floor(L/R)                                        Sec. 3.2
  *   polar order p = |sum e^{i theta}| / N                               Sec. 3.4
@@ -50,6 +51,8 @@ typedef struct {
     int32_t  weight;     /* 0: h(n) = 1/(1+n), 1: h(n) = 1                     */
     int32_t  bx, by;     /* 0 periodic, nonzero reflecting                     */
     int32_t  self_image; /* 1: a particle's own mirror image is a neighbour    */
+    int32_t  kn;         /* 0: metric neighbourhood (radius R); k > 0: the k
+                            nearest particles (metric-free, Sec. 2.3)          */
 } orc_params;
 
 /* OpenMP threads used by orc_step_subset / orc_run (1 without OpenMP). */
@@ -74,11 +77,21 @@ int64_t  orc_neighbours_brute(const orc_params *p, const double *x, const double
 void     orc_counts_brute(const orc_params *p, const double *x, const double *y, int32_t *cnt);
 int      orc_counts_cell(const orc_params *p, const double *x, const double *y, int32_t *cnt);
 
+/* Metric-free neighbourhood of particle i (Sec. 2.3): the m nearest
+ * candidates in ascending (distance, j, image) order.  Candidates are all
+ * particles j with their nearest copy along a periodic axis and all three
+ * copies (itself, mirror at 0, mirror at L) along a reflecting axis; the
+ * untransformed particle i is excluded, its mirror images are not (self_image).
+ * Returns the number stored (< m only when there are fewer candidates). */
+int64_t  orc_knn(const orc_params *p, const double *x, const double *y, int64_t i, int64_t m,
+                 int64_t *j_out, int32_t *img_out, double *d_out);
+
 /* ---- dynamics ----------------------------------------------------------- */
 /* One update t -> t+1 of particles idx[0..m) (all particles if idx == NULL,
  * then m must be N) from the state (x, y, th) at step `step`.  Outputs are
  * indexed like idx.  nb: |Omega_i|; smag: |S_i| of the VM/NVM sum (0 for
- * Langevin); amb: 1 if some candidate lies within `band` of the radius R. */
+ * Langevin); amb: 1 if some candidate lies within `band` of the radius R, or,
+ * metric-free, if the k-th and (k+1)-th nearest lie within `band` of each other. */
 int      orc_step_subset(const orc_params *p, const double *x, const double *y, const double *th,
                          uint64_t step, const int64_t *idx, int64_t m,
                          double *x_out, double *y_out, double *th_out,

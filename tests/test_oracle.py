@@ -408,3 +408,105 @@ def test_cell_step_equals_brute_force_neighbour_sums(oracle):
             assert cnt == nb[i]
             assert abs(abs(s) - sm[i]) < 1e-12
             assert abs(_wrap(np.angle(s) - to[i])) < 1e-12
+
+
+# ------------------------------------------- metric-free neighbourhoods -----
+
+@pytest.mark.parametrize("k", [1, 6, 17])
+def test_knn_periodic_matches_kdtree(oracle, k):
+    """Metric-free neighbourhood (Sec. 2.3) in a periodic box = the k nearest
+    other particles returned by scipy's periodic k-d tree."""
+    lx, ly, n = 40.0, 25.0, 1500
+    x, y, _ = inputs.uniform_state(n, lx, ly, 30 + k)
+    m = oracle.Model(n=n, lx=lx, ly=ly, kn=k)
+    tree = cKDTree(np.c_[x, y], boxsize=[lx, ly])
+    for i in np.random.default_rng(k).choice(n, 150, replace=False):
+        d_ref, j_ref = tree.query([x[i], y[i]], k=k + 1)
+        j, img, d = oracle.knn(m, x, y, int(i), k)
+        assert j_ref[0] == i and (j == j_ref[1:]).all()
+        assert np.allclose(d, d_ref[1:], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("bx,by", [(1, 0), (0, 1), (1, 1)])
+def test_knn_reflecting_matches_mirror_extension(oracle, bx, by):
+    """Reflecting walls with image particles (Sec. 2.4) in the metric-free
+    neighbourhood = the k nearest in the periodic doubled box of mirror
+    copies (k-d tree); own mirror images take part like any other image."""
+    lx, ly, n, k = 14.0, 11.0, 500, 7
+    x, y, th = inputs.uniform_state(n, lx, ly, 40 + bx + 2 * by)
+    x[:15] = np.linspace(0.02, 0.6, 15)
+    y[15:30] = ly - np.linspace(0.02, 0.6, 15)
+    m = oracle.Model(n=n, lx=lx, ly=ly, bx=bx, by=by, kn=k)
+    xe, ye, _ = _mirror_extension(x, y, th, lx, ly, bx, by)
+    box = [lx * (2 if bx else 1), ly * (2 if by else 1)]
+    tree = cKDTree(np.c_[xe, ye], boxsize=box)
+    ncopy = xe.size // n
+    flips = [(0, 0), (1, 0), (0, 1), (1, 1)] if (bx and by) else ([(0, 0), (1, 0)] if bx else [(0, 0), (0, 1)])
+    for i in list(range(30)) + list(np.random.default_rng(3).choice(n, 60, replace=False)):
+        d_ref, e_ref = tree.query([x[i], y[i]], k=k + 1)
+        assert e_ref[0] == i
+        j, img, d = oracle.knn(m, x, y, int(i), k)
+        assert np.allclose(d, d_ref[1:], rtol=0, atol=1e-12)
+        # image code (ix+1) + 3 (iy+1): a nonzero ix is a mirror image only at a reflecting axis
+        got = sorted((int(jj), int(bx and c % 3 != 1), int(by and c // 3 != 1)) for jj, c in zip(j, img))
+        ref = sorted((int(e % n),) + flips[int(e // n)] for e in e_ref[1:])
+        assert got == ref and ncopy == len(flips)
+
+
+def test_mfvm_all_neighbours_reach_the_global_mean(oracle):
+    """k >= N-1: every particle's neighbourhood is all the others, so at
+    eta = omega = 0 every particle takes arg sum_j e^{i theta_j} (Eq. collision_VM)."""
+    for k in (11, 30):
+        m = oracle.Model(n=12, lx=20.0, ly=20.0, v=0.3, eta=0.0, kn=k)
+        x, y, th = inputs.uniform_state(12, 20.0, 20.0, 5)
+        xo, yo, to, nb, _, _ = oracle.step(m, x, y, th, 0)
+        mean = math.atan2(np.sin(th).sum(), np.cos(th).sum())
+        assert np.abs(_wrap(to - mean)).max() < 1e-12
+        assert (nb == 11).all()
+        assert np.allclose(np.mod(x + 0.3 * math.cos(mean), 20.0), xo, atol=1e-12)
+
+
+def test_mfvm_pair_with_noise_closed_form(oracle):
+    """N = 2, k = 1: each particle's neighbour is the other one wherever it is;
+    theta' = arg(e^{i theta_i} + e^{i theta_j}) + omega + eta pi (2u - 1)."""
+    m = oracle.Model(n=2, lx=30.0, ly=30.0, v=0.0, eta=0.3, omega=0.1, kn=1, seed=9)
+    x, y, th = np.array([3.0, 25.0]), np.array([4.0, 17.0]), np.array([0.4, 2.9])
+    _, _, to, nb, _, _ = oracle.step(m, x, y, th, 7)
+    for i in range(2):
+        u = oracle.u01(int(oracle.draw(m, i, 7, 0)[0]))
+        e = math.atan2(math.sin(th[0]) + math.sin(th[1]), math.cos(th[0]) + math.cos(th[1]))
+        assert abs(_wrap(to[i] - (e + 0.1 + 0.3 * math.pi * (2 * u - 1)))) < 1e-12
+    assert (nb == 1).all()
+
+
+def test_mfnvm_anti_aligned_pair(oracle):
+    """mfNVM (Eq. collision_NVM with the k = 1 neighbourhood): a partner more
+    than pi/2 away enters reversed, so the pair keeps its axis."""
+    m = oracle.Model(n=2, lx=30.0, ly=30.0, v=0.0, eta=0.0, model=oracle.NVM, kn=1)
+    a, b = 0.2, 0.2 + np.pi - 0.4
+    _, _, to, _, _, _ = oracle.step(m, np.array([5.0, 20.0]), np.array([5.0, 9.0]), np.array([a, b]), 0)
+    ea = math.atan2(math.sin(a) + math.sin(b + np.pi), math.cos(a) + math.cos(b + np.pi))
+    assert abs(_wrap(to[0] - ea)) < 1e-12
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_mfl_pair_relaxation_uses_h_equal_one(oracle, order):
+    """mfL (Sec. 2.3): h = 1 whatever the weight setting, so a k = 1 pair at
+    v = eta = 0 relaxes as tan(o Delta / 2) = tan(o Delta_0 / 2) exp(-2 o Gamma t)."""
+    g, dt, T = 0.9, 1e-3, 700
+    m = oracle.Model(n=2, lx=30.0, ly=30.0, v=0.0, eta=0.0, gamma=g, dt=dt, model=oracle.LANGEVIN,
+                     weight=0, order=order, kn=1)
+    d0 = 1.1 if order == 1 else 0.5
+    x, y, th = np.array([2.0, 21.0]), np.array([3.0, 14.0]), np.array([d0 / 2, -d0 / 2])
+    _, _, tT, _ = oracle.run(m, x, y, th, 0, T)
+    expect = 2.0 / order * math.atan(math.tan(order * d0 / 2) * math.exp(-order * 2 * g * dt * T))
+    assert abs((tT[0] - tT[1]) - expect) < 5 * dt
+
+
+def test_knn_band_flags_near_ties(oracle):
+    """The ambiguity flag marks particles whose k-th and (k+1)-th nearest
+    candidates are closer than `band` to each other."""
+    m = oracle.Model(n=3, lx=20.0, ly=20.0, v=0.0, eta=0.0, kn=1)
+    x, y, th = np.array([10.0, 11.0, 9.0 + 1e-7]), np.array([10.0, 10.0, 10.0]), np.zeros(3)
+    amb = oracle.step(m, x, y, th, 0, band=1e-5)[5]
+    assert amb[0] == 1 and amb[1] == 0
