@@ -100,6 +100,10 @@ typedef struct aap_params {
     int32_t  binnum_neighbors;  /* bins 0..binnum_neighbors-1 of the neighbour-
                                    number histogram, the last collecting all
                                    larger |Omega_i|; 0 = 100, at most 512         */
+    int32_t  kn;         /* [kn] 0: metric neighbourhood of radius r; k in
+                            [1, 32]: metric-free, Omega_i = the k nearest other
+                            particles (mfVM / mfNVM / mfL, Sec. 2.3, with h = 1
+                            whatever `weight` says; r is then unused)          */
 } aap_params;
 
 /* Observables of the current state (Sec. 3.4). */

@@ -52,7 +52,7 @@ class aap_params(C.Structure):
         ("dt", C.c_double), ("seed", C.c_uint64), ("model", C.c_int32), ("order", C.c_int32),
         ("weight", C.c_int32), ("bx", C.c_int32), ("by", C.c_int32), ("tile_w", C.c_int32),
         ("tile_h", C.c_int32), ("threads", C.c_int32), ("capacity", C.c_double),
-        ("binnum_theta", C.c_int32), ("binnum_neighbors", C.c_int32),
+        ("binnum_theta", C.c_int32), ("binnum_neighbors", C.c_int32), ("kn", C.c_int32),
     ]
 
 

@@ -135,12 +135,19 @@ int check_params(const aap_params *p)
 {
     if (!p) return fail(AAP_EINVAL, "params is NULL");
     if (p->n < 0 || p->n >= (1ll << 31)) return fail(AAP_EINVAL, "n must be in [0, 2^31)");
-    if (!finite(p->lx) || !finite(p->ly) || !finite(p->r) || !(p->lx > 0) || !(p->ly > 0) || !(p->r > 0))
-        return fail(AAP_EINVAL, "lx, ly and r must be finite and positive");
-    if (std::floor(p->lx / p->r) < 3 || std::floor(p->ly / p->r) < 3)
-        return fail(AAP_EINVAL, "the box must hold at least 3 cells of side >= R per axis (L >= 3R)");
-    if (std::floor(p->lx / p->r) > (1 << 26) || std::floor(p->ly / p->r) > (1 << 26))
-        return fail(AAP_EINVAL, "more than 2^26 cells per axis");
+    if (p->kn < 0 || p->kn > aapk::kMaxKnn) return fail(AAP_EINVAL, "kn must be in [0, 32]");
+    if (!finite(p->lx) || !finite(p->ly) || !(p->lx > 0) || !(p->ly > 0))
+        return fail(AAP_EINVAL, "lx and ly must be finite and positive");
+    if (p->kn > 0) {
+        // metric-free (Sec. 2.3): R is not used and may be anything
+        if (p->n >= (1ll << 28)) return fail(AAP_EINVAL, "metric-free systems need n < 2^28");
+    } else {
+        if (!finite(p->r) || !(p->r > 0)) return fail(AAP_EINVAL, "r must be finite and positive");
+        if (std::floor(p->lx / p->r) < 3 || std::floor(p->ly / p->r) < 3)
+            return fail(AAP_EINVAL, "the box must hold at least 3 cells of side >= R per axis (L >= 3R)");
+        if (std::floor(p->lx / p->r) > (1 << 26) || std::floor(p->ly / p->r) > (1 << 26))
+            return fail(AAP_EINVAL, "more than 2^26 cells per axis");
+    }
     if (!finite(p->v) || p->v < 0) return fail(AAP_EINVAL, "v must be finite and >= 0");
     if (!finite(p->eta) || p->eta < 0) return fail(AAP_EINVAL, "eta must be finite and >= 0");
     if (!finite(p->omega) || !finite(p->gamma)) return fail(AAP_EINVAL, "omega and gamma must be finite");
@@ -151,10 +158,15 @@ int check_params(const aap_params *p)
     if (p->order < 1 || p->order > 64) return fail(AAP_EINVAL, "order must be in [1, 64]");
     if (p->weight != AAP_H_INV_1PN && p->weight != AAP_H_ONE)
         return fail(AAP_EINVAL, "weight must be AAP_H_INV_1PN or AAP_H_ONE");
-    const double cs = std::min(p->lx / std::floor(p->lx / p->r), p->ly / std::floor(p->ly / p->r));
     const double disp = p->model == AAP_LANGEVIN ? p->v * p->dt : p->v;
-    if (disp > cs)
-        return fail(AAP_EINVAL, "the displacement per step (v, or v*dt) must not exceed one cell side");
+    if (p->kn > 0) {
+        if (disp > 0.25 * std::min(p->lx, p->ly))
+            return fail(AAP_EINVAL, "the displacement per step (v, or v*dt) must not exceed a quarter of the box");
+    } else {
+        const double cs = std::min(p->lx / std::floor(p->lx / p->r), p->ly / std::floor(p->ly / p->r));
+        if (disp > cs)
+            return fail(AAP_EINVAL, "the displacement per step (v, or v*dt) must not exceed one cell side");
+    }
     if (p->tile_w < 0 || p->tile_h < 0 || p->tile_w > aapk::kMaxTile || p->tile_h > aapk::kMaxTile)
         return fail(AAP_EINVAL, "tile_w and tile_h must be 0 (automatic) or in [6, 64]");
     if ((p->tile_w && p->tile_w < 6) || (p->tile_h && p->tile_h < 6))
@@ -201,8 +213,40 @@ void layout_regions(Sys &S, double mu, double factor)
 
 // Region capacities, spill list, staging capacities and launch shapes for a
 // capacity factor (slots per region over the mean occupancy).
+// Metric-free layout: one tile over the box, every record in region 0.
+int set_capacity_mf(aap_handle *h)
+{
+    const aap_params &p = h->p;
+    Sys &S = h->hs;
+    S.cap[0] = aapk::round_up((int)std::max<long long>(p.n, 1), 4);
+    S.off[0] = 0;
+    for (int r = 1; r < aapk::kRegions; ++r) {
+        S.cap[r] = 0;
+        S.off[r] = S.cap[0];
+    }
+    S.tile_slots = S.cap[0];
+    S.spill_cap = 64;
+    LaunchCfg &L = h->L;
+    L.spill_list_cap = 0;
+    L.scratch_cap = 0;
+    L.scratch_per_block = 0;
+    L.threads = 256;
+    L.model = p.model;
+    L.stage_cap = 0;
+    L.nce_max = 0;
+    L.hist_words = (p.binnum_theta ? p.binnum_theta : 100) + (p.binnum_neighbors ? p.binnum_neighbors : 100);
+    L.grid_step = 0;
+    L.grid_finish = 1;
+    L.nsys = 1;
+    L.knn = p.kn;
+    L.mf_n = p.n;
+    L.mf_ncell = (long long)S.ncx * S.ncy;
+    return AAP_OK;
+}
+
 int set_capacity(aap_handle *h, double factor)
 {
+    if (h->p.kn > 0) return set_capacity_mf(h);
     const aap_params &p = h->p;
     Sys &S = h->hs;
     const int nsm = sm_count();
@@ -240,8 +284,62 @@ int set_capacity(aap_handle *h, double factor)
     return AAP_OK;
 }
 
+void set_model(Sys &S, const aap_params &p)
+{
+    S.model = p.model;
+    S.order = p.model == AAP_LANGEVIN ? p.order : 1;
+    S.weight = p.kn > 0 ? AAP_H_ONE : p.weight;       // metric-free: h = 1 (Sec. 2.3)
+    S.bx = p.bx != 0;
+    S.by = p.by != 0;
+    S.eta_pi = (float)(p.eta * M_PI);
+    S.omega_step = (float)(p.model == AAP_LANGEVIN ? p.omega * p.dt : p.omega);
+    S.gamma_dt = (float)(p.gamma * p.dt);
+    S.noise_amp = (float)(p.eta * std::sqrt(p.dt));
+    S.seed_lo = (uint32_t)p.seed;
+    S.seed_hi = (uint32_t)(p.seed >> 32);
+    S.n = p.n;
+}
+
+// Metric-free geometry (Sec. 3.3): cells of side about
+// R_eff = sqrt(Lx Ly k / (N pi)) (Eq. effective_radius), one flat tile.
+int build_layout_mf(aap_handle *h)
+{
+    const aap_params &p = h->p;
+    Sys &S = h->hs;
+    const double reff = p.n > 0 ? std::sqrt(p.lx * p.ly * p.kn / ((double)p.n * M_PI)) : std::max(p.lx, p.ly);
+    h->ncx = (int)std::max(1.0, std::min(std::floor(p.lx / reff), (double)(1 << 24)));
+    h->ncy = (int)std::max(1.0, std::min(std::floor(p.ly / reff), (double)(1 << 24)));
+    if ((long long)h->ncx * h->ncy >= (1ll << 30)) return fail(AAP_EINVAL, "too many metric-free cells");
+    h->csx = p.lx / h->ncx;
+    h->csy = p.ly / h->ncy;
+    S.ncx = h->ncx;
+    S.ncy = h->ncy;
+    S.ntx = S.nty = 1;
+    S.twmax = S.ncx;
+    S.thmax = S.ncy;
+    S.ntiles = 1;
+    S.sx = fix_bits(2 * S.ncx);      // twice the box fits int32: exact image coordinates
+    S.sy = fix_bits(2 * S.ncy);
+    S.lx = p.lx;
+    S.ly = p.ly;
+    S.csx_d = h->csx;
+    S.csy_d = h->csy;
+    S.ux = (float)(h->csx / (double)(1ll << S.sx));
+    S.uy = (float)(h->csy / (double)(1ll << S.sy));
+    const double disp = p.model == AAP_LANGEVIN ? p.v * p.dt : p.v;
+    S.kx = (float)(disp / h->csx * (double)(1ll << S.sx));
+    S.ky = (float)(disp / h->csy * (double)(1ll << S.sy));
+    S.r2 = 0.f;
+    set_model(S, p);
+    S.flat = 1;
+    S.knn = p.kn;
+    h->factor = 1.0;
+    return set_capacity_mf(h);
+}
+
 int build_layout(aap_handle *h)
 {
+    if (h->p.kn > 0) return build_layout_mf(h);
     const aap_params &p = h->p;
     Sys &S = h->hs;
     h->ncx = (int)std::floor(p.lx / p.r);
@@ -281,18 +379,7 @@ int build_layout(aap_handle *h)
     S.kx = (float)(disp / h->csx * (double)(1ll << S.sx));
     S.ky = (float)(disp / h->csy * (double)(1ll << S.sy));
     S.r2 = (float)(p.r * p.r);
-    S.model = p.model;
-    S.order = p.model == AAP_LANGEVIN ? p.order : 1;
-    S.weight = p.weight;
-    S.bx = p.bx != 0;
-    S.by = p.by != 0;
-    S.eta_pi = (float)(p.eta * M_PI);
-    S.omega_step = (float)(p.model == AAP_LANGEVIN ? p.omega * p.dt : p.omega);
-    S.gamma_dt = (float)(p.gamma * p.dt);
-    S.noise_amp = (float)(p.eta * std::sqrt(p.dt));
-    S.seed_lo = (uint32_t)p.seed;
-    S.seed_hi = (uint32_t)(p.seed >> 32);
-    S.n = p.n;
+    set_model(S, p);
     h->factor = p.capacity > 0 ? p.capacity : 4.0;
     return set_capacity(h, h->factor);
 }
@@ -384,6 +471,17 @@ int alloc_all(aap_handle *h)
     S.bins_nbr = h->p.binnum_neighbors ? h->p.binnum_neighbors : 100;
     if ((rc = dev_alloc(h, &S.hist, (size_t)(S.bins_theta + S.bins_nbr) * sizeof(unsigned long long)))) return rc;
     if ((rc = dev_alloc(h, &S.err, sizeof(int)))) return rc;
+    if (S.knn > 0) {
+        const long long ncell = (long long)S.ncx * S.ncy;
+        const long long nchunk = (ncell + 1 + aapk::kScanChunk - 1) / aapk::kScanChunk;
+        const size_t n = (size_t)std::max<long long>(h->p.n, 1);
+        if ((rc = dev_alloc(h, &S.mf_cnt, (size_t)ncell * sizeof(int)))) return rc;
+        if ((rc = dev_alloc(h, &S.mf_start, (size_t)(ncell + 1) * sizeof(int)))) return rc;
+        if ((rc = dev_alloc(h, &S.mf_blk, (size_t)(nchunk + 1) * sizeof(int)))) return rc;
+        if ((rc = dev_alloc(h, &S.mf_cs, n * sizeof(int2)))) return rc;
+        if ((rc = dev_alloc(h, &S.mf_sorted, n * sizeof(int4)))) return rc;
+        AAP_CK(cudaMemsetAsync(S.mf_cnt, 0, (size_t)ncell * sizeof(int), h->stream));
+    }
     if (!h->member) {
         if ((rc = dev_alloc(h, &h->d_sys, sizeof(Sys)))) return rc;
         if ((rc = dev_alloc(h, &h->d_tile_base, 2 * sizeof(int)))) return rc;
@@ -1228,6 +1326,7 @@ int aap_ens_create(const aap_params *params, int32_t count, void *stream, aap_en
             g_err = "replica " + std::to_string(r) + ": " + g_err;
             return rc;
         }
+        if (params[r].kn > 0) return fail(AAP_EINVAL, "metric-free systems (kn > 0) are not batched; use aap_create");
         if (params[r].model != params[0].model) return fail(AAP_EINVAL, "all replicas must use the same model");
         if (params[r].threads != params[0].threads) return fail(AAP_EINVAL, "all replicas must use the same threads");
     }

@@ -85,7 +85,19 @@ struct Sys {
     int bins_theta, bins_nbr;
     int *nbr_out;               // optional |Omega_i| by particle id
     int *err;
+    // metric-free neighbourhoods (Sec. 2.3): one tile over the whole box whose
+    // records all sit in region 0 (flat), re-sorted by cell every step
+    int flat;                   // 1: every record goes to region 0 of tile 0
+    int knn;                    // k nearest neighbours (0: metric, radius R)
+    int *mf_cnt;                // [ncx * ncy] records per cell (zero between steps)
+    int *mf_start;              // [ncx * ncy + 1] chunk-local exclusive prefix of mf_cnt
+    int *mf_blk;                // [chunks + 1] exclusive prefix of the chunk totals
+    int2 *mf_cs;                // [n] cell and arrival rank of each record
+    int4 *mf_sorted;            // [n] records in cell order
 };
+
+constexpr int kScanChunk = 4096;    // cells per block of the metric-free cell scan
+constexpr int kMaxKnn = 32;         // largest metric-free k
 
 struct Ctl {
     long long step;             // steps taken; parity selects the current buffer

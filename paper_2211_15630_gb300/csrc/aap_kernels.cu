@@ -20,6 +20,7 @@
 
 #include <cuda_runtime.h>
 
+#include "aap_device.cuh"
 #include "aap_internal.cuh"
 #include "aap_kernels.cuh"
 
@@ -43,33 +44,6 @@ __device__ unsigned long long g_phase[16];
 #define PHASE_START() do { } while (0)
 #define PHASE_MARK(i) do { } while (0)
 #endif
-
-#define AAP_PI_F 3.14159265358979f
-#define AAP_2PI_F 6.28318530717959f
-
-// ---------------------------------------------------------------- Philox --
-// Philox4x32-10 (Salmon et al., SC'11): counter c, key (k0, k1).
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
-        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-        c[0] = n0;
-        c[1] = lo1;
-        c[2] = n2;
-        c[3] = lo0;
-    }
-}
-
-// (w >> 9 + 1/2) 2^-23: exact in FP32.
-__device__ __forceinline__ float u01f(uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); }
-__device__ __forceinline__ double u01d(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 // ------------------------------------------------------------ geometry ----
 __device__ __forceinline__ int tile_x0(const Sys &S, int tx) { return S.x0tab[tx]; }
@@ -120,23 +94,6 @@ __device__ __forceinline__ void warp_insert(const Sys &S, int b, bool act, int d
     }
 }
 
-__device__ __forceinline__ long long warp_sum_ll(long long v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ int warp_incl_scan(int v)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    return v;
-}
 
 // ---------------------------------------------------------- tile context --
 struct TileCtx {
@@ -762,7 +719,7 @@ __global__ void k_insert(Sys S, int b, const double *x, const double *y, const f
         const int tw = tile_x0(S, tx + 1) - x0, th_ = tile_y0(S, ty + 1) - y0;
         if (pt >= AAP_PI_F || pt < -AAP_PI_F) pt -= AAP_2PI_F * floorf((pt + AAP_PI_F) * (1.0f / AAP_2PI_F));
         dtile = ty * S.ntx + tx;
-        region = region_of(X >> S.sx, Y >> S.sy, tw, th_);
+        region = S.flat ? 0 : region_of(X >> S.sx, Y >> S.sy, tw, th_);
         rec = make_int4(X, Y, __float_as_int(pt), (int)i);
     }
     warp_insert(S, b, act, dtile, region, rec);
@@ -931,6 +888,15 @@ static cudaError_t launch_step_m(const LaunchCfg &L, cudaStream_t st, cudaEvent_
 
 cudaError_t launch_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev)
 {
+    if (L.knn > 0) {
+        cudaError_t e = launch_mf_step(L, st, ev);
+        if (e != cudaSuccess) return e;
+        k_finish<<<L.grid_finish, 256, 0, st>>>(L.sys, L.nsys, L.ctl);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
     switch (L.model) {
     case 0: return launch_step_m<0>(L, st, ev);
     case 1: return launch_step_m<1>(L, st, ev);

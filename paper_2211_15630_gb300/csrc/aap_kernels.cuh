@@ -24,6 +24,9 @@ struct LaunchCfg {
     int nce_max;                 // cells of the largest tile plus its ring
     int hist_words;              // histogram bins (theta + |Omega|) of the widest system
     int grid_step, grid_finish;
+    // metric-free step (knn > 0): cell count, scan, scatter, k-nearest update
+    int knn;
+    long long mf_n, mf_ncell;
 };
 
 size_t step_smem_bytes(int stage_cap, int nce_max, int hist_words);
@@ -34,6 +37,9 @@ cudaError_t configure_step_kernel(int model, int threads, size_t smem_bytes, int
 // One full step: k_step then k_finish.  With ev != nullptr, ev[0..2] are
 // recorded before k_step, after k_step and after k_finish.
 cudaError_t launch_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev = nullptr);
+
+// The metric-free step (knn > 0): the kernels of launch_step for a flat system.
+cudaError_t launch_mf_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev);
 
 cudaError_t launch_insert(const Sys &S, int b, const double *x, const double *y, const float *th,
                           int mode, cudaStream_t st);

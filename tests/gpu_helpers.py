@@ -3,7 +3,8 @@ and compare with the FP64 oracle on the same state.
 
 Tolerances (one step from the same state, FP32 device arithmetic vs FP64):
   - neighbour counts: bit-exact, except particles with a candidate pair within
-    1e-5 of R (|d - R| < 1e-5), which are reported and skipped;
+    1e-5 of R (|d - R| < 1e-5), or, metric-free, whose k-th and (k+1)-th
+    nearest lie within 1e-5 of each other, which are reported and skipped;
   - orientation: 1e-5 rad, or, where the FP32 condition of arg S is worse, the
     derived bound 5 (n_i + 1) 2^-23 / |S_i| (the error of an FP32 sum of
     n_i + 1 unit vectors divided by its length); such particles are counted;
@@ -30,7 +31,7 @@ def params(**kw):
 def oracle_model(O, p):
     return O.Model(n=p.n, lx=p.lx, ly=p.ly, r=p.r, v=p.v, eta=p.eta, omega=p.omega,
                    gamma=p.gamma, dt=p.dt, seed=p.seed, model=p.model, order=p.order,
-                   weight=p.weight, bx=int(p.bx != 0), by=int(p.by != 0))
+                   weight=p.weight, bx=int(p.bx != 0), by=int(p.by != 0), kn=p.kn)
 
 
 def compare_one_step(O, p, h, idx=None, band=1e-5, max_bad_frac=0.0):
