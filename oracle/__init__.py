@@ -47,6 +47,9 @@ class Params(C.Structure):
         ("gamma", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64),
         ("model", C.c_int32), ("order", C.c_int32), ("weight", C.c_int32),
         ("bx", C.c_int32), ("by", C.c_int32), ("self_image", C.c_int32), ("kn", C.c_int32),
+        ("nspecies", C.c_int32), ("pad_", C.c_int32), ("species_n", C.c_int64 * 8),
+        ("species_v", C.c_double * 8), ("species_eta", C.c_double * 8),
+        ("species_omega", C.c_double * 8), ("species_gamma", C.c_double * 64),
     ]
 
 
@@ -71,11 +74,28 @@ class Model:
     by: int = 0
     self_image: int = 1
     kn: int = 0
+    # species (Sec. 2.5): counts per species, then per-species v, eta, omega
+    # and the coupling matrix gamma[a][b]; empty = one species
+    species_n: tuple = ()
+    species_v: tuple = ()
+    species_eta: tuple = ()
+    species_omega: tuple = ()
+    species_gamma: tuple = ()
 
     def c(self) -> Params:
-        return Params(self.n, self.lx, self.ly, self.r, self.v, self.eta, self.omega,
-                      self.gamma, self.dt, self.seed, self.model, self.order, self.weight,
-                      self.bx, self.by, self.self_image, self.kn)
+        p = Params(self.n, self.lx, self.ly, self.r, self.v, self.eta, self.omega,
+                   self.gamma, self.dt, self.seed, self.model, self.order, self.weight,
+                   self.bx, self.by, self.self_image, self.kn)
+        ns = len(self.species_n)
+        p.nspecies = ns
+        for s in range(ns):
+            p.species_n[s] = int(self.species_n[s])
+            p.species_v[s] = float(self.species_v[s]) if self.species_v else self.v
+            p.species_eta[s] = float(self.species_eta[s]) if self.species_eta else self.eta
+            p.species_omega[s] = float(self.species_omega[s]) if self.species_omega else self.omega
+            for b in range(ns):
+                p.species_gamma[8 * s + b] = float(self.species_gamma[s][b]) if self.species_gamma else self.gamma
+        return p
 
 
 _lib = None
@@ -99,6 +119,7 @@ def lib():
             "orc_neighbours_brute": (i64, [P(Params), vp, vp, i64, vp, vp, i64]),
             "orc_counts_brute": (None, [P(Params), vp, vp, vp]),
             "orc_knn": (i64, [P(Params), vp, vp, i64, i64, vp, vp, vp]),
+            "orc_species_of": (C.c_int, [P(Params), i64]),
             "orc_counts_cell": (C.c_int, [P(Params), vp, vp, vp]),
             "orc_step_subset": (C.c_int, [P(Params), vp, vp, vp, u64, vp, i64, vp, vp, vp,
                                           vp, vp, vp, d]),

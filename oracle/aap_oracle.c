@@ -239,8 +239,33 @@ typedef struct {
     int     amb;        /* a candidate within `band` of R                      */
 } accum;
 
-/* One neighbour with (image) orientation tj joins the sums of particle i. */
-static void add_neighbour(const orc_params *p, double ti, double tj, accum *a)
+/* ------------------------------------------------------------------------
+ * Species (Sec. 2.5): each species has its own v, eta, omega, and the
+ * Langevin coupling of i to a neighbour j is Gamma_{s_i s_j}.  Species are
+ * consecutive blocks of particle ids.
+ * ---------------------------------------------------------------------- */
+int orc_species_of(const orc_params *p, int64_t id)
+{
+    if (p->nspecies <= 1) return 0;
+    int64_t end = 0;
+    for (int s = 0; s < p->nspecies; ++s) {
+        end += p->species_n[s];
+        if (id < end) return s;
+    }
+    return p->nspecies - 1;
+}
+
+static double sp_v(const orc_params *p, int s) { return p->nspecies > 1 ? p->species_v[s] : p->v; }
+static double sp_eta(const orc_params *p, int s) { return p->nspecies > 1 ? p->species_eta[s] : p->eta; }
+static double sp_omega(const orc_params *p, int s) { return p->nspecies > 1 ? p->species_omega[s] : p->omega; }
+static double sp_gamma(const orc_params *p, int a, int b)
+{
+    return p->nspecies > 1 ? p->species_gamma[a * 8 + b] : p->gamma;
+}
+
+/* One neighbour with (image) orientation tj and coupling g (Langevin)
+ * joins the sums of particle i. */
+static void add_neighbour(const orc_params *p, double ti, double tj, double g, accum *a)
 {
     a->n++;
     if (p->model == 0) {                 /* Eq. (collision_VM) */
@@ -251,8 +276,8 @@ static void add_neighbour(const orc_params *p, double ti, double tj, accum *a)
         double tn = tj + 0.5 * ORC_PI * (1.0 - sgn);
         a->sx += cos(tn);
         a->sy += sin(tn);
-    } else {                             /* Eq. (Langevin_dynamics) */
-        a->t += sin((double)p->order * (tj - ti));
+    } else {                             /* Eq. (Langevin_dynamics), Gamma inside the sum */
+        a->t += g * sin((double)p->order * (tj - ti));
     }
 }
 
@@ -356,7 +381,8 @@ static void gather_knn(const orc_params *p, const double *x, const double *y, co
     if (cnt > k && sqrt(c[k].d2) - sqrt(c[k - 1].d2) < band) a->amb = 1;
     for (int64_t s = 0; s < cnt && s < k; ++s) {
         int ix = c[s].img % 3 - 1, iy = c[s].img / 3 - 1;
-        add_neighbour(p, ti, image_theta(th[c[s].j], ix, iy, p), a);
+        add_neighbour(p, ti, image_theta(th[c[s].j], ix, iy, p),
+                      sp_gamma(p, orc_species_of(p, i), orc_species_of(p, c[s].j)), a);
     }
     free(c);
 }
@@ -390,7 +416,8 @@ static void gather(const orc_params *p, const cell_list *cl, const double *x, co
                 double d2 = dx * dx + dy * dy;
                 if (fabs(sqrt(d2) - p->r) < band) a->amb = 1;
                 if (d2 > r2) continue;
-                add_neighbour(p, ti, image_theta(th[j], ix, iy, p), a);
+                add_neighbour(p, ti, image_theta(th[j], ix, iy, p),
+                              sp_gamma(p, orc_species_of(p, i), orc_species_of(p, j)), a);
             }
         }
     }
@@ -430,21 +457,23 @@ static void update_one(const orc_params *p, const cell_list *cl, const double *x
     uint32_t w[4];
     orc_draw(p, (uint32_t)i, step, 0, w);
     double u0 = orc_u01(w[0]), u1 = orc_u01(w[1]);
+    const int si = orc_species_of(p, i);
+    const double v = sp_v(p, si), eta = sp_eta(p, si), omega = sp_omega(p, si);
     double tn, xn, yn;
     if (p->model == 0 || p->model == 2) {
         /* Eq. (collision): f + eta * xi with xi uniform on [-pi, pi]. */
-        tn = atan2(a.sy, a.sx) + p->omega + p->eta * ORC_PI * (2.0 * u0 - 1.0);
+        tn = atan2(a.sy, a.sx) + omega + eta * ORC_PI * (2.0 * u0 - 1.0);
         /* Eq. (streaming) uses the new orientation. */
-        xn = x[i] + p->v * cos(tn);
-        yn = y[i] + p->v * sin(tn);
+        xn = x[i] + v * cos(tn);
+        yn = y[i] + v * sin(tn);
     } else {
         /* metric-free: h = 1 (Sec. 2.3, the weight is absorbed in Gamma) */
         double h = (p->weight == 0 && p->kn == 0) ? 1.0 / (1.0 + (double)a.n) : 1.0;
         /* Box-Muller Gaussian (Sec. 3.1). */
         double g = sqrt(-2.0 * log(u0)) * cos(2.0 * ORC_PI * u1);
-        tn = th[i] + p->dt * (p->gamma * h * a.t + p->omega) + p->eta * sqrt(p->dt) * g;
-        xn = x[i] + p->v * p->dt * cos(th[i]);
-        yn = y[i] + p->v * p->dt * sin(th[i]);
+        tn = th[i] + p->dt * (h * a.t + omega) + eta * sqrt(p->dt) * g;
+        xn = x[i] + v * p->dt * cos(th[i]);
+        yn = y[i] + v * p->dt * sin(th[i]);
     }
     if (!p->bx) {
         if (xn < 0.0) xn += p->lx;

@@ -20,6 +20,7 @@
  *              or the k nearest j != i (metric-free, h = 1)            Sec. 2.3
  *   boundaries periodic or reflecting per axis, with image particles   Sec. 2.4
  *   cell lists side L/floor(L/R)                                        Sec. 3.2
+ *   species    per-species v, eta, omega and a coupling matrix Gamma_ab  Sec. 2.5
  *   polar order p = |sum e^{i theta}| / N                               Sec. 3.4
  *
  * Random numbers: counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
@@ -53,7 +54,22 @@ typedef struct {
     int32_t  self_image; /* 1: a particle's own mirror image is a neighbour    */
     int32_t  kn;         /* 0: metric neighbourhood (radius R); k > 0: the k
                             nearest particles (metric-free, Sec. 2.3)          */
+    /* Particle species (Sec. 2.5): with nspecies >= 2, particles
+     * 0 .. species_n[0]-1 are species 0, the next species_n[1] species 1, ...;
+     * particle i then uses v, eta, omega of its species s_i and, in the
+     * Langevin sum, Gamma_{s_i s_j} = species_gamma[s_i * 8 + s_j] for each
+     * neighbour j.  nspecies 0 or 1: the scalar parameters above. */
+    int32_t  nspecies;
+    int32_t  pad_;
+    int64_t  species_n[8];
+    double   species_v[8];
+    double   species_eta[8];
+    double   species_omega[8];
+    double   species_gamma[64];
 } orc_params;
+
+/* Species of particle `id` (0 with a single species). */
+int      orc_species_of(const orc_params *p, int64_t id);
 
 /* OpenMP threads used by orc_step_subset / orc_run (1 without OpenMP). */
 void     orc_set_threads(int n);

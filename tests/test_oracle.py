@@ -510,3 +510,93 @@ def test_knn_band_flags_near_ties(oracle):
     x, y, th = np.array([10.0, 11.0, 9.0 + 1e-7]), np.array([10.0, 10.0, 10.0]), np.zeros(3)
     amb = oracle.step(m, x, y, th, 0, band=1e-5)[5]
     assert amb[0] == 1 and amb[1] == 0
+
+
+# ------------------------------------------------------------- species -----
+
+def test_species_blocks_of_ids(oracle):
+    """Species are consecutive blocks of particle ids (Sec. 2.5 gives N as a list)."""
+    m = oracle.Model(n=10, lx=10.0, ly=10.0, species_n=(3, 0, 7))
+    p = m.c()
+    got = [oracle.lib().orc_species_of(ctypes.byref(p), i) for i in range(10)]
+    assert got == [0, 0, 0, 2, 2, 2, 2, 2, 2, 2]
+
+
+def test_species_isolated_particles_closed_form(oracle):
+    """Three isolated particles of three species (VM, Sec. 2.1 + 2.5): each
+    turns by its own omega_s + eta_s pi (2u - 1) and moves by its own v_s."""
+    v, eta, om = (0.1, 0.3, 0.5), (0.0, 0.2, 0.6), (0.05, -0.3, 0.0)
+    m = oracle.Model(n=3, lx=30.0, ly=30.0, species_n=(1, 1, 1), species_v=v, species_eta=eta,
+                     species_omega=om, seed=3)
+    x, y, th = np.array([5.0, 15.0, 25.0]), np.array([5.0, 15.0, 25.0]), np.array([0.3, -1.0, 2.0])
+    xo, yo, to, _, _, _ = oracle.step(m, x, y, th, 4)
+    for i in range(3):
+        u = oracle.u01(int(oracle.draw(m, i, 4, 0)[0]))
+        t = th[i] + om[i] + eta[i] * math.pi * (2 * u - 1)
+        assert abs(_wrap(to[i] - t)) < 1e-12
+        assert abs(xo[i] - (x[i] + v[i] * math.cos(t))) < 1e-12
+        assert abs(yo[i] - (y[i] + v[i] * math.sin(t))) < 1e-12
+
+
+def test_species_ordered_mixture_translates_at_own_speeds(oracle):
+    """eta = omega = 0, every theta equal: the VM keeps the common angle, and
+    each species translates rigidly with its own speed."""
+    n, L, t0 = 900, 20.0, 0.7
+    x, y, _ = inputs.uniform_state(n, L, L, 8)
+    th = np.full(n, t0)
+    m = oracle.Model(n=n, lx=L, ly=L, eta=0.0, species_n=(300, 600), species_v=(0.2, 0.7))
+    xT, yT, tT, _ = oracle.run(m, x, y, th, 0, 5)
+    assert np.abs(_wrap(tT - t0)).max() < 1e-12
+    v = np.where(np.arange(n) < 300, 0.2, 0.7)
+    assert np.allclose(xT, np.mod(x + 5 * v * math.cos(t0), L), atol=1e-9)
+    assert np.allclose(yT, np.mod(y + 5 * v * math.sin(t0), L), atol=1e-9)
+
+
+def test_species_langevin_pair_nonreciprocal_coupling(oracle):
+    """Langevin A-B pair, v = eta = 0, h = 1/(1+n) = 1/2 (Eq. Langevin_dynamics
+    with Gamma_{s_i s_j}): each Euler-Maruyama step conserves
+    Gamma_BA theta_A + Gamma_AB theta_B exactly, and Delta = theta_A - theta_B
+    relaxes as tan(Delta/2) = tan(Delta_0/2) exp(-(Gamma_AB + Gamma_BA) t / 2)."""
+    gab, gba, dt, T = 1.6, 0.4, 1e-3, 900
+    G = ((0.0, gab), (gba, 0.0))
+    m = oracle.Model(n=2, lx=10.0, ly=10.0, v=0.0, eta=0.0, dt=dt, model=oracle.LANGEVIN,
+                     species_n=(1, 1), species_v=(0.0, 0.0), species_eta=(0.0, 0.0),
+                     species_omega=(0.0, 0.0), species_gamma=G)
+    x, y, th = np.array([5.0, 5.5]), np.array([5.0, 5.0]), np.array([0.6, -0.5])
+    inv0 = gba * th[0] + gab * th[1]
+    xs, ys, ts = x, y, th
+    for t in range(5):
+        xs, ys, ts, _, _, _ = oracle.step(m, xs, ys, ts, t)
+        assert abs(gba * ts[0] + gab * ts[1] - inv0) < 1e-14
+    _, _, tT, _ = oracle.run(m, x, y, th, 0, T)
+    d0 = th[0] - th[1]
+    expect = 2 * math.atan(math.tan(d0 / 2) * math.exp(-(gab + gba) / 2 * dt * T))
+    assert abs((tT[0] - tT[1]) - expect) < 5 * dt
+    assert abs(gba * tT[0] + gab * tT[1] - inv0) < 1e-12
+
+
+def test_species_one_way_coupling_leaves_the_leader_free(oracle):
+    """Gamma_AB = 0: species A ignores B, so at eta = 0 it just rotates with
+    omega_A; B (Gamma_BA > 0) turns towards A (metric-free k = 1 as well)."""
+    for kn in (0, 1):
+        m = oracle.Model(n=2, lx=10.0, ly=10.0, v=0.0, dt=0.01, model=oracle.LANGEVIN, kn=kn,
+                         species_n=(1, 1), species_v=(0.0, 0.0), species_eta=(0.0, 0.0),
+                         species_omega=(0.3, 0.0), species_gamma=((0.0, 0.0), (2.0, 0.0)))
+        x, y, th = np.array([5.0, 5.5]), np.array([5.0, 5.0]), np.array([0.2, 1.5])
+        _, _, tT, _ = oracle.run(m, x, y, th, 0, 100)
+        assert abs(_wrap(tT[0] - (0.2 + 0.3 * 0.01 * 100))) < 1e-12
+        assert abs(_wrap(tT[1] - tT[0])) < abs(_wrap(th[1] - th[0])) - 0.3
+
+
+def test_species_identical_parameters_reduce_to_one_species(oracle):
+    """Splitting one species into identical ones changes nothing (Langevin,
+    with the coupling moved inside the sum: equal up to rounding)."""
+    n, L = 700, 15.0
+    x, y, th = inputs.uniform_state(n, L, L, 12)
+    kw = dict(n=n, lx=L, ly=L, v=0.3, eta=0.2, omega=0.1, gamma=1.3, dt=0.05, model=oracle.LANGEVIN)
+    a = oracle.step(oracle.Model(**kw), x, y, th, 2)
+    G = ((1.3, 1.3), (1.3, 1.3))
+    b = oracle.step(oracle.Model(**kw, species_n=(200, 500), species_v=(0.3, 0.3), species_eta=(0.2, 0.2),
+                                 species_omega=(0.1, 0.1), species_gamma=G), x, y, th, 2)
+    for u, w in zip(a[:3], b[:3]):
+        assert np.allclose(u, w, rtol=0, atol=1e-12)
