@@ -182,6 +182,30 @@ def _bench_brownian(A, W, torch, stream, steps):
             "ms_per_step": ms / steps, "steps": steps}
 
 
+def _bench_metric_free(A, W, torch, stream, steps, kn=6):
+    """mfVM (k nearest neighbours, Sec. 2.3) at N = 2^24, L = 2896: whole
+    steps timed with events, then the kernel split from the library's timers."""
+    p = W.metric_free_vicsek(kn=kn, seed=1)
+    h = A.aap_create(p, stream.cuda_stream)
+    A.aap_step(h, 20)
+    A.aap_sync(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    A.aap_step(h, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    A.aap_set_timing(h, True)
+    A.aap_step(h, 20)
+    A.aap_sync(h)
+    kms, kl = A.aap_get_timing(h)
+    A.aap_set_timing(h, False)
+    A.aap_destroy(h)
+    return {"workload": f"mfvm_k{kn}_N2^24_L2896", "updates_per_s": p.n * steps / (ms / 1e3),
+            "ms_per_step": ms / steps, "steps": steps,
+            "search_update_kernels_ms": kms[0] / max(kl[0], 1), "finish_ms": kms[1] / max(kl[1], 1)}
+
+
 def _bench_ensemble(A, W, torch, stream, steps):
     """256 Vicsek replicas (N log-uniform 2^10..2^18, rho in {0.5,1,2,4}, eta in
     [0.1,0.7]): one batched, graph-replayed launch per step vs the same replicas
@@ -473,6 +497,7 @@ def main():
             extras[f"vicsek_eta_{eta}_updates_per_s"] = args.n * max(args.steps // 4, 50) / (msx / 1e3)
             A.aap_destroy(he)
         extras["brownian"] = _bench_brownian(A, W, torch, stream, 500)
+        extras["metric_free"] = _bench_metric_free(A, W, torch, stream, 100)
         extras["ensemble"] = _bench_ensemble(A, W, torch, stream, 200)
         with torch.cuda.stream(stream):     # torch copies and library calls share one stream
             extras["surrogate"] = _bench_surrogate(A, W, torch, stream)

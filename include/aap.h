@@ -104,6 +104,19 @@ typedef struct aap_params {
                             [1, 32]: metric-free, Omega_i = the k nearest other
                             particles (mfVM / mfNVM / mfL, Sec. 2.3, with h = 1
                             whatever `weight` says; r is then unused)          */
+    /* Species (Sec. 2.5; the paper lets v, eta, omega, N and gamma be lists).
+     * nspecies 0 or 1: one species with the scalars above.  2..8: particles
+     * 0 .. species_n[0]-1 are species 0, the next species_n[1] species 1, and
+     * so on (the counts must add up to n); particle i moves with
+     * species_v[s_i], takes noise species_eta[s_i] and chirality
+     * species_omega[s_i], and its Langevin sum weighs neighbour j by
+     * species_gamma[8 * s_i + s_j] (the scalar gamma is then unused).        */
+    int32_t  nspecies;
+    int64_t  species_n[8];
+    double   species_v[8];
+    double   species_eta[8];
+    double   species_omega[8];
+    double   species_gamma[64];
 } aap_params;
 
 /* Observables of the current state (Sec. 3.4). */

@@ -53,6 +53,8 @@ class aap_params(C.Structure):
         ("weight", C.c_int32), ("bx", C.c_int32), ("by", C.c_int32), ("tile_w", C.c_int32),
         ("tile_h", C.c_int32), ("threads", C.c_int32), ("capacity", C.c_double),
         ("binnum_theta", C.c_int32), ("binnum_neighbors", C.c_int32), ("kn", C.c_int32),
+        ("nspecies", C.c_int32), ("species_n", C.c_int64 * 8), ("species_v", C.c_double * 8),
+        ("species_eta", C.c_double * 8), ("species_omega", C.c_double * 8), ("species_gamma", C.c_double * 64),
     ]
 
 
@@ -174,6 +176,24 @@ def aap_params_default(**kw) -> aap_params:
         if not hasattr(p, k):
             raise AttributeError(k)
         setattr(p, k, v)
+    return p
+
+
+def set_species(p: aap_params, counts, v=None, eta=None, omega=None, gamma=None) -> aap_params:
+    """Fill the species fields of p (Sec. 2.5): counts per species (consecutive
+    id blocks, adding up to p.n), per-species v, eta, omega (default: the
+    scalars) and the coupling matrix gamma[a][b] (default: the scalar gamma)."""
+    ns = len(counts)
+    if ns > 8:
+        raise ValueError("at most 8 species")
+    p.nspecies = ns
+    for a in range(ns):
+        p.species_n[a] = int(counts[a])
+        p.species_v[a] = float(v[a]) if v is not None else p.v
+        p.species_eta[a] = float(eta[a]) if eta is not None else p.eta
+        p.species_omega[a] = float(omega[a]) if omega is not None else p.omega
+        for b in range(ns):
+            p.species_gamma[8 * a + b] = float(gamma[a][b]) if gamma is not None else p.gamma
     return p
 
 

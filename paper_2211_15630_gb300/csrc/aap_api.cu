@@ -158,7 +158,24 @@ int check_params(const aap_params *p)
     if (p->order < 1 || p->order > 64) return fail(AAP_EINVAL, "order must be in [1, 64]");
     if (p->weight != AAP_H_INV_1PN && p->weight != AAP_H_ONE)
         return fail(AAP_EINVAL, "weight must be AAP_H_INV_1PN or AAP_H_ONE");
-    const double disp = p->model == AAP_LANGEVIN ? p->v * p->dt : p->v;
+    double vmax = p->v;
+    if (p->nspecies < 0 || p->nspecies > aapk::kMaxSpecies) return fail(AAP_EINVAL, "nspecies must be in [0, 8]");
+    if (p->nspecies > 1) {
+        long long tot = 0;
+        vmax = 0.0;
+        for (int a = 0; a < p->nspecies; ++a) {
+            if (p->species_n[a] < 0) return fail(AAP_EINVAL, "species_n must be >= 0");
+            tot += p->species_n[a];
+            if (!finite(p->species_v[a]) || p->species_v[a] < 0 || !finite(p->species_eta[a]) ||
+                p->species_eta[a] < 0 || !finite(p->species_omega[a]))
+                return fail(AAP_EINVAL, "species_v and species_eta must be finite and >= 0, species_omega finite");
+            for (int b = 0; b < p->nspecies; ++b)
+                if (!finite(p->species_gamma[8 * a + b])) return fail(AAP_EINVAL, "species_gamma must be finite");
+            vmax = std::max(vmax, p->species_v[a]);
+        }
+        if (tot != p->n) return fail(AAP_EINVAL, "species_n must add up to n");
+    }
+    const double disp = p->model == AAP_LANGEVIN ? vmax * p->dt : vmax;
     if (p->kn > 0) {
         if (disp > 0.25 * std::min(p->lx, p->ly))
             return fail(AAP_EINVAL, "the displacement per step (v, or v*dt) must not exceed a quarter of the box");
@@ -298,7 +315,49 @@ void set_model(Sys &S, const aap_params &p)
     S.seed_lo = (uint32_t)p.seed;
     S.seed_hi = (uint32_t)(p.seed >> 32);
     S.n = p.n;
+    // species (Sec. 2.5); entry 0 repeats the scalars with a single species
+    const bool multi = p.nspecies > 1;
+    S.nsp = multi ? p.nspecies : 1;
+    long long end = 0;
+    for (int a = 0; a < aapk::kMaxSpecies; ++a) {
+        end += (multi && a < p.nspecies) ? p.species_n[a] : 0;
+        S.sp_end[a] = multi ? end : p.n;
+        const double eta = multi ? p.species_eta[a] : p.eta, om = multi ? p.species_omega[a] : p.omega;
+        S.sp_eta_pi[a] = (float)(eta * M_PI);
+        S.sp_omega_step[a] = (float)(p.model == AAP_LANGEVIN ? om * p.dt : om);
+        S.sp_noise_amp[a] = (float)(eta * std::sqrt(p.dt));
+        for (int b = 0; b < aapk::kMaxSpecies; ++b)
+            S.sp_gamma_dt[a * aapk::kMaxSpecies + b] = (float)((multi ? p.species_gamma[8 * a + b] : p.gamma) * p.dt);
+    }
+    if (!multi) {
+        S.sp_eta_pi[0] = S.eta_pi;
+        S.sp_omega_step[0] = S.omega_step;
+        S.sp_noise_amp[0] = S.noise_amp;
+    }
 }
+
+// Displacement per step of each species in fixed-point units (after the
+// geometry is known); entry 0 repeats kx, ky with a single species.
+void set_species_kinematics(Sys &S, const aap_params &p)
+{
+    for (int a = 0; a < aapk::kMaxSpecies; ++a) {
+        const double v = p.nspecies > 1 ? p.species_v[a] : p.v;
+        const double disp = p.model == AAP_LANGEVIN ? v * p.dt : v;
+        S.sp_kx[a] = (float)(disp / S.csx_d * (double)(1ll << S.sx));
+        S.sp_ky[a] = (float)(disp / S.csy_d * (double)(1ll << S.sy));
+    }
+    if (p.nspecies <= 1) {
+        S.sp_kx[0] = S.kx;
+        S.sp_ky[0] = S.ky;
+    }
+}
+
+// Cell side of the metric-free search over R_eff.  The result does not
+// depend on it (the search is exact for any cell size); it only trades the
+// number of rings against the particles per cell.
+#ifndef AAP_MF_CELL_FACTOR
+#define AAP_MF_CELL_FACTOR 1.0
+#endif
 
 // Metric-free geometry (Sec. 3.3): cells of side about
 // R_eff = sqrt(Lx Ly k / (N pi)) (Eq. effective_radius), one flat tile.
@@ -306,7 +365,8 @@ int build_layout_mf(aap_handle *h)
 {
     const aap_params &p = h->p;
     Sys &S = h->hs;
-    const double reff = p.n > 0 ? std::sqrt(p.lx * p.ly * p.kn / ((double)p.n * M_PI)) : std::max(p.lx, p.ly);
+    const double reff = AAP_MF_CELL_FACTOR *
+                        (p.n > 0 ? std::sqrt(p.lx * p.ly * p.kn / ((double)p.n * M_PI)) : std::max(p.lx, p.ly));
     h->ncx = (int)std::max(1.0, std::min(std::floor(p.lx / reff), (double)(1 << 24)));
     h->ncy = (int)std::max(1.0, std::min(std::floor(p.ly / reff), (double)(1 << 24)));
     if ((long long)h->ncx * h->ncy >= (1ll << 30)) return fail(AAP_EINVAL, "too many metric-free cells");
@@ -331,6 +391,7 @@ int build_layout_mf(aap_handle *h)
     S.ky = (float)(disp / h->csy * (double)(1ll << S.sy));
     S.r2 = 0.f;
     set_model(S, p);
+    set_species_kinematics(S, p);
     S.flat = 1;
     S.knn = p.kn;
     h->factor = 1.0;
@@ -380,6 +441,7 @@ int build_layout(aap_handle *h)
     S.ky = (float)(disp / h->csy * (double)(1ll << S.sy));
     S.r2 = (float)(p.r * p.r);
     set_model(S, p);
+    set_species_kinematics(S, p);
     h->factor = p.capacity > 0 ? p.capacity : 4.0;
     return set_capacity(h, h->factor);
 }

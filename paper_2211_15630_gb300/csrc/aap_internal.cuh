@@ -94,7 +94,22 @@ struct Sys {
     int *mf_blk;                // [chunks + 1] exclusive prefix of the chunk totals
     int2 *mf_cs;                // [n] cell and arrival rank of each record
     int4 *mf_sorted;            // [n] records in cell order
+    // species (Sec. 2.5): ids in [sp_end[s-1], sp_end[s]) are species s; with
+    // one species, entry 0 repeats the scalar parameters above
+    int nsp;
+    long long sp_end[8];
+    float sp_eta_pi[8], sp_omega_step[8], sp_noise_amp[8], sp_kx[8], sp_ky[8];
+    float sp_gamma_dt[64];      // Gamma_{s_i s_j} dt, row s_i
 };
+
+constexpr int kMaxSpecies = 8;
+
+__host__ __device__ inline int species_of(const Sys &S, unsigned id)
+{
+    int s = 0;
+    for (int k = 0; k < S.nsp - 1; ++k) s += (long long)id >= S.sp_end[k];
+    return s;
+}
 
 constexpr int kScanChunk = 4096;    // cells per block of the metric-free cell scan
 constexpr int kMaxKnn = 32;         // largest metric-free k

@@ -260,6 +260,32 @@ __device__ __forceinline__ void neighbour_sum(const float4 *__restrict__ P, cons
     }
 }
 
+// Langevin sums with per-species couplings (Sec. 2.5): each neighbour's
+// (cos o theta_j, sin o theta_j) weighted by grow[species of j] = Gamma_{s_i s_j} dt.
+__device__ __forceinline__ void neighbour_sum_sp(const float4 *__restrict__ P, const unsigned short *spc,
+                                                 const int *cstart, int ec, int W2, float4 pi, float r2,
+                                                 const float *grow, float &sc, float &ss, int &cnt)
+{
+    sc = 0.f;
+    ss = 0.f;
+    cnt = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int c0 = ec + dy * W2 - 1;
+        const int a = cstart[c0], b = cstart[c0 + 3];
+        for (int j = a; j < b; ++j) {
+            const float4 pj = P[j];
+            const float dx = pj.x - pi.x, dyy = pj.y - pi.y;
+            if (fmaf(dx, dx, dyy * dyy) <= r2) {
+                const float g = grow[spc[j]];
+                sc = fmaf(g, pj.z, sc);
+                ss = fmaf(g, pj.w, ss);
+                ++cnt;
+            }
+        }
+    }
+}
+
 // Phase 2 of a tile, staged in A (shared memory or the block's scratch).
 template <int NT, int MODEL>
 __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tables &tb, long long step,
@@ -380,6 +406,7 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             rank += (id2 < myid) || (id2 == myid && k2 < k);
         }
         const int q = a + rank;
+        if (S.nsp > 1) A.slot[q] = (unsigned short)species_of(S, myid);   // slot is free again: species by sorted position
         float thv = A.rth[k];
         float sn, cs;
         if (MODEL == 1 && S.order != 1) {
@@ -424,7 +451,12 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             const float4 pi = A.P[q];
             float sc, ss;
             int cnt;
-            neighbour_sum<MODEL>(A.P, tb.cstart, ec, W2, pi, r2, sc, ss, cnt);
+            const int sp = S.nsp > 1 ? species_of(S, id) : 0;
+            if (MODEL == 1 && S.nsp > 1)
+                neighbour_sum_sp(A.P, A.slot, tb.cstart, ec, W2, pi, r2, S.sp_gamma_dt + sp * kMaxSpecies, sc, ss,
+                                 cnt);
+            else
+                neighbour_sum<MODEL>(A.P, tb.cstart, ec, W2, pi, r2, sc, ss, cnt);
             const int nb = cnt - 1;          // the particle itself was counted
             if (measure) {
                 int bt = (int)floorf((thi + AAP_PI_F) * ((float)S.bins_theta * (1.0f / AAP_2PI_F)));
@@ -439,21 +471,22 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             int dX, dY;
             if (MODEL != 1) {
                 // Eq. (collision_VM) / (collision_NVM) + noise; Eq. (streaming)
-                thn = atan2f(ss, sc) + S.omega_step + S.eta_pi * (2.0f * u0 - 1.0f);
+                thn = atan2f(ss, sc) + S.sp_omega_step[sp] + S.sp_eta_pi[sp] * (2.0f * u0 - 1.0f);
                 __sincosf(thn, &sn, &cn);
-                dX = __float2int_rn(S.kx * cn);
-                dY = __float2int_rn(S.ky * sn);
+                dX = __float2int_rn(S.sp_kx[sp] * cn);
+                dY = __float2int_rn(S.sp_ky[sp] * sn);
             } else {
                 // Eq. (Langevin_dynamics), one Euler-Maruyama step
                 const float u1 = u01f(c4[1]);
                 const float h = S.weight ? 1.0f : 1.0f / (1.0f + (float)nb);
-                const float tsum = pi.z * ss - pi.w * sc;
+                const float tsum = pi.z * ss - pi.w * sc;   // Gamma dt inside with several species
                 const float gz = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
-                thn = thi + S.gamma_dt * h * tsum + S.omega_step + S.noise_amp * gz;
+                const float drift = S.nsp > 1 ? h * tsum : S.gamma_dt * h * tsum;
+                thn = thi + drift + S.sp_omega_step[sp] + S.sp_noise_amp[sp] * gz;
                 float co = pi.z, so = pi.w;
                 if (S.order != 1) sincosf(thi, &so, &co);
-                dX = __float2int_rn(S.kx * co);
-                dY = __float2int_rn(S.ky * so);
+                dX = __float2int_rn(S.sp_kx[sp] * co);
+                dY = __float2int_rn(S.sp_ky[sp] * so);
                 cn = 0.f;
                 sn = 0.f;
             }

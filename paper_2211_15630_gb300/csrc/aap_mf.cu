@@ -231,6 +231,103 @@ __device__ __forceinline__ void visit_cell(const MfGeo &G, const int4 *__restric
     }
 }
 
+// Neighbour sums over a finished list (ascending distance, id, image):
+// VM / NVM add e^{i theta_j} (NVM reversed when more than pi/2 from theta_i,
+// Eq. collision_NVM), Langevin adds sin(o (theta_j - theta_i)).  Returns |Omega_i|.
+template <int MODEL, int KMAX>
+__device__ __forceinline__ void list_sums(const float (&d)[KMAX], const unsigned (&ref)[KMAX],
+                                          const int4 *__restrict__ srt, const Sys &S, const float *grow, int order,
+                                          float ci, float si, float oci, float osi, float &sc, float &ss,
+                                          float &tsum, int &nb)
+{
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) {
+        if (d[s] >= 0.0f && d[s] < __int_as_float(0x7f800000)) {
+            const unsigned rf = ref[s];
+            const int4 rj = srt[rf & 0x3fffffffu];
+            const float tj = __int_as_float(rj.z);
+            float sn, cs;
+            if (MODEL == 1 && order != 1) sincosf(tj * (float)order, &sn, &cs);
+            else __sincosf(tj, &sn, &cs);
+            if (rf & (1u << 30)) {                   // mirrored in x: theta -> pi - theta
+                if (MODEL != 1 || (order & 1)) cs = -cs; else sn = -sn;
+            }
+            if (rf & (2u << 30)) sn = -sn;           // mirrored in y: theta -> -theta
+            ++nb;
+            if (MODEL == 1) {
+                const float t = oci * sn - osi * cs;             // sin(o (theta_j - theta_i))
+                tsum = grow ? fmaf(grow[species_of(S, (unsigned)rj.w)], t, tsum) : tsum + t;
+            } else {
+                if (MODEL == 2 && fmaf(ci, cs, si * sn) < 0.f) {
+                    cs = -cs;
+                    sn = -sn;
+                }
+                sc += cs;
+                ss += sn;
+            }
+        }
+    }
+}
+
+// The k nearest by exhaustive scan of all n records (out of line: it only
+// runs when a periodic window cannot certify the list, i.e. for systems with
+// about k particles or fewer across half the box).  out: sum cos, sum sin,
+// Langevin sum; returns |Omega_i|.
+template <int MODEL, int KMAX>
+__device__ __noinline__ int brute_sums(const MfGeo &G, const int4 *__restrict__ srt, const Sys &S, const float *grow,
+                                       long long n, long long q, int X, int Y, int k, int order, float ci, float si,
+                                       float oci, float osi, float *out)
+{
+    float d[KMAX];
+    unsigned key[KMAX], ref[KMAX];
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) {
+        const bool dummy = s < KMAX - k;
+        d[s] = dummy ? -1.0f : __int_as_float(0x7f800000);
+        key[s] = dummy ? 0u : 0xffffffffu;
+        ref[s] = 0u;
+    }
+    for (long long j = 0; j < n; ++j) {
+        const int4 rj = srt[j];
+        int ox[3], cxs[3], ax[3], nx = 0, oy[3], cys[3], ay[3], ny = 0;
+        if (!G.bx) {
+            int dd = rj.x - X, c = 0;
+            if (2 * dd > G.W) { dd -= G.W; c = -1; } else if (2 * dd < -G.W) { dd += G.W; c = 1; }
+            ox[0] = dd; cxs[0] = c; ax[0] = 0; nx = 1;
+        } else {
+            ox[0] = rj.x - X;           cxs[0] = 0;  ax[0] = 0;
+            ox[1] = -rj.x - X;          cxs[1] = -1; ax[1] = 1;
+            ox[2] = 2 * G.W - rj.x - X; cxs[2] = 1;  ax[2] = 1;
+            nx = 3;
+        }
+        if (!G.by) {
+            int dd = rj.y - Y, c = 0;
+            if (2 * dd > G.H) { dd -= G.H; c = -1; } else if (2 * dd < -G.H) { dd += G.H; c = 1; }
+            oy[0] = dd; cys[0] = c; ay[0] = 0; ny = 1;
+        } else {
+            oy[0] = rj.y - Y;           cys[0] = 0;  ay[0] = 0;
+            oy[1] = -rj.y - Y;          cys[1] = -1; ay[1] = 2;
+            oy[2] = 2 * G.H - rj.y - Y; cys[2] = 1;  ay[2] = 2;
+            ny = 3;
+        }
+        for (int b = 0; b < ny; ++b)
+            for (int a = 0; a < nx; ++a) {
+                if (j == q && cxs[a] == 0 && cys[b] == 0) continue;     // j != i
+                const float dx = (float)ox[a] * G.ux, dy = (float)oy[b] * G.uy;
+                const unsigned code = (unsigned)((cxs[a] + 1) + 3 * (cys[b] + 1));
+                topk_offer<KMAX>(d, key, ref, fmaf(dx, dx, dy * dy), (unsigned)rj.w * 9u + code,
+                                 (unsigned)j | ((unsigned)(ax[a] | ay[b]) << 30));
+            }
+    }
+    float sc = 0.f, ss = 0.f, tsum = 0.f;
+    int nb = 0;
+    list_sums<MODEL, KMAX>(d, ref, srt, S, grow, order, ci, si, oci, osi, sc, ss, tsum, nb);
+    out[0] = sc;
+    out[1] = ss;
+    out[2] = tsum;
+    return nb;
+}
+
 template <int NT, int MODEL, int KMAX>
 __global__ void __launch_bounds__(NT) k_mf_update(const Sys *__restrict__ sys, const Ctl *__restrict__ ctl)
 {
@@ -306,48 +403,6 @@ __global__ void __launch_bounds__(NT) k_mf_update(const Sys *__restrict__ sys, c
             }
             if (ring >= rmx && ring >= rmy) break;
         }
-        if (!certified) {
-            // the periodic window is exhausted: the definition itself, over
-            // every particle at its nearest periodic copy (and mirror images)
-#pragma unroll
-            for (int s = 0; s < KMAX; ++s) {
-                const bool dummy = s < KMAX - k;
-                d[s] = dummy ? -1.0f : __int_as_float(0x7f800000);
-                key[s] = dummy ? 0u : 0xffffffffu;
-            }
-            for (long long j = 0; j < n; ++j) {
-                const int4 rj = srt[j];
-                int ox[3], cxs[3], ax[3], nx = 0, oy[3], cys[3], ay[3], ny = 0;
-                if (!G.bx) {
-                    int dd = rj.x - X, c = 0;
-                    if (2 * dd > G.W) { dd -= G.W; c = -1; } else if (2 * dd < -G.W) { dd += G.W; c = 1; }
-                    ox[0] = dd; cxs[0] = c; ax[0] = 0; nx = 1;
-                } else {
-                    ox[0] = rj.x - X;         cxs[0] = 0;  ax[0] = 0;
-                    ox[1] = -rj.x - X;        cxs[1] = -1; ax[1] = 1;
-                    ox[2] = 2 * G.W - rj.x - X; cxs[2] = 1; ax[2] = 1;
-                    nx = 3;
-                }
-                if (!G.by) {
-                    int dd = rj.y - Y, c = 0;
-                    if (2 * dd > G.H) { dd -= G.H; c = -1; } else if (2 * dd < -G.H) { dd += G.H; c = 1; }
-                    oy[0] = dd; cys[0] = c; ay[0] = 0; ny = 1;
-                } else {
-                    oy[0] = rj.y - Y;         cys[0] = 0;  ay[0] = 0;
-                    oy[1] = -rj.y - Y;        cys[1] = -1; ay[1] = 2;
-                    oy[2] = 2 * G.H - rj.y - Y; cys[2] = 1; ay[2] = 2;
-                    ny = 3;
-                }
-                for (int b = 0; b < ny; ++b)
-                    for (int a = 0; a < nx; ++a) {
-                        if (j == q && cxs[a] == 0 && cys[b] == 0) continue;
-                        const float dx = (float)ox[a] * G.ux, dy = (float)oy[b] * G.uy;
-                        const unsigned code = (unsigned)((cxs[a] + 1) + 3 * (cys[b] + 1));
-                        topk_offer<KMAX>(d, key, ref, fmaf(dx, dx, dy * dy), (unsigned)rj.w * 9u + code,
-                                         (unsigned)j | ((unsigned)(ax[a] | ay[b]) << 30));
-                    }
-            }
-        }
         // sums over Omega_i in (distance, id, image) order
         float si, ci;
         __sincosf(thi, &si, &ci);                    // |theta| <= pi
@@ -355,30 +410,18 @@ __global__ void __launch_bounds__(NT) k_mf_update(const Sys *__restrict__ sys, c
         if (MODEL == 1 && S.order != 1) sincosf(thi * (float)S.order, &osi, &oci);
         float sc = MODEL == 1 ? 0.f : ci, ss = MODEL == 1 ? 0.f : si, tsum = 0.f;
         int nb = 0;
-#pragma unroll
-        for (int s = 0; s < KMAX; ++s) {
-            if (d[s] >= 0.0f && d[s] < __int_as_float(0x7f800000)) {
-                const unsigned rf = ref[s];
-                const float tj = __int_as_float(srt[rf & 0x3fffffffu].z);
-                float sn, cs;
-                if (MODEL == 1 && S.order != 1) sincosf(tj * (float)S.order, &sn, &cs);
-                else __sincosf(tj, &sn, &cs);
-                if (rf & (1u << 30)) {                   // mirrored in x: theta -> pi - theta
-                    if (MODEL != 1 || (S.order & 1)) cs = -cs; else sn = -sn;
-                }
-                if (rf & (2u << 30)) sn = -sn;           // mirrored in y: theta -> -theta
-                ++nb;
-                if (MODEL == 1) {
-                    tsum += oci * sn - osi * cs;         // sin(o (theta_j - theta_i))
-                } else {
-                    if (MODEL == 2 && fmaf(ci, cs, si * sn) < 0.f) {
-                        cs = -cs;                        // Eq. (collision_NVM)
-                        sn = -sn;
-                    }
-                    sc += cs;
-                    ss += sn;
-                }
-            }
+        const int sp = S.nsp > 1 ? species_of(S, id) : 0;
+        const float *grow = (MODEL == 1 && S.nsp > 1) ? S.sp_gamma_dt + sp * kMaxSpecies : nullptr;
+        if (certified) {
+            list_sums<MODEL, KMAX>(d, ref, srt, S, grow, S.order, ci, si, oci, osi, sc, ss, tsum, nb);
+        } else {
+            // the periodic window is exhausted: the definition itself, over
+            // every particle at its nearest periodic copy (and mirror images)
+            float out[3];
+            nb = brute_sums<MODEL, KMAX>(G, srt, S, grow, n, q, X, Y, k, S.order, ci, si, oci, osi, out);
+            sc += out[0];
+            ss += out[1];
+            tsum = out[2];
         }
         if (measure) {
             int bt = (int)floorf((thi + AAP_PI_F) * ((float)S.bins_theta * (1.0f / AAP_2PI_F)));
@@ -393,17 +436,17 @@ __global__ void __launch_bounds__(NT) k_mf_update(const Sys *__restrict__ sys, c
         int dX, dY;
         if (MODEL != 1) {
             // Eq. (collision_VM) / (collision_NVM) + noise; Eq. (streaming)
-            thn = atan2f(ss, sc) + S.omega_step + S.eta_pi * (2.0f * u0 - 1.0f);
+            thn = atan2f(ss, sc) + S.sp_omega_step[sp] + S.sp_eta_pi[sp] * (2.0f * u0 - 1.0f);
             __sincosf(thn, &sn, &cn);
-            dX = __float2int_rn(S.kx * cn);
-            dY = __float2int_rn(S.ky * sn);
+            dX = __float2int_rn(S.sp_kx[sp] * cn);
+            dY = __float2int_rn(S.sp_ky[sp] * sn);
         } else {
             // Eq. (Langevin_dynamics) with h = 1 (Sec. 2.3), one Euler-Maruyama step
             const float u1 = u01f(c4[1]);
             const float gz = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
-            thn = thi + S.gamma_dt * tsum + S.omega_step + S.noise_amp * gz;
-            dX = __float2int_rn(S.kx * ci);
-            dY = __float2int_rn(S.ky * si);
+            thn = thi + (grow ? tsum : S.gamma_dt * tsum) + S.sp_omega_step[sp] + S.sp_noise_amp[sp] * gz;
+            dX = __float2int_rn(S.sp_kx[sp] * ci);
+            dY = __float2int_rn(S.sp_ky[sp] * si);
         }
         // boundary rule (Sec. 2.4) in exact fixed point
         int Xn = X + dX, Yn = Y + dY;

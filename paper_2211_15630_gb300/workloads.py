@@ -19,6 +19,12 @@ def vicsek_large(eta: float = 0.45, seed: int = 1, **kw):
                               model=AAP_VM, **kw)
 
 
+def metric_free_vicsek(kn: int = 6, eta: float = 0.45, seed: int = 1, **kw):
+    """Metric-free Vicsek model (mfVM), N = 2^24, L = 2896 (rho = 2.0004), k nearest, v0 = 0.5, periodic."""
+    return aap_params_default(n=1 << 24, lx=2896.0, ly=2896.0, r=1.0, v=0.5, eta=eta, seed=seed,
+                              model=AAP_VM, kn=kn, **kw)
+
+
 def vicsek_small(eta: float = 0.4, seed: int = 1, **kw):
     """Standard Vicsek model, N = 8192, L = 64 (rho = 2), R = 1, v0 = 0.5, periodic."""
     return aap_params_default(n=8192, lx=64.0, ly=64.0, r=1.0, v=0.5, eta=eta, seed=seed,

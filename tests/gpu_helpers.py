@@ -29,9 +29,15 @@ def params(**kw):
 
 
 def oracle_model(O, p):
+    ns = p.nspecies if p.nspecies > 1 else 0
+    sp = {}
+    if ns:
+        sp = dict(species_n=tuple(p.species_n[:ns]), species_v=tuple(p.species_v[:ns]),
+                  species_eta=tuple(p.species_eta[:ns]), species_omega=tuple(p.species_omega[:ns]),
+                  species_gamma=tuple(tuple(p.species_gamma[8 * a: 8 * a + ns]) for a in range(ns)))
     return O.Model(n=p.n, lx=p.lx, ly=p.ly, r=p.r, v=p.v, eta=p.eta, omega=p.omega,
                    gamma=p.gamma, dt=p.dt, seed=p.seed, model=p.model, order=p.order,
-                   weight=p.weight, bx=int(p.bx != 0), by=int(p.by != 0), kn=p.kn)
+                   weight=p.weight, bx=int(p.bx != 0), by=int(p.by != 0), kn=p.kn, **sp)
 
 
 def compare_one_step(O, p, h, idx=None, band=1e-5, max_bad_frac=0.0):
@@ -57,7 +63,8 @@ def compare_one_step(O, p, h, idx=None, band=1e-5, max_bad_frac=0.0):
         tol_t = np.maximum(1e-5, 5.0 * (nbo + 1) * EPS32 / np.maximum(smag, 1e-30))
     dth = np.abs(wrap(t1[idx].astype(np.float64) - to))
     bad_t = np.nonzero(ok & (dth > tol_t))[0]
-    disp = p.v * (p.dt if p.model == A.AAP_LANGEVIN else 1.0)
+    vmax = max(p.species_v[:p.nspecies]) if p.nspecies > 1 else p.v
+    disp = vmax * (p.dt if p.model == A.AAP_LANGEVIN else 1.0)
     tol_x = 1e-5 * p.lx + disp * np.minimum(tol_t, 2 * np.pi)
     tol_y = 1e-5 * p.ly + disp * np.minimum(tol_t, 2 * np.pi)
     dx = x1[idx] - xo
