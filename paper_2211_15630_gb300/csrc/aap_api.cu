@@ -542,6 +542,9 @@ int alloc_all(aap_handle *h)
         if ((rc = dev_alloc(h, &S.mf_blk, (size_t)(nchunk + 1) * sizeof(int)))) return rc;
         if ((rc = dev_alloc(h, &S.mf_cs, n * sizeof(int2)))) return rc;
         if ((rc = dev_alloc(h, &S.mf_sorted, n * sizeof(int4)))) return rc;
+        if ((rc = dev_alloc(h, &S.mf_fix, n * sizeof(int2)))) return rc;
+        if ((rc = dev_alloc(h, &S.mf_nfix, sizeof(int)))) return rc;
+        AAP_CK(cudaMemsetAsync(S.mf_nfix, 0, sizeof(int), h->stream));
         AAP_CK(cudaMemsetAsync(S.mf_cnt, 0, (size_t)ncell * sizeof(int), h->stream));
     }
     if (!h->member) {

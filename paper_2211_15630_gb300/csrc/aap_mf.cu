@@ -18,14 +18,21 @@
 //   k_mf_scan_top  exclusive prefix of the chunk totals
 //   k_mf_scatter   records into cell order
 //   k_mf_update    one thread per record, in cell order so that a warp shares
-//                  its rings: ring search with a sorted top-k list in
-//                  registers, the VM / NVM / Langevin update with h = 1
-//                  (Sec. 2.3), streaming, boundary rule, the new record, and
-//                  exact integer sums for p, q and the histograms
+//                  its rings: ring search for the k-th smallest distance tau
+//                  (a register list kept by min/max passes), a second pass
+//                  over the same cells that sums the neighbours (distance
+//                  below tau, or at tau) in 2^32 fixed point, then the VM /
+//                  NVM / Langevin update with h = 1 (Sec. 2.3), streaming,
+//                  boundary rule, the new record, and exact integer sums for
+//                  p, q and the histograms
+//   k_mf_exact     the few particles the first kernel queued: several
+//                  candidates at exactly tau (the tie is broken by id and
+//                  image), or a periodic window too small to certify the list
+//                  (an exhaustive scan)
 // followed by the k_finish of the metric path.
 //
-// Determinism: the selected set is ordered by (distance, id, image) and the
-// sums run in that order, so nothing depends on the arrival order in a cell.
+// Determinism: the neighbour set is fixed by (distance, id, image) and the
+// sums are integers, so nothing depends on the arrival order in a cell.
 // Fixed point: positions carry 2^s units per cell with s chosen so that twice
 // the box still fits int32; every image coordinate and displacement below is
 // then an exact int32.
@@ -42,6 +49,7 @@ namespace aapk {
 namespace {
 
 constexpr int kMfThreads = 256;
+constexpr float kFix32F = 4294967296.0f;    // 2^32: order-free neighbour sums
 
 __global__ void k_mf_count(const Sys *__restrict__ sys, const Ctl *__restrict__ ctl)
 {
@@ -49,6 +57,7 @@ __global__ void k_mf_count(const Sys *__restrict__ sys, const Ctl *__restrict__ 
     const int cur = (int)(ctl->step & 1);
     const int ncx = S.ncx, ncy = S.ncy, sx = S.sx, sy = S.sy;
     const int4 *__restrict__ rec = S.rec[cur];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *S.mf_nfix = 0;      // queue of k_mf_exact
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S.n;
          i += (long long)gridDim.x * blockDim.x) {
         const int4 r = rec[i];
@@ -208,11 +217,14 @@ struct MfGeo {
     bool bx, by;
 };
 
-// Offer every particle of virtual cell (vx, vy) to the list of particle q.
-template <int KMAX>
-__device__ __forceinline__ void visit_cell(const MfGeo &G, const int4 *__restrict__ srt, const int *__restrict__ st,
-                                           const int *__restrict__ blk, int vx, int vy, int X, int Y, long long q,
-                                           float (&d)[KMAX], unsigned (&key)[KMAX], unsigned (&ref)[KMAX])
+// Every candidate of virtual cell (vx, vy) for particle q (at X, Y):
+// f(d2, record, sorted index, image code, mirror flips).  The untransformed
+// particle itself is skipped (j != i); d2 is computed the same way for every
+// pass, so passes over the same cells see bit-identical distances.
+template <class F>
+__device__ __forceinline__ void for_cell(const MfGeo &G, const int4 *__restrict__ srt, const int *__restrict__ st,
+                                         const int *__restrict__ blk, int vx, int vy, int X, int Y, long long q,
+                                         F &&f)
 {
     AxisMap mx, my;
     if (!map_axis(vx, G.ncx, G.W, G.bx, X, mx) || !map_axis(vy, G.ncy, G.H, G.by, Y, my)) return;
@@ -221,14 +233,74 @@ __device__ __forceinline__ void visit_cell(const MfGeo &G, const int4 *__restric
     const bool untransformed = mx.code == 0 && my.code == 0;
     const unsigned code = (unsigned)((mx.code + 1) + 3 * (my.code + 1));
     const unsigned flips = (G.bx && mx.code ? 1u : 0u) | (G.by && my.code ? 2u : 0u);
+#pragma unroll 1
     for (int j = b; j < e; ++j) {
-        if (untransformed && j == q) continue;             // j != i
+        if (untransformed && j == q) continue;
         const int4 rj = srt[j];
         const float dx = (float)(mx.a * rj.x + mx.off) * G.ux;
         const float dy = (float)(my.a * rj.y + my.off) * G.uy;
-        const float d2 = fmaf(dx, dx, dy * dy);
-        topk_offer<KMAX>(d, key, ref, d2, (unsigned)rj.w * 9u + code, (unsigned)j | (flips << 30));
+        f(fmaf(dx, dx, dy * dy), rj, j, code, flips);
     }
+}
+
+// Every candidate in ring `ring` (the cells at Chebyshev distance ring from
+// (cx, cy)) of a window capped at rmx, rmy cells per axis.
+template <class F>
+__device__ __forceinline__ void for_ring(const MfGeo &G, const int4 *__restrict__ srt, const int *__restrict__ st,
+                                         const int *__restrict__ blk, int ring, int rmx, int rmy, int cx, int cy,
+                                         int X, int Y, long long q, F &&f)
+{
+    const int rx = min(ring, rmx), ry = min(ring, rmy);
+    for (int dy = -ry; dy <= ry; ++dy) {
+        if (dy == -ring || dy == ring) {
+            for (int dx = -rx; dx <= rx; ++dx) for_cell(G, srt, st, blk, cx + dx, cy + dy, X, Y, q, f);
+        } else if (ring <= rmx) {
+            for_cell(G, srt, st, blk, cx - ring, cy + dy, X, Y, q, f);
+            for_cell(G, srt, st, blk, cx + ring, cy + dy, X, Y, q, f);
+        }
+    }
+}
+
+// The k-th smallest distance so far: an ascending list whose first KMAX - k
+// entries hold -1, updated by a min/max pass (no branches, no indices).
+template <int KMAX>
+__device__ __forceinline__ void kth_offer(float (&d)[KMAX], float d2)
+{
+    if (d2 < d[KMAX - 1]) {
+        float x = d2;
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) {
+            const float lo = fminf(d[s], x);
+            x = fmaxf(d[s], x);
+            d[s] = lo;
+        }
+    }
+}
+
+// sin and cos of o theta for |theta| <= pi and an order o <= 64: Cody-Waite
+// reduction (Cody and Waite, "Software Manual for the Elementary Functions",
+// 1980) of o theta by 2 pi split into a float head and tail, then the hardware
+// sine and cosine on [-pi, pi].
+__device__ __forceinline__ void sincos_order(float t, int order, float &sn, float &cs)
+{
+    const float x = t * (float)order;
+    const float m = rintf(x * 0.15915494309189535f);              // 1 / (2 pi)
+    float r = fmaf(-m, 6.28318548202514648f, x);                  // 2 pi rounded to float
+    r = fmaf(-m, -1.7484556025237907e-07f, r);                    // 2 pi minus that
+    __sincosf(r, &sn, &cs);
+}
+
+// Orientation term of neighbour j: (cos, sin) of o theta_j for its image
+// (mirrored in x: theta -> pi - theta; in y: theta -> -theta).
+template <int MODEL>
+__device__ __forceinline__ void image_cos_sin(float tj, unsigned flips, int order, float &cs, float &sn)
+{
+    if (MODEL == 1 && order != 1) sincos_order(tj, order, sn, cs);
+    else __sincosf(tj, &sn, &cs);                // |theta| <= pi
+    if (flips & 1u) {
+        if (MODEL != 1 || (order & 1)) cs = -cs; else sn = -sn;
+    }
+    if (flips & 2u) sn = -sn;
 }
 
 // Neighbour sums over a finished list (ascending distance, id, image):
@@ -245,14 +317,8 @@ __device__ __forceinline__ void list_sums(const float (&d)[KMAX], const unsigned
         if (d[s] >= 0.0f && d[s] < __int_as_float(0x7f800000)) {
             const unsigned rf = ref[s];
             const int4 rj = srt[rf & 0x3fffffffu];
-            const float tj = __int_as_float(rj.z);
             float sn, cs;
-            if (MODEL == 1 && order != 1) sincosf(tj * (float)order, &sn, &cs);
-            else __sincosf(tj, &sn, &cs);
-            if (rf & (1u << 30)) {                   // mirrored in x: theta -> pi - theta
-                if (MODEL != 1 || (order & 1)) cs = -cs; else sn = -sn;
-            }
-            if (rf & (2u << 30)) sn = -sn;           // mirrored in y: theta -> -theta
+            image_cos_sin<MODEL>(__int_as_float(rj.z), rf >> 30, order, cs, sn);
             ++nb;
             if (MODEL == 1) {
                 const float t = oci * sn - osi * cs;             // sin(o (theta_j - theta_i))
@@ -269,12 +335,12 @@ __device__ __forceinline__ void list_sums(const float (&d)[KMAX], const unsigned
     }
 }
 
-// The k nearest by exhaustive scan of all n records (out of line: it only
-// runs when a periodic window cannot certify the list, i.e. for systems with
-// about k particles or fewer across half the box).  out: sum cos, sum sin,
-// Langevin sum; returns |Omega_i|.
+// The k nearest by exhaustive scan of all n records (only for a periodic
+// window that cannot certify the list, i.e. systems with about k particles or
+// fewer across half the box).  out: sum cos, sum sin, Langevin sum; returns
+// |Omega_i|.
 template <int MODEL, int KMAX>
-__device__ __noinline__ int brute_sums(const MfGeo &G, const int4 *__restrict__ srt, const Sys &S, const float *grow,
+__device__ __forceinline__ int brute_sums(const MfGeo &G, const int4 *__restrict__ srt, const Sys &S, const float *grow,
                                        long long n, long long q, int X, int Y, int k, int order, float ci, float si,
                                        float oci, float osi, float *out)
 {
@@ -328,6 +394,192 @@ __device__ __noinline__ int brute_sums(const MfGeo &G, const int4 *__restrict__ 
     return nb;
 }
 
+// The k nearest over rings 0 .. rfin with the full (distance, id, image)
+// order, for the rare particle whose k-th distance is shared by several
+// candidates.  Same outputs as brute_sums.
+template <int MODEL, int KMAX>
+__device__ __forceinline__ int exact_sums(const MfGeo &G, const int4 *__restrict__ srt, const int *__restrict__ st,
+                                       const int *__restrict__ blk, const Sys &S, const float *grow, int rfin,
+                                       int rmx, int rmy, int cx, int cy, long long q, int X, int Y, int k,
+                                       int order, float ci, float si, float oci, float osi, float *out)
+{
+    float d[KMAX];
+    unsigned key[KMAX], ref[KMAX];
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) {
+        const bool dummy = s < KMAX - k;
+        d[s] = dummy ? -1.0f : __int_as_float(0x7f800000);
+        key[s] = dummy ? 0u : 0xffffffffu;
+        ref[s] = 0u;
+    }
+    for (int ring = 0; ring <= rfin; ++ring)
+        for_ring(G, srt, st, blk, ring, rmx, rmy, cx, cy, X, Y, q,
+                 [&](float d2, const int4 &rj, int j, unsigned code, unsigned flips) {
+                     topk_offer<KMAX>(d, key, ref, d2, (unsigned)rj.w * 9u + code, (unsigned)j | (flips << 30));
+                 });
+    float sc = 0.f, ss = 0.f, tsum = 0.f;
+    int nb = 0;
+    list_sums<MODEL, KMAX>(d, ref, srt, S, grow, order, ci, si, oci, osi, sc, ss, tsum, nb);
+    out[0] = sc;
+    out[1] = ss;
+    out[2] = tsum;
+    return nb;
+}
+
+// Geometry of the flat system, read once per thread.
+__device__ __forceinline__ MfGeo mf_geo(const Sys &S)
+{
+    MfGeo G;
+    G.ncx = S.ncx;
+    G.ncy = S.ncy;
+    G.W = S.ncx << S.sx;
+    G.H = S.ncy << S.sy;
+    G.ux = S.ux;
+    G.uy = S.uy;
+    G.bx = S.bx != 0;
+    G.by = S.by != 0;
+    return G;
+}
+
+// One particle's own quantities and its search window.
+struct MfSelf {
+    int X, Y, cx, cy, rmx, rmy, sp;
+    float thi, ci, si, oci, osi;     // theta, cos/sin theta, cos/sin of o theta
+    unsigned id;
+    const float *grow;               // Gamma_{s_i .} dt with several species (Langevin), else null
+};
+
+template <int MODEL>
+__device__ __forceinline__ MfSelf mf_self(const Sys &S, const MfGeo &G, int4 r)
+{
+    MfSelf P;
+    P.X = r.x;
+    P.Y = r.y;
+    P.thi = __int_as_float(r.z);
+    P.id = (unsigned)r.w;
+    P.cx = min(P.X >> S.sx, G.ncx - 1);
+    P.cy = min(P.Y >> S.sy, G.ncy - 1);
+    // a periodic window stops short of wrapping onto itself, a reflecting
+    // one at the outermost mirror image
+    P.rmx = G.bx ? max(P.cx + G.ncx, 2 * G.ncx - 1 - P.cx) : (G.ncx - 1) / 2;
+    P.rmy = G.by ? max(P.cy + G.ncy, 2 * G.ncy - 1 - P.cy) : (G.ncy - 1) / 2;
+    __sincosf(P.thi, &P.si, &P.ci);              // |theta| <= pi
+    P.oci = P.ci;
+    P.osi = P.si;
+    if (MODEL == 1 && S.order != 1) sincos_order(P.thi, S.order, P.osi, P.oci);
+    P.sp = S.nsp > 1 ? species_of(S, P.id) : 0;
+    P.grow = (MODEL == 1 && S.nsp > 1) ? S.sp_gamma_dt + P.sp * kMaxSpecies : nullptr;
+    return P;
+}
+
+// Integer contributions of one particle to the step's sums (p, q, |Omega|).
+struct MfAcc {
+    long long c, s, n, c2, s2;
+};
+
+// The update of particle q from its neighbour sums (sc, ss: VM / NVM sum S_i
+// including e^{i theta_i}; tsum: Langevin sum, Gamma dt already inside with
+// several species): noise, Eq. (collision) or the Euler-Maruyama step with
+// h = 1 (Sec. 2.3), streaming, the boundary rule (Sec. 2.4) in fixed point,
+// the new record, histograms and sums.
+template <int MODEL>
+__device__ __forceinline__ void mf_finish(const Sys &S, const MfGeo &G, const MfSelf &P, long long step, int nxt,
+                                          long long q, float sc, float ss, float tsum, int nb, bool measure,
+                                          int *s_hist, MfAcc &acc)
+{
+    if (measure) {
+        int bt = (int)floorf((P.thi + AAP_PI_F) * ((float)S.bins_theta * (1.0f / AAP_2PI_F)));
+        bt = min(max(bt, 0), S.bins_theta - 1);
+        atomicAdd(&s_hist[bt], 1);
+        atomicAdd(&s_hist[S.bins_theta + min(nb, S.bins_nbr - 1)], 1);
+    }
+    uint32_t c4[4] = {P.id, (uint32_t)step, (uint32_t)((unsigned long long)step >> 32), 0u};
+    philox4x32_10(c4, S.seed_lo, S.seed_hi);
+    const float u0 = u01f(c4[0]);
+    const int sp = P.sp;
+    float thn, cn = 0.f, sn = 0.f;
+    int dX, dY;
+    if (MODEL != 1) {
+        // Eq. (collision_VM) / (collision_NVM) + noise; Eq. (streaming)
+        thn = atan2f(ss, sc) + S.sp_omega_step[sp] + S.sp_eta_pi[sp] * (2.0f * u0 - 1.0f);
+        __sincosf(thn, &sn, &cn);
+        dX = __float2int_rn(S.sp_kx[sp] * cn);
+        dY = __float2int_rn(S.sp_ky[sp] * sn);
+    } else {
+        // Eq. (Langevin_dynamics) with h = 1 (Sec. 2.3), one Euler-Maruyama step
+        const float u1 = u01f(c4[1]);
+        const float gz = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
+        thn = P.thi + (P.grow ? tsum : S.gamma_dt * tsum) + S.sp_omega_step[sp] + S.sp_noise_amp[sp] * gz;
+        dX = __float2int_rn(S.sp_kx[sp] * P.ci);
+        dY = __float2int_rn(S.sp_ky[sp] * P.si);
+    }
+    int Xn = P.X + dX, Yn = P.Y + dY;
+    bool fx = false, fy = false;
+    if (Xn < 0) {
+        if (G.bx) { Xn = -Xn; fx = true; } else Xn += G.W;
+    } else if (Xn >= G.W) {
+        if (G.bx) {
+            if (Xn == G.W) Xn = G.W - 1; else { Xn = 2 * G.W - Xn; fx = true; }
+        } else Xn -= G.W;
+    }
+    if (Yn < 0) {
+        if (G.by) { Yn = -Yn; fy = true; } else Yn += G.H;
+    } else if (Yn >= G.H) {
+        if (G.by) {
+            if (Yn == G.H) Yn = G.H - 1; else { Yn = 2 * G.H - Yn; fy = true; }
+        } else Yn -= G.H;
+    }
+    if (fx) { thn = AAP_PI_F - thn; cn = -cn; }
+    if (fy) { thn = -thn; sn = -sn; }
+    if (thn >= AAP_PI_F || thn < -AAP_PI_F)
+        thn -= AAP_2PI_F * floorf((thn + AAP_PI_F) * (1.0f / AAP_2PI_F));
+    if (MODEL == 1) __sincosf(thn, &sn, &cn);
+    if (!isfinite(thn)) atomicOr(S.err, ERR_NAN);
+    S.rec[nxt][q] = make_int4(Xn, Yn, __float_as_int(thn), (int)P.id);
+    acc.c += __float2int_rn(cn * kFixStepF);
+    acc.s += __float2int_rn(sn * kFixStepF);
+    acc.c2 += __float2int_rn(fmaf(cn, cn, -sn * sn) * kFixStepF);
+    acc.s2 += __float2int_rn(2.0f * cn * sn * kFixStepF);
+    acc.n += nb;
+    if (S.nbr_out && P.id < (unsigned long long)S.n) S.nbr_out[P.id] = nb;
+}
+
+// Block sums into the step's accumulators; the block's histogram counts.
+template <int NT>
+__device__ __forceinline__ void mf_flush(const Sys &S, int cur, MfAcc acc, long long (*s_red)[NT / 32],
+                                         bool measure, const int *s_hist)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    acc.c = warp_sum_ll(acc.c);
+    acc.s = warp_sum_ll(acc.s);
+    acc.n = warp_sum_ll(acc.n);
+    acc.c2 = warp_sum_ll(acc.c2);
+    acc.s2 = warp_sum_ll(acc.s2);
+    if (lane == 0) {
+        s_red[0][warp] = acc.c;
+        s_red[1][warp] = acc.s;
+        s_red[2][warp] = acc.n;
+        s_red[3][warp] = acc.c2;
+        s_red[4][warp] = acc.s2;
+    }
+    __syncthreads();
+    if (tid < 5) {
+        long long v = 0;
+        for (int w = 0; w < NT / 32; ++w) v += s_red[tid][w];
+        unsigned long long *slot = S.acc + ((size_t)cur * kAccSlots + (blockIdx.x & (kAccSlots - 1))) * kAccWords;
+        atomicAdd(slot + tid, (unsigned long long)v);
+    }
+    if (measure)
+        for (int i = tid; i < S.bins_theta + S.bins_nbr; i += NT)
+            if (s_hist[i]) atomicAdd(S.hist + i, (unsigned long long)s_hist[i]);
+}
+
+// One thread per record in cell order.  Pass 1 finds the k-th smallest
+// distance tau by the ring search (Sec. 3.3); pass 2 sums over the candidates
+// below tau and at tau in 2^32 fixed point, so that the sums do not depend on
+// the arrival order inside a cell.  Particles whose window cannot certify the
+// list, or with several candidates at exactly tau, are queued for
+// k_mf_exact and left to it.
 template <int NT, int MODEL, int KMAX>
 __global__ void __launch_bounds__(NT) k_mf_update(const Sys *__restrict__ sys, const Ctl *__restrict__ ctl)
 {
@@ -338,178 +590,129 @@ __global__ void __launch_bounds__(NT) k_mf_update(const Sys *__restrict__ sys, c
     const int cur = (int)(step & 1), nxt = cur ^ 1;
     const long long n = S.n;
     const int sx = S.sx, sy = S.sy, k = S.knn;
-    MfGeo G;
-    G.ncx = S.ncx;
-    G.ncy = S.ncy;
-    G.W = S.ncx << sx;
-    G.H = S.ncy << sy;
-    G.ux = S.ux;
-    G.uy = S.uy;
-    G.bx = S.bx != 0;
-    G.by = S.by != 0;
+    const MfGeo G = mf_geo(S);
     const int4 *__restrict__ srt = S.mf_sorted;
     const int *__restrict__ st = S.mf_start;
     const int *__restrict__ blk = S.mf_blk;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool measure = step < S.meas_until;       // on-the-fly histograms (Sec. 3.4)
-    const int nbins = S.bins_theta + S.bins_nbr;
     if (measure)
-        for (int i = tid; i < nbins; i += NT) s_hist[i] = 0;
+        for (int i = threadIdx.x; i < S.bins_theta + S.bins_nbr; i += NT) s_hist[i] = 0;
     __syncthreads();
-    long long acc_c = 0, acc_s = 0, acc_n = 0, acc_c2 = 0, acc_s2 = 0;
-    const long long q = blockIdx.x * (long long)NT + tid;
+    MfAcc acc = {0, 0, 0, 0, 0};
+    const long long q = blockIdx.x * (long long)NT + threadIdx.x;
     if (q < n) {
-        const int4 r = srt[q];
-        const int X = r.x, Y = r.y;
-        const float thi = __int_as_float(r.z);
-        const unsigned id = (unsigned)r.w;
-        const int cx = min(X >> sx, G.ncx - 1), cy = min(Y >> sy, G.ncy - 1);
+        const MfSelf P = mf_self<MODEL>(S, G, srt[q]);
         float d[KMAX];
-        unsigned key[KMAX], ref[KMAX];
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) {
-            const bool dummy = s < KMAX - k;
-            d[s] = dummy ? -1.0f : __int_as_float(0x7f800000);
-            key[s] = dummy ? 0u : 0xffffffffu;
-            ref[s] = 0u;
-        }
-        // ring search (Sec. 3.3); a periodic window stops short of wrapping
-        // onto itself, a reflecting one at the outermost mirror image
-        const int rmx = G.bx ? max(cx + G.ncx, 2 * G.ncx - 1 - cx) : (G.ncx - 1) / 2;
-        const int rmy = G.by ? max(cy + G.ncy, 2 * G.ncy - 1 - cy) : (G.ncy - 1) / 2;
+        for (int s = 0; s < KMAX; ++s) d[s] = s < KMAX - k ? -1.0f : __int_as_float(0x7f800000);
         bool certified = false;
+        int rfin = 0;
         for (int ring = 0;; ++ring) {
-            const int rx = min(ring, rmx), ry = min(ring, rmy);
-            for (int dy = -ry; dy <= ry; ++dy) {
-                if (dy == -ring || dy == ring) {
-                    for (int dx = -rx; dx <= rx; ++dx)
-                        visit_cell<KMAX>(G, srt, st, blk, cx + dx, cy + dy, X, Y, q, d, key, ref);
-                } else if (ring <= rmx) {
-                    visit_cell<KMAX>(G, srt, st, blk, cx - ring, cy + dy, X, Y, q, d, key, ref);
-                    visit_cell<KMAX>(G, srt, st, blk, cx + ring, cy + dy, X, Y, q, d, key, ref);
-                }
-            }
+            for_ring(G, srt, st, blk, ring, P.rmx, P.rmy, P.cx, P.cy, P.X, P.Y, q,
+                     [&](float d2, const int4 &, int, unsigned, unsigned) { kth_offer<KMAX>(d, d2); });
             // every unvisited candidate lies at least this far away
+            const int rx = min(ring, P.rmx), ry = min(ring, P.rmy);
             float gx = __int_as_float(0x7f800000), gy = gx;
-            const int lo = cx - rx, hi = cx + rx, lo2 = cy - ry, hi2 = cy + ry;
-            if (!(G.bx && lo <= -G.ncx)) gx = (float)(X - lo * (1 << sx)) * G.ux;
-            if (!(G.bx && hi >= 2 * G.ncx - 1)) gx = fminf(gx, (float)((hi + 1) * (1 << sx) - X) * G.ux);
-            if (!(G.by && lo2 <= -G.ncy)) gy = (float)(Y - lo2 * (1 << sy)) * G.uy;
-            if (!(G.by && hi2 >= 2 * G.ncy - 1)) gy = fminf(gy, (float)((hi2 + 1) * (1 << sy) - Y) * G.uy);
+            const int lo = P.cx - rx, hi = P.cx + rx, lo2 = P.cy - ry, hi2 = P.cy + ry;
+            if (!(G.bx && lo <= -G.ncx)) gx = (float)(P.X - lo * (1 << sx)) * G.ux;
+            if (!(G.bx && hi >= 2 * G.ncx - 1)) gx = fminf(gx, (float)((hi + 1) * (1 << sx) - P.X) * G.ux);
+            if (!(G.by && lo2 <= -G.ncy)) gy = (float)(P.Y - lo2 * (1 << sy)) * G.uy;
+            if (!(G.by && hi2 >= 2 * G.ncy - 1)) gy = fminf(gy, (float)((hi2 + 1) * (1 << sy) - P.Y) * G.uy);
             const float g = fminf(gx, gy);
             if (d[KMAX - 1] <= g * g * 0.99999f) {
                 certified = true;
+                rfin = ring;
                 break;
             }
-            if (ring >= rmx && ring >= rmy) break;
+            if (ring >= P.rmx && ring >= P.rmy) break;
         }
-        // sums over Omega_i in (distance, id, image) order
-        float si, ci;
-        __sincosf(thi, &si, &ci);                    // |theta| <= pi
-        float oci = ci, osi = si;                    // cos, sin of o theta_i
-        if (MODEL == 1 && S.order != 1) sincosf(thi * (float)S.order, &osi, &oci);
-        float sc = MODEL == 1 ? 0.f : ci, ss = MODEL == 1 ? 0.f : si, tsum = 0.f;
-        int nb = 0;
-        const int sp = S.nsp > 1 ? species_of(S, id) : 0;
-        const float *grow = (MODEL == 1 && S.nsp > 1) ? S.sp_gamma_dt + sp * kMaxSpecies : nullptr;
+        bool queued = !certified;
         if (certified) {
-            list_sums<MODEL, KMAX>(d, ref, srt, S, grow, S.order, ci, si, oci, osi, sc, ss, tsum, nb);
-        } else {
-            // the periodic window is exhausted: the definition itself, over
-            // every particle at its nearest periodic copy (and mirror images)
-            float out[3];
-            nb = brute_sums<MODEL, KMAX>(G, srt, S, grow, n, q, X, Y, k, S.order, ci, si, oci, osi, out);
-            sc += out[0];
-            ss += out[1];
-            tsum = out[2];
+            const float tau = d[KMAX - 1];
+            long long a0 = 0, a1 = 0;
+            int nlt = 0, neq = 0;
+            const int order = S.order;
+            for (int ring = 0; ring <= rfin; ++ring)
+                for_ring(G, srt, st, blk, ring, P.rmx, P.rmy, P.cx, P.cy, P.X, P.Y, q,
+                         [&](float d2, const int4 &rj, int, unsigned, unsigned flips) {
+                             if (d2 > tau) return;
+                             float cs, sn;
+                             image_cos_sin<MODEL>(__int_as_float(rj.z), flips, order, cs, sn);
+                             if (MODEL == 1) {
+                                 float t = P.osi * -cs + P.oci * sn;      // sin(o (theta_j - theta_i))
+                                 if (P.grow) t *= P.grow[species_of(S, (unsigned)rj.w)];
+                                 a0 += __float2ll_rn(t * kFix32F);
+                             } else {
+                                 if (MODEL == 2 && fmaf(P.ci, cs, P.si * sn) < 0.f) {   // Eq. (collision_NVM)
+                                     cs = -cs;
+                                     sn = -sn;
+                                 }
+                                 a0 += __float2ll_rn(cs * kFix32F);
+                                 a1 += __float2ll_rn(sn * kFix32F);
+                             }
+                             if (d2 < tau) ++nlt; else ++neq;
+                         });
+            if (nlt + neq <= k) {
+                const float f0 = (float)a0 * (1.0f / kFix32F), f1 = (float)a1 * (1.0f / kFix32F);
+                mf_finish<MODEL>(S, G, P, step, nxt, q, P.ci + f0, P.si + f1, f0, nlt + neq, measure, s_hist, acc);
+            } else {
+                queued = true;                       // several candidates at exactly tau
+            }
         }
-        if (measure) {
-            int bt = (int)floorf((thi + AAP_PI_F) * ((float)S.bins_theta * (1.0f / AAP_2PI_F)));
-            bt = min(max(bt, 0), S.bins_theta - 1);
-            atomicAdd(&s_hist[bt], 1);
-            atomicAdd(&s_hist[S.bins_theta + min(nb, S.bins_nbr - 1)], 1);
+        if (queued) {
+            const int e = atomicAdd(S.mf_nfix, 1);
+            S.mf_fix[e] = make_int2((int)q, certified ? rfin : -1);
         }
-        uint32_t c4[4] = {id, (uint32_t)step, (uint32_t)((unsigned long long)step >> 32), 0u};
-        philox4x32_10(c4, S.seed_lo, S.seed_hi);
-        const float u0 = u01f(c4[0]);
-        float thn, cn = 0.f, sn = 0.f;
-        int dX, dY;
-        if (MODEL != 1) {
-            // Eq. (collision_VM) / (collision_NVM) + noise; Eq. (streaming)
-            thn = atan2f(ss, sc) + S.sp_omega_step[sp] + S.sp_eta_pi[sp] * (2.0f * u0 - 1.0f);
-            __sincosf(thn, &sn, &cn);
-            dX = __float2int_rn(S.sp_kx[sp] * cn);
-            dY = __float2int_rn(S.sp_ky[sp] * sn);
-        } else {
-            // Eq. (Langevin_dynamics) with h = 1 (Sec. 2.3), one Euler-Maruyama step
-            const float u1 = u01f(c4[1]);
-            const float gz = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
-            thn = thi + (grow ? tsum : S.gamma_dt * tsum) + S.sp_omega_step[sp] + S.sp_noise_amp[sp] * gz;
-            dX = __float2int_rn(S.sp_kx[sp] * ci);
-            dY = __float2int_rn(S.sp_ky[sp] * si);
-        }
-        // boundary rule (Sec. 2.4) in exact fixed point
-        int Xn = X + dX, Yn = Y + dY;
-        bool fx = false, fy = false;
-        if (Xn < 0) {
-            if (G.bx) { Xn = -Xn; fx = true; } else Xn += G.W;
-        } else if (Xn >= G.W) {
-            if (G.bx) {
-                if (Xn == G.W) Xn = G.W - 1; else { Xn = 2 * G.W - Xn; fx = true; }
-            } else Xn -= G.W;
-        }
-        if (Yn < 0) {
-            if (G.by) { Yn = -Yn; fy = true; } else Yn += G.H;
-        } else if (Yn >= G.H) {
-            if (G.by) {
-                if (Yn == G.H) Yn = G.H - 1; else { Yn = 2 * G.H - Yn; fy = true; }
-            } else Yn -= G.H;
-        }
-        if (fx) { thn = AAP_PI_F - thn; cn = -cn; }
-        if (fy) { thn = -thn; sn = -sn; }
-        if (thn >= AAP_PI_F || thn < -AAP_PI_F)
-            thn -= AAP_2PI_F * floorf((thn + AAP_PI_F) * (1.0f / AAP_2PI_F));
-        if (MODEL == 1) __sincosf(thn, &sn, &cn);
-        if (!isfinite(thn)) atomicOr(S.err, ERR_NAN);
-        S.rec[nxt][q] = make_int4(Xn, Yn, __float_as_int(thn), (int)id);
-        acc_c = __float2int_rn(cn * kFixStepF);
-        acc_s = __float2int_rn(sn * kFixStepF);
-        acc_c2 = __float2int_rn(fmaf(cn, cn, -sn * sn) * kFixStepF);
-        acc_s2 = __float2int_rn(2.0f * cn * sn * kFixStepF);
-        acc_n = nb;
-        if (S.nbr_out && id < (unsigned long long)n) S.nbr_out[id] = nb;
     }
-    acc_c = warp_sum_ll(acc_c);
-    acc_s = warp_sum_ll(acc_s);
-    acc_n = warp_sum_ll(acc_n);
-    acc_c2 = warp_sum_ll(acc_c2);
-    acc_s2 = warp_sum_ll(acc_s2);
-    if (lane == 0) {
-        s_red[0][warp] = acc_c;
-        s_red[1][warp] = acc_s;
-        s_red[2][warp] = acc_n;
-        s_red[3][warp] = acc_c2;
-        s_red[4][warp] = acc_s2;
-    }
-    __syncthreads();
-    if (tid < 5) {
-        long long v = 0;
-        for (int w = 0; w < NT / 32; ++w) v += s_red[tid][w];
-        unsigned long long *slot = S.acc + ((size_t)cur * kAccSlots + (blockIdx.x & (kAccSlots - 1))) * kAccWords;
-        atomicAdd(slot + tid, (unsigned long long)v);
-    }
+    mf_flush<NT>(S, cur, acc, s_red, measure, s_hist);
+    if (blockIdx.x == 0 && threadIdx.x == 0) S.cnt[nxt][0] = (int)n;   // all records in region 0 of tile 0
+}
+
+// The queued particles: the k nearest with the full (distance, id, image)
+// order, over the certified rings (ties at tau) or over every particle (a
+// periodic window that cannot certify: systems of about k particles or fewer
+// across half the box).
+template <int NT, int MODEL, int KMAX>
+__global__ void __launch_bounds__(NT) k_mf_exact(const Sys *__restrict__ sys, const Ctl *__restrict__ ctl)
+{
+    extern __shared__ int s_hist[];
+    __shared__ long long s_red[5][NT / 32];
+    const Sys &S = *sys;
+    const long long step = ctl->step;
+    const int cur = (int)(step & 1), nxt = cur ^ 1;
+    const MfGeo G = mf_geo(S);
+    const bool measure = step < S.meas_until;
     if (measure)
-        for (int i = tid; i < nbins; i += NT)
-            if (s_hist[i]) atomicAdd(S.hist + i, (unsigned long long)s_hist[i]);
-    if (blockIdx.x == 0 && tid == 0) S.cnt[nxt][0] = (int)n;   // all records in region 0 of tile 0
+        for (int i = threadIdx.x; i < S.bins_theta + S.bins_nbr; i += NT) s_hist[i] = 0;
+    __syncthreads();
+    MfAcc acc = {0, 0, 0, 0, 0};
+    const int nfix = *S.mf_nfix;
+    for (int e = blockIdx.x * NT + threadIdx.x; e < nfix; e += gridDim.x * NT) {
+        const int2 f = S.mf_fix[e];
+        const long long q = f.x;
+        const MfSelf P = mf_self<MODEL>(S, G, S.mf_sorted[q]);
+        float out[3];
+        int nb;
+        if (f.y >= 0)
+            nb = exact_sums<MODEL, KMAX>(G, S.mf_sorted, S.mf_start, S.mf_blk, S, P.grow, f.y, P.rmx, P.rmy, P.cx,
+                                         P.cy, q, P.X, P.Y, S.knn, S.order, P.ci, P.si, P.oci, P.osi, out);
+        else
+            nb = brute_sums<MODEL, KMAX>(G, S.mf_sorted, S, P.grow, S.n, q, P.X, P.Y, S.knn, S.order, P.ci, P.si,
+                                         P.oci, P.osi, out);
+        const float sc = (MODEL == 1 ? 0.f : P.ci) + out[0], ss = (MODEL == 1 ? 0.f : P.si) + out[1];
+        mf_finish<MODEL>(S, G, P, step, nxt, q, sc, ss, out[2], nb, measure, s_hist, acc);
+    }
+    mf_flush<NT>(S, cur, acc, s_red, measure, s_hist);
 }
 
 template <int MODEL, int KMAX>
 cudaError_t launch_update(const LaunchCfg &L, cudaStream_t st)
 {
     const long long blocks = (L.mf_n + kMfThreads - 1) / kMfThreads;
-    k_mf_update<kMfThreads, MODEL, KMAX><<<(unsigned)blocks, kMfThreads, (size_t)L.hist_words * sizeof(int), st>>>(
-        L.sys, L.ctl);
+    const size_t smem = (size_t)L.hist_words * sizeof(int);
+    k_mf_update<kMfThreads, MODEL, KMAX><<<(unsigned)blocks, kMfThreads, smem, st>>>(L.sys, L.ctl);
+    k_mf_exact<64, MODEL, KMAX><<<(unsigned)std::min<long long>((L.mf_n + 63) / 64, 1024), 64, smem, st>>>(L.sys,
+                                                                                                           L.ctl);
     return cudaGetLastError();
 }
 
