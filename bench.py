@@ -111,7 +111,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for fn in ("aap_kernels.cu", "aap_internal.cuh"):
+    for fn in ("aap_kernels.cu", "aap_internal.cuh", "aap_device.cuh"):
         with open(os.path.join(ROOT, "paper_2211_15630_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -395,6 +395,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--tile", type=str, default="0x0")
+    ap.add_argument("--kn", type=int, default=0,
+                    help="k > 0: the metric-free variant (k nearest neighbours, Sec. 2.3) of the workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -424,7 +426,7 @@ def main():
 
     def make(eta, seed):
         p = A.aap_params_default(n=args.n, lx=args.L, ly=args.L, r=1.0, v=0.5, eta=eta,
-                                 seed=seed, threads=args.threads, tile_w=tw, tile_h=th_)
+                                 seed=seed, threads=args.threads, tile_w=tw, tile_h=th_, kn=args.kn)
         return p, A.aap_create(p, stream.cuda_stream)
 
     def timed(h, k):
@@ -509,26 +511,32 @@ def main():
     peak, peak_kind = _peaks()
     kstep_ms = kms[0] / max(klaunch[0], 1)
     achieved = ALG_BYTES * args.n / (kstep_ms / 1e3) / 1e9
-    traffic = _traffic(args.n)
+    traffic = _traffic(args.n) if args.kn == 0 else None
     csum = clocks.summary(t_begin, t_end)
+    default_size = args.n == N_FULL and args.L == L_FULL
+    workload = ("vicsek_N2^24_L2896_rho2" if default_size else f"vicsek_N{args.n}_L{args.L:g}")
+    if args.kn:
+        workload = "mf" + workload + f"_k{args.kn}"
+    step_kernel = "k_step" if args.kn == 0 else "k_mf_count+scan+scatter+update+exact"
+    launches_per_step = 2 if args.kn == 0 else 7
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (uniform isotropic Philox initial state)",
-        "config": {"workload": "vicsek_N2^24_L2896_rho2", "n": args.n, "L": args.L, "R": 1.0,
+        "config": {"workload": workload, "n": args.n, "L": args.L, "R": 1.0, "kn": args.kn,
                    "v0": 0.5, "eta": args.eta, "boundary": "periodic", "l2": "state > L2 (no flush)",
                    "tile": [lay.tile_w, lay.tile_h], "threads": lay.threads,
                    "stage_cap": lay.stage_cap, "parallelism": "replicas only" if world > 1 else "1 gpu"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_step",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": step_kernel,
                      "kernel_ms": kstep_ms, "peak_kind": peak_kind,
                      "alg_bytes_per_update": ALG_BYTES},
-        "step_kernels_ms": {"k_step": kstep_ms, "k_finish": kms[1] / max(klaunch[1], 1)},
+        "step_kernels_ms": {step_kernel: kstep_ms, "k_finish": kms[1] / max(klaunch[1], 1)},
         "e2e": {"value": e2e_val, "unit": UNIT, "steps": ke,
                 "h2d_bytes_per_step": state_bytes / ke,
                 "d2h_bytes_per_step": (state_bytes + 8 * (ke + 1)) / ke},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": csum,
         "phi_end": float(phi[-1]),
         "mean_neighbours": obs.mean_neighbours,
