@@ -130,6 +130,20 @@ def _traffic(n):
     return float(d["bytes_per_particle"]) * n
 
 
+def replica_throughput(ms_local, units_per_rank, world, dist=None, device="cpu"):
+    """Whole-job throughput of `world` independent replicas (one per rank, no
+    data-path collective): the units all ranks processed over the slowest
+    rank's time (a MAX all-reduce of the per-rank milliseconds).  Returns
+    (units per second, max ms)."""
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return world * units_per_rank / (ms_max / 1e3), ms_max
+
+
 def _cpu_baseline(eta, budget_s=20.0):
     """The oracle as it stands, on all host cores, on the full workload for as
     many steps as fit in about budget_s seconds (at least one)."""
@@ -458,11 +472,7 @@ def main():
     clocks.stop()
     A.aap_sync(h)
     obs = A.aap_observe(h)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * args.n * args.steps / (ms_max / 1e3)
+    value, ms_max = replica_throughput(ms, args.n * args.steps, world, dist, "cuda")
 
     # end to end through the C ABI with host buffers: upload the state from
     # pinned memory, K steps recording p(t) into host memory, download the state
@@ -479,10 +489,7 @@ def main():
     phi = A.aap_phi_trace(h, ke)
     xs2, ys2, ts2 = A.aap_get_state(h, args.n)
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_val = world * args.n * ke / float(e2e_t.item())
+    e2e_val, _ = replica_throughput(e2e_s * 1e3, args.n * ke, world, dist, "cuda")
     state_bytes = args.n * (8 + 8 + 4)
     A.aap_destroy(h)
 
