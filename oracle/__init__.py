@@ -50,6 +50,7 @@ class Params(C.Structure):
         ("nspecies", C.c_int32), ("pad_", C.c_int32), ("species_n", C.c_int64 * 8),
         ("species_v", C.c_double * 8), ("species_eta", C.c_double * 8),
         ("species_omega", C.c_double * 8), ("species_gamma", C.c_double * 64),
+        ("weight_len", C.c_int32), ("pad2_", C.c_int32), ("weight_table", C.c_double * 128),
     ]
 
 
@@ -81,6 +82,8 @@ class Model:
     species_eta: tuple = ()
     species_omega: tuple = ()
     species_gamma: tuple = ()
+    # tabulated Langevin weight h(0), h(1), ... (Sec. 4); empty = `weight`
+    weight_table: tuple = ()
 
     def c(self) -> Params:
         p = Params(self.n, self.lx, self.ly, self.r, self.v, self.eta, self.omega,
@@ -95,6 +98,9 @@ class Model:
             p.species_omega[s] = float(self.species_omega[s]) if self.species_omega else self.omega
             for b in range(ns):
                 p.species_gamma[8 * s + b] = float(self.species_gamma[s][b]) if self.species_gamma else self.gamma
+        p.weight_len = len(self.weight_table)
+        for k, w in enumerate(self.weight_table):
+            p.weight_table[k] = float(w)
         return p
 
 

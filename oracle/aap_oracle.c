@@ -467,8 +467,11 @@ static void update_one(const orc_params *p, const cell_list *cl, const double *x
         xn = x[i] + v * cos(tn);
         yn = y[i] + v * sin(tn);
     } else {
-        /* metric-free: h = 1 (Sec. 2.3, the weight is absorbed in Gamma) */
+        /* metric-free: h = 1 (Sec. 2.3, the weight is absorbed in Gamma); a
+         * tabulated h(n) uses its last entry beyond its length (Sec. 4) */
         double h = (p->weight == 0 && p->kn == 0) ? 1.0 / (1.0 + (double)a.n) : 1.0;
+        if (p->kn == 0 && p->weight_len > 0)
+            h = p->weight_table[a.n < p->weight_len ? a.n : p->weight_len - 1];
         /* Box-Muller Gaussian (Sec. 3.1). */
         double g = sqrt(-2.0 * log(u0)) * cos(2.0 * ORC_PI * u1);
         tn = th[i] + p->dt * (h * a.t + omega) + eta * sqrt(p->dt) * g;

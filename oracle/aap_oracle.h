@@ -66,6 +66,12 @@ typedef struct {
     double   species_eta[8];
     double   species_omega[8];
     double   species_gamma[64];
+    /* Tabulated weight function (Sec. 4, weight_function / weight_vector_length):
+     * with weight_len > 0 the Langevin weight is h(n) = weight_table[min(n, weight_len-1)]
+     * (metric neighbourhoods only; metric-free models use h = 1, Sec. 2.3). */
+    int32_t  weight_len;
+    int32_t  pad2_;
+    double   weight_table[128];
 } orc_params;
 
 /* Species of particle `id` (0 with a single species). */

@@ -600,3 +600,39 @@ def test_species_identical_parameters_reduce_to_one_species(oracle):
                                  species_omega=(0.1, 0.1), species_gamma=G), x, y, th, 2)
     for u, w in zip(a[:3], b[:3]):
         assert np.allclose(u, w, rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------ tabulated weight h(n) -----
+
+def test_weight_table_reduces_to_the_built_in_weights(oracle):
+    """A table h(n) = 1/(1+n) or h = 1 (Sec. 4's weight_function, sampled at
+    n = 0 .. len-1) gives the built-in weights."""
+    n, L = 800, 16.0
+    x, y, th = inputs.uniform_state(n, L, L, 14)
+    kw = dict(n=n, lx=L, ly=L, v=0.3, eta=0.2, gamma=1.4, dt=0.05, model=oracle.LANGEVIN)
+    for weight, table in ((0, tuple(1.0 / (1.0 + k) for k in range(64))), (1, (1.0,) * 3)):
+        a = oracle.step(oracle.Model(**kw, weight=weight), x, y, th, 1)
+        b = oracle.step(oracle.Model(**kw, weight=1 - weight, weight_table=table), x, y, th, 1)
+        for u, w in zip(a[:3], b[:3]):
+            assert np.array_equal(u, w)
+
+
+def test_weight_table_pair_rate_and_clamp(oracle):
+    """A pair at v = eta = 0 relaxes at rate 2 h(1) Gamma (tan(Delta/2) law); a
+    particle with more neighbours than the table covers uses its last entry."""
+    g, dt, T, c = 1.1, 1e-3, 600, 0.37
+    m = oracle.Model(n=2, lx=10.0, ly=10.0, v=0.0, eta=0.0, gamma=g, dt=dt, model=oracle.LANGEVIN,
+                     weight_table=(5.0, c))
+    d0 = 1.0
+    _, _, tT, _ = oracle.run(m, np.array([5.0, 5.5]), np.array([5.0, 5.0]), np.array([d0 / 2, -d0 / 2]), 0, T)
+    expect = 2 * math.atan(math.tan(d0 / 2) * math.exp(-2 * c * g * dt * T))
+    assert abs((tT[0] - tT[1]) - expect) < 5 * dt
+    # four particles within R of each other: n = 3 > len - 1 = 1 -> h = c
+    m4 = oracle.Model(n=4, lx=10.0, ly=10.0, v=0.0, eta=0.0, gamma=g, dt=dt, model=oracle.LANGEVIN,
+                      weight_table=(5.0, c))
+    x = np.array([5.0, 5.3, 5.0, 5.3]); y = np.array([5.0, 5.0, 5.3, 5.3]); th = np.array([0.1, 0.7, -0.4, 1.2])
+    _, _, t1, nb, _, _ = oracle.step(m4, x, y, th, 0)
+    assert (nb == 3).all()
+    for i in range(4):
+        s = sum(math.sin(th[j] - th[i]) for j in range(4) if j != i)
+        assert abs(_wrap(t1[i] - (th[i] + dt * g * c * s))) < 1e-14
