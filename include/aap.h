@@ -117,6 +117,13 @@ typedef struct aap_params {
     double   species_eta[8];
     double   species_omega[8];
     double   species_gamma[64];
+    /* [weight_function, weight_vector_length] (Sec. 4): weight_len in [0, 128];
+     * with weight_len > 0 the Langevin weight is h(n) = weight_table[min(n,
+     * weight_len - 1)] for |Omega_i| = n (the paper evaluates the function once
+     * for n = 0 .. weight_vector_length - 1 and uses the last value beyond);
+     * 0: `weight` decides.  Metric-free models always use h = 1 (Sec. 2.3).   */
+    int32_t  weight_len;
+    double   weight_table[128];
 } aap_params;
 
 /* Observables of the current state (Sec. 3.4). */

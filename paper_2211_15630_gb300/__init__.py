@@ -55,6 +55,7 @@ class aap_params(C.Structure):
         ("binnum_theta", C.c_int32), ("binnum_neighbors", C.c_int32), ("kn", C.c_int32),
         ("nspecies", C.c_int32), ("species_n", C.c_int64 * 8), ("species_v", C.c_double * 8),
         ("species_eta", C.c_double * 8), ("species_omega", C.c_double * 8), ("species_gamma", C.c_double * 64),
+        ("weight_len", C.c_int32), ("weight_table", C.c_double * 128),
     ]
 
 
@@ -194,6 +195,18 @@ def set_species(p: aap_params, counts, v=None, eta=None, omega=None, gamma=None)
         p.species_omega[a] = float(omega[a]) if omega is not None else p.omega
         for b in range(ns):
             p.species_gamma[8 * a + b] = float(gamma[a][b]) if gamma is not None else p.gamma
+    return p
+
+
+def set_weight_table(p: aap_params, values) -> aap_params:
+    """Tabulated Langevin weight h(n) = values[min(n, len-1)] (Sec. 4's
+    weight_function sampled at n = 0 .. len-1; at most 128 values)."""
+    vals = [float(v) for v in values]
+    if len(vals) > 128:
+        raise ValueError("at most 128 weights")
+    p.weight_len = len(vals)
+    for k, v in enumerate(vals):
+        p.weight_table[k] = v
     return p
 
 

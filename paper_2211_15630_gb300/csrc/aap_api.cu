@@ -192,6 +192,9 @@ int check_params(const aap_params *p)
         return fail(AAP_EINVAL, "threads must be 0, 256 or 512");
     if (!finite(p->capacity) || p->capacity < 0 || (p->capacity > 0 && p->capacity < 1))
         return fail(AAP_EINVAL, "capacity must be 0 (automatic) or >= 1");
+    if (p->weight_len < 0 || p->weight_len > 128) return fail(AAP_EINVAL, "weight_len must be in [0, 128]");
+    for (int k = 0; k < p->weight_len; ++k)
+        if (!finite(p->weight_table[k])) return fail(AAP_EINVAL, "weight_table must be finite");
     if (p->binnum_theta < 0 || p->binnum_theta > aapk::kMaxBins || p->binnum_neighbors < 0 ||
         p->binnum_neighbors > aapk::kMaxBins)
         return fail(AAP_EINVAL, "binnum_theta and binnum_neighbors must be in [0, 512]");
@@ -315,6 +318,9 @@ void set_model(Sys &S, const aap_params &p)
     S.seed_lo = (uint32_t)p.seed;
     S.seed_hi = (uint32_t)(p.seed >> 32);
     S.n = p.n;
+    // tabulated weight (Sec. 4); metric-free models use h = 1 (Sec. 2.3)
+    S.wlen = p.kn > 0 ? 0 : p.weight_len;
+    for (int k = 0; k < 128; ++k) S.wtab[k] = k < S.wlen ? (float)p.weight_table[k] : 0.f;
     // species (Sec. 2.5); entry 0 repeats the scalars with a single species
     const bool multi = p.nspecies > 1;
     S.nsp = multi ? p.nspecies : 1;

@@ -102,6 +102,8 @@ struct Sys {
     long long sp_end[8];
     float sp_eta_pi[8], sp_omega_step[8], sp_noise_amp[8], sp_kx[8], sp_ky[8];
     float sp_gamma_dt[64];      // Gamma_{s_i s_j} dt, row s_i
+    int wlen;                   // tabulated Langevin weight h(n), n < wlen (0: none)
+    float wtab[128];
 };
 
 constexpr int kMaxSpecies = 8;

@@ -478,7 +478,8 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             } else {
                 // Eq. (Langevin_dynamics), one Euler-Maruyama step
                 const float u1 = u01f(c4[1]);
-                const float h = S.weight ? 1.0f : 1.0f / (1.0f + (float)nb);
+                const float h = S.wlen > 0 ? S.wtab[min(nb, S.wlen - 1)]
+                                           : (S.weight ? 1.0f : 1.0f / (1.0f + (float)nb));
                 const float tsum = pi.z * ss - pi.w * sc;   // Gamma dt inside with several species
                 const float gz = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
                 const float drift = S.nsp > 1 ? h * tsum : S.gamma_dt * h * tsum;

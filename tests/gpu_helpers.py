@@ -35,6 +35,8 @@ def oracle_model(O, p):
         sp = dict(species_n=tuple(p.species_n[:ns]), species_v=tuple(p.species_v[:ns]),
                   species_eta=tuple(p.species_eta[:ns]), species_omega=tuple(p.species_omega[:ns]),
                   species_gamma=tuple(tuple(p.species_gamma[8 * a: 8 * a + ns]) for a in range(ns)))
+    if p.weight_len > 0:
+        sp["weight_table"] = tuple(p.weight_table[:p.weight_len])
     return O.Model(n=p.n, lx=p.lx, ly=p.ly, r=p.r, v=p.v, eta=p.eta, omega=p.omega,
                    gamma=p.gamma, dt=p.dt, seed=p.seed, model=p.model, order=p.order,
                    weight=p.weight, bx=int(p.bx != 0), by=int(p.by != 0), kn=p.kn, **sp)

@@ -52,7 +52,7 @@ def test_abi_version_and_defaults(lib):
     (dict(binnum_theta=513), "binnum"), (dict(binnum_neighbors=-1), "binnum"),
     (dict(kn=33), "kn"), (dict(kn=-1), "kn"), (dict(kn=4, n=1 << 28), "2^28"),
     (dict(kn=4, v=9.0), "quarter"), (dict(nspecies=9), "nspecies"),
-    (dict(nspecies=2), "add up"),
+    (dict(nspecies=2), "add up"), (dict(weight_len=129), "weight_len"),
 ])
 def test_invalid_parameters(lib, kw, frag):
     with pytest.raises(A.AapError) as e:

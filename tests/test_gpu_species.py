@@ -83,3 +83,30 @@ def test_single_species_list_equals_scalars(lib):
     finally:
         A.aap_destroy(h0)
         A.aap_destroy(h1)
+
+
+def test_weight_table_matches_oracle_and_builtin(lib, oracle):
+    """Tabulated Langevin weight h(n) (Sec. 4): one step against the oracle with
+    a table shorter than the neighbour numbers (its last entry is reused), and
+    an all-ones table equal to h = 1 bit for bit."""
+    p = params(n=12000, lx=80.0, ly=80.0, seed=19, model=A.AAP_LANGEVIN, dt=0.1, gamma=2.0)
+    A.set_weight_table(p, (0.9, 0.5, 0.45, 0.3, 0.22, 0.2, 0.17))
+    h = A.aap_create(p)
+    try:
+        A.aap_step(h, 3)
+        compare_one_step(oracle, p, h)
+    finally:
+        A.aap_destroy(h)
+    p1 = params(n=12000, lx=80.0, ly=80.0, seed=19, model=A.AAP_LANGEVIN, dt=0.1, gamma=2.0,
+                weight=A.AAP_H_ONE)
+    p2 = params(n=12000, lx=80.0, ly=80.0, seed=19, model=A.AAP_LANGEVIN, dt=0.1, gamma=2.0)
+    A.set_weight_table(p2, (1.0, 1.0))
+    h1, h2 = A.aap_create(p1), A.aap_create(p2)
+    try:
+        A.aap_step(h1, 8)
+        A.aap_step(h2, 8)
+        for u, v in zip(A.aap_get_state(h1, p1.n), A.aap_get_state(h2, p2.n)):
+            assert np.array_equal(u, v)
+    finally:
+        A.aap_destroy(h1)
+        A.aap_destroy(h2)
