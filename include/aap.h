@@ -240,6 +240,12 @@ int aap_measure(aap_handle *h, int64_t nsteps);
  * aap_clear_results (like aappp_get_results, Sec. 4).  Synchronises. */
 int aap_get_results(aap_handle *h, aap_results *out);
 
+/* Fault injection for tests: the allocation after n more successful device
+ * allocations of any handle fails with AAP_ENOMEM (the library must then
+ * release everything it holds); n < 0 switches it off.  Not thread-safe with
+ * respect to which call sees the failure. */
+int aap_test_fail_alloc_after(int32_t n);
+
 /* Forget the accumulated measurements (moments and histograms). */
 int aap_clear_results(aap_handle *h);
 

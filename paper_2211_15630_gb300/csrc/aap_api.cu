@@ -4,6 +4,7 @@
 // layout, device allocations, the step loop (optionally replayed from a
 // captured CUDA graph), and the transfers in and out of host memory.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -11,6 +12,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/aap.h"
 #include "aap_internal.cuh"
@@ -29,6 +31,16 @@ int fail(int code, const std::string &msg)
     g_err = msg;
     return code;
 }
+
+// NVTX range around an entry point (tracing; free unless a tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
+// Test hook: the allocation after g_fail_after more successful ones fails
+// (negative: never).  Set through aap_test_fail_alloc_after.
+std::atomic<int> g_fail_after{-1};
 
 #define AAP_CK(call)                                                                    \
     do {                                                                                \
@@ -102,6 +114,10 @@ int dev_alloc(aap_handle *h, T **ptr, size_t bytes)
 {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
+    int left = g_fail_after.load();
+    while (left >= 0 && !g_fail_after.compare_exchange_weak(left, left - 1)) {
+    }
+    if (left == 0) return fail(AAP_ENOMEM, "injected allocation failure (aap_test_fail_alloc_after)");
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1019,6 +1035,12 @@ extern "C" {
 
 const char *aap_last_error(void) { return g_err.c_str(); }
 
+int aap_test_fail_alloc_after(int32_t n)
+{
+    g_fail_after.store(n < 0 ? -1 : n);
+    return AAP_OK;
+}
+
 int32_t aap_abi_version(void) { return 2; }
 
 void aap_params_default(aap_params *p)
@@ -1041,6 +1063,7 @@ void aap_params_default(aap_params *p)
 
 int aap_create(const aap_params *p, void *stream, aap_handle **out)
 {
+    Range range_("aap_create");
     g_err.clear();
     if (!out) return fail(AAP_EINVAL, "out is NULL");
     *out = nullptr;
@@ -1074,6 +1097,7 @@ int aap_destroy(aap_handle *h)
 
 int aap_step(aap_handle *h, int64_t nsteps)
 {
+    Range range_("aap_step");
     if (!h) return fail(AAP_EINVAL, "handle is NULL");
     if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
     if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
@@ -1126,6 +1150,7 @@ int aap_observe(aap_handle *h, aap_obs *out)
 
 int aap_phi_trace(aap_handle *h, int64_t nsteps, double *phi_out)
 {
+    Range range_("aap_phi_trace");
     if (!h || !phi_out) return fail(AAP_EINVAL, "NULL argument");
     if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
     aap_obs ob;
@@ -1134,6 +1159,11 @@ int aap_phi_trace(aap_handle *h, int64_t nsteps, double *phi_out)
     phi_out[0] = ob.phi;
     if (nsteps == 0) return AAP_OK;
     if (h->trace_alloc < nsteps + 1) {
+        // replace the smaller buffers (a failed allocation leaves none)
+        const size_t old = (size_t)h->trace_alloc * sizeof(double);
+        if ((rc = dev_free(h, h->d_trace, old)) || (rc = dev_free(h, h->d_trace_nbar, old))) return rc;
+        h->d_trace = h->d_trace_nbar = nullptr;
+        h->trace_alloc = 0;
         if ((rc = dev_alloc(h, &h->d_trace, (size_t)(nsteps + 1) * sizeof(double)))) return rc;
         if ((rc = dev_alloc(h, &h->d_trace_nbar, (size_t)(nsteps + 1) * sizeof(double)))) return rc;
         h->trace_alloc = nsteps + 1;
@@ -1156,6 +1186,7 @@ int aap_phi_trace(aap_handle *h, int64_t nsteps, double *phi_out)
 
 int aap_get_state(aap_handle *h, double *x, double *y, float *theta, int64_t n)
 {
+    Range range_("aap_get_state");
     if (!h || !x || !y || !theta) return fail(AAP_EINVAL, "NULL argument");
     if (n != h->p.n) return fail(AAP_EINVAL, "n must equal the particle number");
     if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
@@ -1181,6 +1212,7 @@ int aap_get_state(aap_handle *h, double *x, double *y, float *theta, int64_t n)
 int aap_set_state(aap_handle *h, const double *x, const double *y, const float *theta, int64_t n,
                   int64_t step)
 {
+    Range range_("aap_set_state");
     if (!h || (n > 0 && (!x || !y || !theta))) return fail(AAP_EINVAL, "NULL argument");
     if (n != h->p.n) return fail(AAP_EINVAL, "n must equal the particle number");
     if (step < 0) return fail(AAP_EINVAL, "step < 0");
@@ -1210,6 +1242,7 @@ int aap_set_state(aap_handle *h, const double *x, const double *y, const float *
 
 int aap_step_neighbours(aap_handle *h, int32_t *nbr_out, int64_t n)
 {
+    Range range_("aap_step_neighbours");
     if (!h || (n > 0 && !nbr_out)) return fail(AAP_EINVAL, "NULL argument");
     if (n != h->p.n) return fail(AAP_EINVAL, "n must equal the particle number");
     if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
@@ -1232,6 +1265,7 @@ int aap_step_neighbours(aap_handle *h, int32_t *nbr_out, int64_t n)
 
 int aap_measure(aap_handle *h, int64_t nsteps)
 {
+    Range range_("aap_measure");
     if (!h) return fail(AAP_EINVAL, "handle is NULL");
     if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
     if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
@@ -1286,6 +1320,7 @@ int aap_get_histograms(aap_handle *h, double *theta_hist, int32_t nt, double *nb
 
 int aap_save(aap_handle *h, const char *path)
 {
+    Range range_("aap_save");
     if (!h || !path) return fail(AAP_EINVAL, "NULL argument");
     if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
     const int64_t n = h->p.n;
@@ -1317,6 +1352,7 @@ int aap_save(aap_handle *h, const char *path)
 
 int aap_load(const char *path, void *stream, aap_handle **out)
 {
+    Range range_("aap_load");
     if (!path || !out) return fail(AAP_EINVAL, "NULL argument");
     *out = nullptr;
     FileCloser fc{std::fopen(path, "rb")};
@@ -1368,6 +1404,7 @@ int aap_load(const char *path, void *stream, aap_handle **out)
 
 int aap_coarse_grain(aap_handle *h, int32_t nbx, int32_t nby, float *dev_out)
 {
+    Range range_("aap_coarse_grain");
     if (!h || !dev_out) return fail(AAP_EINVAL, "NULL argument");
     if (nbx < 1 || nby < 1 || (long long)nbx * nby > (1ll << 26))
         return fail(AAP_EINVAL, "nbx, nby must be >= 1 with nbx * nby <= 2^26");
@@ -1387,6 +1424,7 @@ int aap_coarse_grain(aap_handle *h, int32_t nbx, int32_t nby, float *dev_out)
 
 int aap_ens_create(const aap_params *params, int32_t count, void *stream, aap_ens **out)
 {
+    Range range_("aap_ens_create");
     g_err.clear();
     if (!out || !params) return fail(AAP_EINVAL, "NULL argument");
     *out = nullptr;
@@ -1436,6 +1474,7 @@ int aap_ens_destroy(aap_ens *e)
 
 int aap_ens_step(aap_ens *e, int64_t nsteps)
 {
+    Range range_("aap_ens_step");
     if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
     if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
     int rc = ens_poll(e);
@@ -1452,6 +1491,7 @@ int aap_ens_step(aap_ens *e, int64_t nsteps)
 
 int aap_ens_measure(aap_ens *e, int64_t nsteps)
 {
+    Range range_("aap_ens_measure");
     if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
     if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
     int rc = ens_poll(e);
@@ -1521,6 +1561,7 @@ int aap_ens_info(aap_ens *e, int32_t *count, int64_t *step)
 
 int aap_ens_autotune(aap_ens *e, int32_t trial_steps, int32_t *policy_out, double *ms_out)
 {
+    Range range_("aap_ens_autotune");
     if (!e) return fail(AAP_EINVAL, "ensemble is NULL");
     if (e->step != 0) return fail(AAP_EINVAL, "autotune is only allowed before the first step");
     if (trial_steps < 1) return fail(AAP_EINVAL, "trial_steps must be >= 1");

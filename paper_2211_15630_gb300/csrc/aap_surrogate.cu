@@ -28,6 +28,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/aap.h"
 #include "../../include/aap_surrogate.h"
@@ -356,6 +357,12 @@ using namespace aaps;
 // ------------------------------------------------------------------ host --
 namespace {
 
+// NVTX range around an entry point (tracing; free unless a tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
 thread_local std::string s_err;
 
 int sfail(int code, const std::string &m)
@@ -513,6 +520,7 @@ void aap_sur_params_default(aap_sur_params *p)
 
 int aap_sur_create(const aap_sur_params *p, void *stream, aap_sur **out)
 {
+    Range range_("aap_sur_create");
     s_err.clear();
     if (!p || !out) return sfail(AAP_EINVAL, "NULL argument");
     *out = nullptr;
@@ -640,6 +648,7 @@ int aap_sur_set_params(aap_sur *s, const float *host, int64_t count)
 int aap_sur_predict(aap_sur *s, const float *dev_in, const float *dev_eta, int32_t batch, int32_t applications,
                     float *dev_out)
 {
+    Range range_("aap_sur_predict");
     if (!s || !dev_in || !dev_eta || !dev_out) return sfail(AAP_EINVAL, "NULL argument");
     if (batch < 1 || batch > s->maxb || applications < 0) return sfail(AAP_EINVAL, "bad batch or applications");
     const int H = s->H, W = s->W;
@@ -666,6 +675,7 @@ int aap_sur_predict(aap_sur *s, const float *dev_in, const float *dev_eta, int32
 int aap_sur_train_step(aap_sur *s, const float *dev_in, const float *dev_target, const float *dev_eta, int32_t batch,
                        double *loss_out)
 {
+    Range range_("aap_sur_train_step");
     if (!s || !dev_in || !dev_target || !dev_eta) return sfail(AAP_EINVAL, "NULL argument");
     if (batch < 1 || batch > s->maxb) return sfail(AAP_EINVAL, "bad batch");
     const int H = s->H, W = s->W;
