@@ -262,3 +262,31 @@ def test_invalid_parameters_rejected(lib):
             A.aap_set_state(h, np.zeros(9), np.zeros(9), np.zeros(9, np.float32))
     finally:
         A.aap_destroy(h)
+
+
+def test_long_run_time_averaged_phi_16_seeds(lib, oracle):
+    """Vicsek N = 8192, L = 64, eta = 0.4, 1000 steps (the small workload):
+    chaotic trajectories part ways after a few steps, so the FP32 GPU and the
+    FP64 oracle are compared statistically.  Per seed 1..16, p(t) averaged over
+    t in [500, 1000); the two 16-seed means agree within 3 sigma, sigma the
+    standard error of their difference (sqrt(s_o^2/16 + s_g^2/16))."""
+    import os
+
+    T, seeds = 1000, range(1, 17)
+    g_means, o_means = [], []
+    for s in seeds:
+        p = params(n=8192, lx=64.0, ly=64.0, r=1.0, v=0.5, eta=0.4, seed=s)
+        h = A.aap_create(p)
+        try:
+            x0, y0, t0 = A.aap_get_state(h, p.n)
+            phi_g = A.aap_phi_trace(h, T)
+        finally:
+            A.aap_destroy(h)
+        m = oracle_model(oracle, p)
+        phi_o = oracle.run(m, x0, y0, t0.astype(np.float64), 0, T, threads=os.cpu_count() or 1)[3]
+        g_means.append(phi_g[T // 2:T].mean())
+        o_means.append(phi_o[T // 2:T].mean())
+    g, o = np.array(g_means), np.array(o_means)
+    sigma = np.sqrt(o.var(ddof=1) / len(o) + g.var(ddof=1) / len(g))
+    assert abs(o.mean() - g.mean()) < 3 * sigma, (o.mean(), g.mean(), sigma)
+    assert 0.05 < g.mean() < 1.0
