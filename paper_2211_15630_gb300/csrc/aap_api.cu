@@ -294,7 +294,7 @@ int set_capacity(aap_handle *h, double factor)
     // shared-memory staging capacity: about twice the mean tile + ring load
     const int nce = (S.twmax + 2) * (S.thmax + 2);
     const double mean_stage = mu * nce;
-    int scap = aapk::round_up((int)std::ceil(1.75 * mean_stage + 128.0), 64);
+    int scap = aapk::round_up((int)std::ceil(1.85 * mean_stage + 128.0), 64);
     scap = std::min(scap, 4096);
     const int own = S.tile_slots;
     const int halo = 2 * (2 * S.cap[0] + S.cap[1]) + 2 * (2 * S.cap[0] + S.cap[3]) + 4 * S.cap[0];

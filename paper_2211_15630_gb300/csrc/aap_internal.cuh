@@ -13,8 +13,9 @@
 //   relative to the tile's lower-left corner with 2^s units per cell side, so
 //   the cell of a particle is X >> s and every wrap or mirror is exact integer
 //   arithmetic.  Regions are filled through warp-aggregated atomic counters;
-//   records inside a region are unordered (the step kernel sorts them by
-//   (cell, id) in shared memory, which makes every sum deterministic).
+//   records inside a region are unordered (the step kernel groups them by
+//   cell in shared memory and sums neighbours in exact integers, so every
+//   result is deterministic whatever the order).
 //   Particles that do not fit their region go to a spill list.
 #pragma once
 
@@ -30,6 +31,7 @@ constexpr int kAccWords = 8;        // sum cos, sin, |Omega|, cos 2theta, sin 2t
 constexpr double kFix = 4294967296.0;     // 2^32: scale of the observation sums
 constexpr float kFixStepF = 1073741824.0f;  // 2^30: scale of the per-step sums
 constexpr double kFixStep = 1073741824.0;
+constexpr float kFixNbF = 4194304.0f;       // 2^22: staged cos / sin as exact integers
 constexpr int kSegs = 25;           // 9 own regions + 16 halo regions
 constexpr int kMaxTile = 64;        // largest tile side in cells
 constexpr int kMaxBins = 512;       // histogram bins (each of theta and |Omega|)
@@ -140,15 +142,14 @@ struct Seg {
 // Per-particle staging arrays of one block: shared memory for ordinary tiles,
 // the block's slice of global scratch for tiles that do not fit.
 struct Stage {
-    float4 *P;                  // sorted by (cell, id): x, y rel. tile centre, cos, sin
+    float4 *P;                  // in cell order: x, y rel. tile centre, then cos, sin as int32 in units of 2^-22
     int *rX, *rY;               // staged, in the tile's extended frame (fixed point)
     float *rth;                 // orientation
     unsigned *id;
     unsigned short *cell;       // extended cell | flip << 14
     unsigned short *slot;       // rank of arrival in the cell
-    unsigned short *gidx;       // grouped-by-cell order -> staged index
-    unsigned short *sk;         // sorted order -> staged index
-    unsigned short *ownq;       // own particle o -> sorted position
+    unsigned short *gidx;       // species by sorted position (several species only)
+    unsigned short *sk;         // cell order -> staged index
     unsigned char *segc;        // segment of staged index 32 i
     int cap;
 };
@@ -157,7 +158,7 @@ __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b *
 
 __host__ __device__ inline size_t stage_bytes(int cap)
 {
-    return (size_t)cap * (16 + 4 * 4 + 5 * 2) + (size_t)round_up(cap / 32 + 2, 16);
+    return (size_t)cap * (16 + 4 * 4 + 4 * 2) + (size_t)round_up(cap / 32 + 2, 16);
 }
 
 __host__ __device__ inline void carve_stage(Stage &st, unsigned char *p, int cap)
@@ -172,7 +173,6 @@ __host__ __device__ inline void carve_stage(Stage &st, unsigned char *p, int cap
     st.slot = (unsigned short *)p;    p += (size_t)cap * 2;
     st.gidx = (unsigned short *)p;    p += (size_t)cap * 2;
     st.sk = (unsigned short *)p;      p += (size_t)cap * 2;
-    st.ownq = (unsigned short *)p;    p += (size_t)cap * 2;
     st.segc = p;
 }
 

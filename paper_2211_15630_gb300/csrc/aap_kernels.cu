@@ -4,9 +4,10 @@
 //   k_step     per tile: stage the tile and its one-cell halo (cell lists,
 //              Sec. 3.2, with periodic or mirror images, Sec. 2.4), counting
 //              sort by cell in shared memory (block histogram + block prefix
-//              scan, then id order inside each cell), sum over the 3x3
-//              cells (Eq. collision_VM / collision_NVM
-//              or the Langevin sum of Eq. Langevin_dynamics), draw Philox
+//              scan; arrival order inside a cell), sum over the 3x3 cells
+//              (Eq. collision_VM / collision_NVM or the Langevin sum of
+//              Eq. Langevin_dynamics) in exact integers, so that the result
+//              does not depend on that arrival order, draw Philox
 //              noise, stream (Eq. streaming or Euler-Maruyama), apply the
 //              boundary rule, and scatter the new record into the region of
 //              its new cell through a warp-aggregated atomic counter.  Also
@@ -228,15 +229,19 @@ __device__ __forceinline__ void tile_setup(TileCtx &T, const Tables &tb, int cur
 
 // The 3x3-cell neighbour sum of one particle (Eq. collision_VM / NVM, or the
 // Langevin coupling sum): rows of three consecutive cells are contiguous in
-// the (cell, id) order.  The particle itself is included: it adds e^{i theta_i}
-// to the VM/NVM sum and sin 0 to the Langevin sum; cnt counts it.
-template <int MODEL>
+// the cell order.  The particle itself is included: it adds e^{i theta_i} to
+// the VM/NVM sum and sin 0 to the Langevin sum; cnt counts it.  The staged
+// (cos, sin) are integers in units of 2^-22 (kFixNb), so the sums are exact and
+// do not depend on the order of the particles inside a cell.  ACC is int for
+// at most 511 candidates (|sum| < 2^31) and long long beyond.
+template <int MODEL, typename ACC>
 __device__ __forceinline__ void neighbour_sum(const float4 *__restrict__ P, const int *cstart, int ec,
-                                              int W2, float4 pi, float r2, float &sc, float &ss, int &cnt)
+                                              int W2, float4 pi, float r2, ACC &sc, ACC &ss, int &cnt)
 {
-    sc = 0.f;
-    ss = 0.f;
+    sc = 0;
+    ss = 0;
     cnt = 0;
+    const float pcf = (float)__float_as_int(pi.z), psf = (float)__float_as_int(pi.w);
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
         const int c0 = ec + dy * W2 - 1;
@@ -247,9 +252,9 @@ __device__ __forceinline__ void neighbour_sum(const float4 *__restrict__ P, cons
             const float dx = pj.x - pi.x, dyy = pj.y - pi.y;
             const float d2 = fmaf(dx, dx, dyy * dyy);
             if (d2 <= r2) {
-                float cj = pj.z, sj = pj.w;
-                if (MODEL == 2 && fmaf(pi.z, cj, pi.w * sj) < 0.f) {
-                    cj = -cj;
+                int cj = __float_as_int(pj.z), sj = __float_as_int(pj.w);
+                if (MODEL == 2 && fmaf(pcf, (float)cj, psf * (float)sj) < 0.f) {
+                    cj = -cj;                         // Eq. (collision_NVM): the reversed direction
                     sj = -sj;
                 }
                 sc += cj;
@@ -261,13 +266,14 @@ __device__ __forceinline__ void neighbour_sum(const float4 *__restrict__ P, cons
 }
 
 // Langevin sums with per-species couplings (Sec. 2.5): each neighbour's
-// (cos o theta_j, sin o theta_j) weighted by grow[species of j] = Gamma_{s_i s_j} dt.
+// (cos o theta_j, sin o theta_j) weighted by grow[species of j] = Gamma_{s_i s_j} dt,
+// rounded to integers in units of 2^-22 and summed exactly (order-free).
 __device__ __forceinline__ void neighbour_sum_sp(const float4 *__restrict__ P, const unsigned short *spc,
                                                  const int *cstart, int ec, int W2, float4 pi, float r2,
-                                                 const float *grow, float &sc, float &ss, int &cnt)
+                                                 const float *grow, long long &sc, long long &ss, int &cnt)
 {
-    sc = 0.f;
-    ss = 0.f;
+    sc = 0;
+    ss = 0;
     cnt = 0;
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
@@ -278,8 +284,8 @@ __device__ __forceinline__ void neighbour_sum_sp(const float4 *__restrict__ P, c
             const float dx = pj.x - pi.x, dyy = pj.y - pi.y;
             if (fmaf(dx, dx, dyy * dyy) <= r2) {
                 const float g = grow[spc[j]];
-                sc = fmaf(g, pj.z, sc);
-                ss = fmaf(g, pj.w, ss);
+                sc += __float2ll_rn(g * (float)__float_as_int(pj.z));
+                ss += __float2ll_rn(g * (float)__float_as_int(pj.w));
                 ++cnt;
             }
         }
@@ -368,10 +374,31 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
     __syncthreads();
     PHASE_MARK(1);
 
-    // --- group by cell; own rows prefix ----------------------------------
+    // --- records into cell order (arrival order inside a cell: the sums are
+    //     exact integers, so this order does not matter); own rows prefix ---
+    const int xc = tw << (S.sx - 1), yc = th << (S.sy - 1);
     for (int k = tid; k < m; k += NT) {
-        const int c = A.cell[k] & 0x3fff;
-        A.gidx[tb.cstart[c] + A.slot[k]] = (unsigned short)k;
+        const unsigned short cf = A.cell[k];
+        const int c = cf & 0x3fff;
+        const int q = tb.cstart[c] + A.slot[k];
+        float thv = A.rth[k];
+        float sn, cs;
+        if (MODEL == 1 && S.order != 1) {
+            thv *= (float)S.order;
+            sincosf(thv, &sn, &cs);
+        } else {
+            // |theta| <= pi: the hardware sine/cosine is within 2^-21.4 absolute
+            __sincosf(thv, &sn, &cs);
+        }
+        const int flip = cf >> 14;
+        if (flip & 1) {
+            if (MODEL != 1 || (S.order & 1)) cs = -cs; else sn = -sn;
+        }
+        if (flip & 2) sn = -sn;
+        A.P[q] = make_float4((float)(A.rX[k] - xc) * S.ux, (float)(A.rY[k] - yc) * S.uy,
+                             __int_as_float(__float2int_rn(cs * kFixNbF)), __int_as_float(__float2int_rn(sn * kFixNbF)));
+        A.sk[q] = (unsigned short)k;
+        if (S.nsp > 1) A.gidx[q] = (unsigned short)species_of(S, A.id[k]);   // species by sorted position
     }
     if (warp == NT / 32 - 1) {
         int carry = 0;
@@ -390,44 +417,6 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
     }
     __syncthreads();
     PHASE_MARK(2);
-
-    // --- order each cell by particle id; sorted records; own list ---------
-    const int xc = tw << (S.sx - 1), yc = th << (S.sy - 1);
-    for (int p = tid; p < m; p += NT) {
-        const int k = A.gidx[p];
-        const unsigned short cf = A.cell[k];
-        const int c = cf & 0x3fff;
-        const int a = tb.cstart[c], b = tb.cstart[c + 1];
-        const unsigned myid = A.id[k];
-        int rank = 0;
-        for (int p2 = a; p2 < b; ++p2) {
-            const int k2 = A.gidx[p2];
-            const unsigned id2 = A.id[k2];
-            rank += (id2 < myid) || (id2 == myid && k2 < k);
-        }
-        const int q = a + rank;
-        if (S.nsp > 1) A.slot[q] = (unsigned short)species_of(S, myid);   // slot is free again: species by sorted position
-        float thv = A.rth[k];
-        float sn, cs;
-        if (MODEL == 1 && S.order != 1) {
-            thv *= (float)S.order;
-            sincosf(thv, &sn, &cs);
-        } else {
-            // |theta| <= pi: the hardware sine/cosine is within 2^-21.4 absolute
-            __sincosf(thv, &sn, &cs);
-        }
-        const int flip = cf >> 14;
-        if (flip & 1) {
-            if (MODEL != 1 || (S.order & 1)) cs = -cs; else sn = -sn;
-        }
-        if (flip & 2) sn = -sn;
-        A.P[q] = make_float4((float)(A.rX[k] - xc) * S.ux, (float)(A.rY[k] - yc) * S.uy, cs, sn);
-        A.sk[q] = (unsigned short)k;
-        const int ey = c / W2, ex = c - ey * W2;
-        if (ey >= 1 && ey <= th && ex >= 1 && ex <= tw)
-            A.ownq[tb.rowpre[ey - 1] + q - tb.cstart[ey * W2 + 1]] = (unsigned short)q;
-    }
-    __syncthreads();
     PHASE_MARK(3);
 
     // --- interact, update, scatter ---------------------------------------
@@ -442,21 +431,43 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
         int4 rec = make_int4(0, 0, 0, 0);
         int dtile = 0, region = 0;
         if (act) {
-            const int q = A.ownq[o];
+            // own particle o -> sorted position: the own row holding it
+            int rlo = 0, rhi = th;
+            while (rhi - rlo > 1) {
+                const int mid = (rlo + rhi) >> 1;
+                if (tb.rowpre[mid] <= o) rlo = mid; else rhi = mid;
+            }
+            const int q = tb.cstart[(rlo + 1) * W2 + 1] + (o - tb.rowpre[rlo]);
             const int k = A.sk[q];
             const int X = A.rX[k], Y = A.rY[k];
             const float thi = A.rth[k];
             const unsigned id = A.id[k];
             const int ec = A.cell[k] & 0x3fff;
             const float4 pi = A.P[q];
-            float sc, ss;
+            float sc, ss;                    // neighbour sums in units of 2^-22
             int cnt;
             const int sp = S.nsp > 1 ? species_of(S, id) : 0;
-            if (MODEL == 1 && S.nsp > 1)
-                neighbour_sum_sp(A.P, A.slot, tb.cstart, ec, W2, pi, r2, S.sp_gamma_dt + sp * kMaxSpecies, sc, ss,
+            if (MODEL == 1 && S.nsp > 1) {
+                long long a, b;
+                neighbour_sum_sp(A.P, A.gidx, tb.cstart, ec, W2, pi, r2, S.sp_gamma_dt + sp * kMaxSpecies, a, b,
                                  cnt);
-            else
-                neighbour_sum<MODEL>(A.P, tb.cstart, ec, W2, pi, r2, sc, ss, cnt);
+                sc = (float)a;
+                ss = (float)b;
+            } else {
+                const int ncand = tb.cstart[ec - W2 + 2] - tb.cstart[ec - W2 - 1] + tb.cstart[ec + 2] -
+                                  tb.cstart[ec - 1] + tb.cstart[ec + W2 + 2] - tb.cstart[ec + W2 - 1];
+                if (ncand < 512) {
+                    int a, b;
+                    neighbour_sum<MODEL, int>(A.P, tb.cstart, ec, W2, pi, r2, a, b, cnt);
+                    sc = (float)a;
+                    ss = (float)b;
+                } else {
+                    long long a, b;
+                    neighbour_sum<MODEL, long long>(A.P, tb.cstart, ec, W2, pi, r2, a, b, cnt);
+                    sc = (float)a;
+                    ss = (float)b;
+                }
+            }
             const int nb = cnt - 1;          // the particle itself was counted
             if (measure) {
                 int bt = (int)floorf((thi + AAP_PI_F) * ((float)S.bins_theta * (1.0f / AAP_2PI_F)));
@@ -480,12 +491,15 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
                 const float u1 = u01f(c4[1]);
                 const float h = S.wlen > 0 ? S.wtab[min(nb, S.wlen - 1)]
                                            : (S.weight ? 1.0f : 1.0f / (1.0f + (float)nb));
-                const float tsum = pi.z * ss - pi.w * sc;   // Gamma dt inside with several species
+                // sum_j sin(o (theta_j - theta_i)) from the exact sums (units 2^-22 x 2^-22);
+                // Gamma dt inside with several species
+                const float tsum = ((float)__float_as_int(pi.z) * ss - (float)__float_as_int(pi.w) * sc) *
+                                   (1.0f / (kFixNbF * kFixNbF));
                 const float gz = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
                 const float drift = S.nsp > 1 ? h * tsum : S.gamma_dt * h * tsum;
                 thn = thi + drift + S.sp_omega_step[sp] + S.sp_noise_amp[sp] * gz;
-                float co = pi.z, so = pi.w;
-                if (S.order != 1) sincosf(thi, &so, &co);
+                float co, so;
+                __sincosf(thi, &so, &co);    // streaming direction theta(t), |theta| <= pi
                 dX = __float2int_rn(S.sp_kx[sp] * co);
                 dY = __float2int_rn(S.sp_ky[sp] * so);
                 cn = 0.f;

@@ -157,8 +157,9 @@ def test_ordered_state_stays_ordered(lib):
 
 
 def test_deterministic_and_resume_bitwise(lib):
-    """Same state -> bit-identical trajectory (region order is atomic, but sums
-    run in (cell, id) order); k steps + get/set_state + rest = all steps."""
+    """Same state -> bit-identical trajectory (region and cell order are set by
+    atomics, but the neighbour sums are exact integers); k steps + get/set_state
+    + rest = all steps."""
     p = params(n=20000, lx=100.0, ly=100.0, eta=0.45, seed=37)
     h1 = A.aap_create(p)
     h2 = A.aap_create(p)
