@@ -94,8 +94,22 @@ def denormalise(state, rho0):
     return f
 
 
-def forward(params, state, x0, round_act=None):
-    """One application: returns (new state, activations)."""
+def conserved_channels(conserve):
+    """Field channels whose sample mean one application keeps: bit 0 the
+    density (the particle number is fixed), bit 1 both polarisation channels."""
+    return [c for c, bit in ((0, 1), (1, 2), (2, 2)) if conserve & bit]
+
+
+def project(r, conserve):
+    """P r: the per-sample mean over the grid removed from the conserved channels."""
+    r = np.array(r, np.float64)
+    for c in conserved_channels(conserve):
+        r[..., c] -= r[..., c].mean(axis=(1, 2), keepdims=True)
+    return r
+
+
+def forward(params, state, x0, round_act=None, conserve=0):
+    """One application F + P Net(F, eta): returns (new state, activations)."""
     L = unpack(params)
     acts = [x0]
     a = x0
@@ -104,19 +118,21 @@ def forward(params, state, x0, round_act=None):
         if round_act is not None:
             a = round_act(a)
         acts.append(a)
-    out = conv_forward(a, *L[3])
+    out = project(conv_forward(a, *L[3]), conserve)
     return state + out, acts
 
 
-def loss_and_grad(params, state, x0, target, round_act=None):
-    """MSE over the 3 field channels and its gradient (library layout)."""
+def loss_and_grad(params, state, x0, target, round_act=None, conserve=0):
+    """MSE over the 3 field channels and its gradient (library layout); the
+    projection P is symmetric, so the gradient reaching the last layer is P g."""
     L = unpack(params)
-    pred, acts = forward(params, state, x0, round_act)
+    pred, acts = forward(params, state, x0, round_act, conserve)
     d = pred[..., :3] - target[..., :3]
     npx = d.shape[0] * d.shape[1] * d.shape[2]
     loss = float((d * d).sum() / (3 * npx))
     g = np.zeros_like(pred)
     g[..., :3] = 2.0 * d / (3 * npx)
+    g = project(g, conserve)
     grads = [None] * 4
     for k in (3, 2, 1, 0):
         dw, db = conv_backward_weight(acts[k], g)

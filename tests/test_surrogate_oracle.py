@@ -88,3 +88,32 @@ def test_bf16_rounding():
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0078125
     assert r[5] == 1.0   # tie to even
     assert np.array_equal(S.from_bf16_bits(S.bf16_bits(vals)), r)
+
+
+@pytest.mark.parametrize("conserve", [1, 2, 3])
+def test_conserving_network_keeps_means_and_gradient(conserve):
+    """With the projection P the conserved channels keep their per-sample grid
+    mean exactly over an application (the total particle number for the
+    density), and the gradient still matches central finite differences."""
+    g = np.random.default_rng(5)
+    n = sum(co * 9 * ci + co for ci, co in S.LAYERS)
+    layers = S.unpack(g.normal(size=n) * 0.2)
+    layers[0][0][:, :, 4:] = 0
+    layers[3][0][3:] = 0
+    layers[3][1][3:] = 0
+    params = S.pack(layers)
+    fields = np.abs(g.normal(size=(2, 3, 8, 16))) + 1.0
+    target = fields + 0.1 * g.normal(size=fields.shape)
+    st, x0 = S.normalise(fields, [0.3, 0.5], 2.0, 0.4, 0.1)
+    tg, _ = S.normalise(target, [0.3, 0.5], 2.0, 0.4, 0.1)
+    out, _ = S.forward(params, st, x0, conserve=conserve)
+    free, _ = S.forward(params, st, x0, conserve=0)
+    for c in range(3):
+        kept = c in S.conserved_channels(conserve)
+        same = np.allclose(out[..., c].mean(axis=(1, 2)), st[..., c].mean(axis=(1, 2)), rtol=0, atol=1e-12)
+        assert same == kept or (not kept and np.allclose(out[..., c], free[..., c]))
+    loss, grad = S.loss_and_grad(params, st, x0, tg, conserve=conserve)
+    f = lambda p: S.loss_and_grad(p, st, x0, tg, conserve=conserve)[0]
+    nz = np.nonzero(grad)[0]
+    for i in np.random.default_rng(6).choice(nz, 12, replace=False):
+        assert abs(_fd(f, params, i, 1e-6) - grad[i]) < 1e-7 + 1e-5 * abs(grad[i])
