@@ -270,7 +270,7 @@ def _bench_ensemble(A, W, torch, stream, steps):
 
 
 def _bench_surrogate(A, W, torch, stream, train_traj=32, iters=300, horizon=100, lr=2e-3,
-                     pushforward=0.0, nfr=40):
+                     pushforward=0.0, nfr=40, conserve=0):
     """Train the field surrogate on Vicsek N = 524,288, L = 512 trajectories
     (eta in [0.3, 0.5]) coarse-grained to 128 x 128 x 3 every 10 steps, then
     advance held-out states by `horizon` particle steps with the surrogate
@@ -294,7 +294,7 @@ def _bench_surrogate(A, W, torch, stream, train_traj=32, iters=300, horizon=100,
     A.aap_ens_destroy(e)
     t_data = time.perf_counter() - t0
     B = 32
-    s = A.aap_sur_create(A.aap_sur_params_default(nbx=nb, nby=nb, max_batch=B, lr=lr, seed=11),
+    s = A.aap_sur_create(A.aap_sur_params_default(nbx=nb, nby=nb, max_batch=B, lr=lr, seed=11, conserve=conserve),
                          stream.cuda_stream)
     xin = torch.zeros(B, 3, nb, nb, device="cuda")
     xtg = torch.zeros_like(xin)
@@ -326,10 +326,11 @@ def _bench_surrogate(A, W, torch, stream, train_traj=32, iters=300, horizon=100,
     fp = torch.zeros_like(f0)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     area = (512.0 / nb) ** 2
-    for j, eta in enumerate((0.35, 0.4, 0.45, 0.5)):
-        p = W.surrogate_training(eta=eta, seed=20000 + j)
+    held_out = np.linspace(0.3, 0.5, 16)          # 16 held-out seeds 20000..20015 over the eta range
+    for j, eta in enumerate(held_out):
+        p = W.surrogate_training(eta=float(eta), seed=20000 + j)
         h = A.aap_create(p, stream.cuda_stream)
-        A.aap_step(h, 100)
+        A.aap_step(h, 300)                        # inside the time range of the training frames
         A.aap_coarse_grain(h, nb, nb, f0.data_ptr())
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -338,7 +339,7 @@ def _bench_surrogate(A, W, torch, stream, train_traj=32, iters=300, horizon=100,
         ev1.record(stream)
         torch.cuda.synchronize()
         t_part += ev0.elapsed_time(ev1)
-        ed = torch.full((1,), eta, device="cuda")
+        ed = torch.full((1,), float(eta), device="cuda")
         ev0.record(stream)
         A.aap_sur_predict(s, f0.data_ptr(), ed.data_ptr(), 1, apps, fp.data_ptr())
         ev1.record(stream)
@@ -355,9 +356,10 @@ def _bench_surrogate(A, W, torch, stream, train_traj=32, iters=300, horizon=100,
     A.aap_sur_destroy(s)
     return {"workload": "Vicsek N=524288 L=512 eta[0.3,0.5] -> 128x128x3 fields, 4-layer 3x3 conv 32 ch",
             "train_trajectories": train_traj, "frames_per_trajectory": nfr, "iterations": iters,
-            "batch": B, "lr": lr, "pushforward": pushforward, "final_loss": loss, "data_s": t_data, "train_s": t_train,
+            "batch": B, "lr": lr, "pushforward": pushforward, "conserve": conserve, "final_loss": loss, "data_s": t_data, "train_s": t_train,
             "horizon_steps": horizon, "speedup_vs_particles": t_part / t_sur,
-            "particle_ms": t_part / 4, "surrogate_ms": t_sur / 4,
+            "particle_ms": t_part / len(held_out), "surrogate_ms": t_sur / len(held_out),
+            "held_out_states": len(held_out),
             "phi_abs_error": float(np.mean(errs)), "phi_abs_error_keep_fields": float(np.mean(keep_errs)),
             "sk_rel_l2_error": float(np.mean(sk_errs)), "sk_rel_l2_error_keep_fields": float(np.mean(sk_keep))}
 
@@ -509,7 +511,9 @@ def main():
         extras["metric_free"] = _bench_metric_free(A, W, torch, stream, 100)
         extras["ensemble"] = _bench_ensemble(A, W, torch, stream, 200)
         with torch.cuda.stream(stream):     # torch copies and library calls share one stream
-            extras["surrogate"] = _bench_surrogate(A, W, torch, stream)
+            # conserving (grid means of density and polarisation kept) and free
+            extras["surrogate"] = _bench_surrogate(A, W, torch, stream, conserve=3)
+            extras["surrogate_unconstrained"] = _bench_surrogate(A, W, torch, stream, conserve=0)
 
     if rank != 0:
         if dist:

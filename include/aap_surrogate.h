@@ -34,7 +34,11 @@ extern "C" {
 typedef struct aap_sur_params {
     int32_t  nbx, nby;      /* field grid: nbx a multiple of 16, nby of 8, <= 4096 */
     int32_t  max_batch;     /* largest batch of a train or predict call (1..4096)  */
-    int32_t  reserved;
+    int32_t  conserve;      /* bit 0: one application keeps each sample's mean
+                               density (the particle number), bit 1: its mean
+                               polarisation; the network's residual is projected
+                               to zero grid mean in those channels (training
+                               included).  0 = free (default)                   */
     double   rho0;          /* mean density: fields are scaled by 1/rho0           */
     double   eta_center;    /* the eta channel is (eta - eta_center) / eta_scale   */
     double   eta_scale;

@@ -79,7 +79,7 @@ class aap_results(C.Structure):
 
 class aap_sur_params(C.Structure):
     _fields_ = [("nbx", C.c_int32), ("nby", C.c_int32), ("max_batch", C.c_int32),
-                ("reserved", C.c_int32), ("rho0", C.c_double), ("eta_center", C.c_double),
+                ("conserve", C.c_int32), ("rho0", C.c_double), ("eta_center", C.c_double),
                 ("eta_scale", C.c_double), ("lr", C.c_double), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64)]
 

@@ -295,17 +295,21 @@ __global__ void k_fields_out(const float *__restrict__ state, int B, int H, int 
 
 // Mean squared error over the 3 field channels of pred vs target (both
 // normalised FP32 NHWC 8), per-block partial sums; dout = d loss / d pred in
-// BF16 NHWC 16 (channels >= 3 zero).
+// BF16 NHWC 16 (channels >= 3 zero), minus the per-sample means dmean of the
+// conserved channels when a projection is on (plane = pixels per sample).
 __global__ void k_mse(const float *__restrict__ pred, const float *__restrict__ target, long long npix,
-                      float scale, float *__restrict__ part, bf16 *__restrict__ dout)
+                      float scale, float *__restrict__ part, bf16 *__restrict__ dout, const float *__restrict__ dmean,
+                      int plane)
 {
     __shared__ float red[256];
     float s = 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
         float d[3];
+        const long long b = i / plane;
         for (int c = 0; c < 3; ++c) {
             d[c] = pred[i * 8 + c] - target[i * 8 + c];
             s += d[c] * d[c];
+            if (dmean) d[c] -= dmean[b * 3 + c];     // through the projection P
         }
         __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(dout + i * 16);
         o[0] = __floats2bfloat162_rn(2.f * scale * d[0], 2.f * scale * d[1]);
@@ -319,6 +323,86 @@ __global__ void k_mse(const float *__restrict__ pred, const float *__restrict__ 
         __syncthreads();
     }
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// Channels whose per-sample grid mean one application keeps (conserve bits:
+// 1 the density, 2 both polarisation channels).
+__host__ __device__ inline bool conserved(int conserve, int c) { return c == 0 ? (conserve & 1) : (conserve & 2); }
+
+// Conservation projection in two passes over chunks of kCenterChunk pixels
+// of a sample (NHWC 8 FP32, channels 0..2 read as one float4 per pixel):
+// k_center_part writes each chunk's sums of a - b per channel (fixed order,
+// so the result is deterministic); the means follow from a sample's chunk
+// sums in chunk order.
+constexpr int kCenterChunk = 2048;
+
+__global__ void __launch_bounds__(256) k_center_part(const float *__restrict__ a, const float *__restrict__ b,
+                                                     int npix, int nchunk, float *__restrict__ part)
+{
+    __shared__ float red[3][256];
+    const int smp = blockIdx.x / nchunk, ch = blockIdx.x % nchunk;
+    const long long base = (long long)smp * npix;
+    const int p0 = ch * kCenterChunk, p1 = min(npix, p0 + kCenterChunk);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int p = p0 + threadIdx.x; p < p1; p += 256) {
+        const float4 u = *reinterpret_cast<const float4 *>(a + (base + p) * 8);
+        const float4 v = *reinterpret_cast<const float4 *>(b + (base + p) * 8);
+        s0 += u.x - v.x;
+        s1 += u.y - v.y;
+        s2 += u.z - v.z;
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    red[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[(long long)blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Grid mean of channel c of sample smp from its chunk sums.
+__device__ __forceinline__ float chunk_mean(const float *__restrict__ part, int smp, int nchunk, int c, int npix)
+{
+    float t = 0.f;
+    for (int k = 0; k < nchunk; ++k) t += part[((long long)smp * nchunk + k) * 4 + c];
+    return t / (float)npix;
+}
+
+// Remove the mean of out - in from the conserved channels of out (one block
+// per chunk of a sample).
+__global__ void __launch_bounds__(256) k_center_apply(float *__restrict__ out, const float *__restrict__ part,
+                                                      int npix, int nchunk, int conserve)
+{
+    __shared__ float mean[3];
+    const int smp = blockIdx.x / nchunk, ch = blockIdx.x % nchunk;
+    if (threadIdx.x < 3)
+        mean[threadIdx.x] = conserved(conserve, threadIdx.x) ? chunk_mean(part, smp, nchunk, threadIdx.x, npix) : 0.f;
+    __syncthreads();
+    const long long base = (long long)smp * npix;
+    const int p0 = ch * kCenterChunk, p1 = min(npix, p0 + kCenterChunk);
+    for (int p = p0 + threadIdx.x; p < p1; p += 256) {
+        float4 *o = reinterpret_cast<float4 *>(out + (base + p) * 8);
+        float4 u = *o;
+        u.x -= mean[0];
+        u.y -= mean[1];
+        u.z -= mean[2];
+        *o = u;
+    }
+}
+
+// dmean[smp * 3 + c] = grid mean of pred - target for the conserved channels
+// (0 otherwise), from the chunk sums: the loss gradient minus it is the
+// gradient through the projection.
+__global__ void k_dmean(const float *__restrict__ part, int B, int npix, int nchunk, int conserve,
+                        float *__restrict__ dmean)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * 3) return;
+    const int smp = i / 3, c = i % 3;
+    dmean[i] = conserved(conserve, c) ? chunk_mean(part, smp, nchunk, c, npix) : 0.f;
 }
 
 // Adam (Kingma & Ba) on the FP32 master parameters.
@@ -432,6 +516,8 @@ struct aap_sur {
     bf16 *x0 = nullptr, *a[3] = {}, *d[3] = {}, *dout = nullptr;       // activations and gradients
     float *state = nullptr, *state2 = nullptr, *target = nullptr, *eta = nullptr;
     float *part = nullptr, *loss_part = nullptr;
+    float *dmean = nullptr;                                            // [max_batch * 3] projected gradient means
+    float *cpart = nullptr;                                            // chunk sums of the projection
     size_t part_floats = 0;
     int loss_blocks = 0;
     long long t = 0;                                                   // Adam step
@@ -485,6 +571,12 @@ int forward(aap_sur *s, int batch)
     SCK((conv<32, 32, MODE_RELU>(s->a[0], batch, H, W, s->wf[1], s->w + s->boff[1], s->a[1], nullptr, nullptr, nullptr, st)));
     SCK((conv<32, 32, MODE_RELU>(s->a[1], batch, H, W, s->wf[2], s->w + s->boff[2], s->a[2], nullptr, nullptr, nullptr, st)));
     SCK((conv<32, 8, MODE_RESID>(s->a[2], batch, H, W, s->wf[3], s->w + s->boff[3], nullptr, nullptr, s->state, s->state2, st)));
+    if (s->p.conserve) {
+        const int nchunk = (H * W + kCenterChunk - 1) / kCenterChunk;
+        k_center_part<<<batch * nchunk, 256, 0, st>>>(s->state2, s->state, H * W, nchunk, s->cpart);
+        k_center_apply<<<batch * nchunk, 256, 0, st>>>(s->state2, s->cpart, H * W, nchunk, s->p.conserve);
+        SCK(cudaGetLastError());
+    }
     return AAP_OK;
 }
 
@@ -528,6 +620,7 @@ int aap_sur_create(const aap_sur_params *p, void *stream, aap_sur **out)
     if (p->max_batch < 1 || p->max_batch > 4096) return sfail(AAP_EINVAL, "max_batch must be in [1, 4096]");
     if (!(p->rho0 > 0) || !(p->eta_scale > 0) || !(p->lr > 0) || !(p->eps > 0))
         return sfail(AAP_EINVAL, "rho0, eta_scale, lr and eps must be positive");
+    if (p->conserve < 0 || p->conserve > 3) return sfail(AAP_EINVAL, "conserve must be in [0, 3]");
     aap_sur *s = new aap_sur();
     s->p = *p;
     s->stream = static_cast<cudaStream_t>(stream);
@@ -571,6 +664,8 @@ int aap_sur_create(const aap_sur_params *p, void *stream, aap_sur **out)
     A(&s->part, s->part_floats * 4);
     s->loss_blocks = 256;
     A(&s->loss_part, (size_t)s->loss_blocks * 4);
+    A(&s->dmean, (size_t)s->maxb * 3 * 4);
+    A(&s->cpart, (size_t)s->maxb * ((s->H * s->W + kCenterChunk - 1) / kCenterChunk) * 4 * 4);
     if (rc) {
         sfree(s);
         delete s;
@@ -691,8 +786,14 @@ int aap_sur_train_step(aap_sur *s, const float *dev_in, const float *dev_target,
     int rc = forward(s, batch);
     if (rc) return rc;
     const long long npix = (long long)batch * H * W;
+    if (s->p.conserve) {
+        const int nchunk = (H * W + kCenterChunk - 1) / kCenterChunk;
+        k_center_part<<<batch * nchunk, 256, 0, st>>>(s->state2, s->target, H * W, nchunk, s->cpart);
+        k_dmean<<<(batch * 3 + 127) / 128, 128, 0, st>>>(s->cpart, batch, H * W, nchunk, s->p.conserve, s->dmean);
+        SCK(cudaGetLastError());
+    }
     k_mse<<<s->loss_blocks, 256, 0, st>>>(s->state2, s->target, npix, (float)(1.0 / (3.0 * (double)npix)),
-                                          s->loss_part, s->dout);
+                                          s->loss_part, s->dout, s->p.conserve ? s->dmean : nullptr, H * W);
     SCK(cudaGetLastError());
     float *g = s->g;
     // layer 4: weight gradient from a[2] and dout (16-channel pixels, 8 used);

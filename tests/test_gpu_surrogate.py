@@ -116,11 +116,13 @@ def _random_params(n, seed):
     return S.pack(layers).astype(np.float32)
 
 
-def test_network_loss_and_gradient(lib):
+@pytest.mark.parametrize("conserve", [0, 3])
+def test_network_loss_and_gradient(lib, conserve):
     """One train step's loss and parameter gradient against the oracle network
-    (BF16-rounded weights, input and activations, FP64 arithmetic)."""
+    (BF16-rounded weights, input and activations, FP64 arithmetic), without and
+    with the projection that keeps the grid means."""
     B, H, W = 2, 16, 32
-    sp = A.aap_sur_params_default(nbx=W, nby=H, max_batch=B)
+    sp = A.aap_sur_params_default(nbx=W, nby=H, max_batch=B, conserve=conserve)
     s = A.aap_sur_create(sp)
     try:
         n = A.aap_sur_param_count(s)
@@ -137,7 +139,7 @@ def test_network_loss_and_gradient(lib):
         st, x0 = S.normalise(fields.astype(np.float32), eta.astype(np.float32), 2.0, 0.4, 0.1)
         tg, _ = S.normalise(target.astype(np.float32), eta.astype(np.float32), 2.0, 0.4, 0.1)
         pw = S.pack([(S.bf16_round(w), b) for w, b in S.unpack(params.astype(np.float64))])
-        rloss, rgrad = S.loss_and_grad(pw, st, S.bf16_round(x0), tg, round_act=S.bf16_round)
+        rloss, rgrad = S.loss_and_grad(pw, st, S.bf16_round(x0), tg, round_act=S.bf16_round, conserve=conserve)
         assert abs(loss - rloss) <= 1e-2 * rloss
         rel = np.linalg.norm(grad - rgrad) / np.linalg.norm(rgrad)
         cos = grad @ rgrad / (np.linalg.norm(grad) * np.linalg.norm(rgrad))
@@ -228,3 +230,27 @@ def test_trained_surrogate_beats_persistence(lib):
         assert mse_net < 0.85 * mse_keep, (mse_net, mse_keep)
     finally:
         A.aap_sur_destroy(s)
+
+
+def test_conserving_predict_keeps_grid_means(lib):
+    """With conserve = 3, ten applications keep every sample's total density
+    (particle number) and total polarisation; without, they drift."""
+    B, H, W = 2, 16, 32
+    g = np.random.default_rng(12)
+    f = (np.abs(g.normal(size=(B, 3, H, W))) + 1.0).astype(np.float32)
+    f[:, 1:] -= 1.2
+    fin, eta = _dev_f32(f), _dev_f32([0.35, 0.45])
+    sums = {}
+    for conserve in (0, 3):
+        s = A.aap_sur_create(A.aap_sur_params_default(nbx=W, nby=H, max_batch=B, seed=8, conserve=conserve))
+        try:
+            A.aap_sur_set_params(s, _random_params(A.aap_sur_param_count(s), 13))
+            out = torch.zeros_like(fin)
+            A.aap_sur_predict(s, fin.data_ptr(), eta.data_ptr(), B, 10, out.data_ptr())
+            torch.cuda.synchronize()
+            sums[conserve] = out.cpu().numpy().astype(np.float64).sum(axis=(2, 3))
+        finally:
+            A.aap_sur_destroy(s)
+    ref = f.astype(np.float64).sum(axis=(2, 3))
+    assert np.allclose(sums[3], ref, rtol=1e-4, atol=1e-3 * H * W)
+    assert not np.allclose(sums[0], ref, rtol=1e-4, atol=1e-3 * H * W)
