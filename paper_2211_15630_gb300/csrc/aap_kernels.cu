@@ -646,7 +646,11 @@ k_step(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_base,
         if (T.m <= stage_cap) {
             tile_body<NT, MODEL>(T, As, tb, step, spill_e, spill_s);
         } else if (T.m <= scratch_cap) {
-            tile_body<NT, MODEL>(T, Ag, tb, step, spill_e, spill_s);
+            // a dense tile: staged in global scratch, except the records the
+            // candidate loops read, which still fit the shared staging area
+            Stage Ah = Ag;
+            if ((size_t)T.m * sizeof(float4) <= stage_bytes(stage_cap)) Ah.P = reinterpret_cast<float4 *>(smem);
+            tile_body<NT, MODEL>(T, Ah, tb, step, spill_e, spill_s);
         } else if (threadIdx.x == 0) {
             atomicOr(T.S.err, ERR_STAGE | ERR_LOST);
         }
