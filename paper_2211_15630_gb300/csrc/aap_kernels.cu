@@ -97,17 +97,38 @@ __device__ __forceinline__ void warp_insert(const Sys &S, int b, bool act, int d
 
 
 // ---------------------------------------------------------- tile context --
+// Geometry of one tile and its neighbours' sizes.
+struct TileGeo {
+    int tx, ty, tw, th;
+    int twL, twR, thD, thU;     // widths / heights of the neighbour tiles
+};
+
 struct TileCtx {
     Sys S;
     int sysi, tile, tx, ty, tw, th, W2, H2, nce;
     int twL, twR, thD, thU;     // widths / heights of the neighbour tiles
     int m_seg, n_spill, m, n_own;
-    int next;                   // prefetched next tile index
+    int next;                   // index of the next tile this block takes
+    int total, nsys;            // tiles and systems of the launch
+    const int *tile_base;
+    int pf_tile, pf_sys, pf_nsp;    // segments of the next tile, read ahead during this one
+    TileGeo pf_geo;
     int segpre[kSegs + 1];
     int warp_tot[32];
     Seg seg[kSegs];
+    Seg pf_seg[kSegs];
     long long red[5][32];
 };
+
+__device__ __forceinline__ int sys_of_tile(const int *tile_base, int nsys, int g)
+{
+    int lo = 0, hi = nsys;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tile_base[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
 
 // Resolve the halo column (side -1: left, +1: right) of tile t into a source
 // tile column, the region column class there, and the position / cell maps.
@@ -135,9 +156,61 @@ __device__ __forceinline__ void resolve_axis(int side, int t, int nt, int w, int
     }
 }
 
+__device__ __forceinline__ TileGeo tile_geo(const Sys &S, int tile)
+{
+    TileGeo G;
+    G.tx = tile % S.ntx;
+    G.ty = tile / S.ntx;
+    const int x0 = S.x0tab[G.tx], y0 = S.y0tab[G.ty];
+    G.tw = S.x0tab[G.tx + 1] - x0;
+    G.th = S.y0tab[G.ty + 1] - y0;
+    const int txl = G.tx > 0 ? G.tx - 1 : S.ntx - 1, txr = G.tx < S.ntx - 1 ? G.tx + 1 : 0;
+    const int tyd = G.ty > 0 ? G.ty - 1 : S.nty - 1, tyu = G.ty < S.nty - 1 ? G.ty + 1 : 0;
+    G.twL = S.x0tab[txl + 1] - S.x0tab[txl];
+    G.twR = S.x0tab[txr + 1] - S.x0tab[txr];
+    G.thD = S.y0tab[tyd + 1] - S.y0tab[tyd];
+    G.thU = S.y0tab[tyu + 1] - S.y0tab[tyu];
+    return G;
+}
+
+// Source segment s of a tile: s < 9 its own region s, then the 16 halo
+// regions of the neighbour tiles (left, right, down, up edges, the corners)
+// with their periodic shift or mirror map into the extended frame.
+__device__ __forceinline__ Seg make_seg(const Sys &S, const TileGeo &G, int s, int cur)
+{
+    int bxo, byo, rx = -1, ry = -1;
+    if (s < 9) {
+        bxo = 0; byo = 0; rx = s % 3; ry = s / 3;
+    } else {
+        const int h = s - 9;
+        if (h < 3)       { bxo = -1; byo = 0;  ry = h; }
+        else if (h < 6)  { bxo = 1;  byo = 0;  ry = h - 3; }
+        else if (h < 9)  { bxo = 0;  byo = -1; rx = h - 6; }
+        else if (h < 12) { bxo = 0;  byo = 1;  rx = h - 9; }
+        else { bxo = (h & 1) ? 1 : -1; byo = (h >= 14) ? 1 : -1; }
+    }
+    int srcx, clsx, ax, cx, fx, srcy, clsy, ay, cy, fy;
+    long long bxx, byy;
+    resolve_axis(bxo, G.tx, S.ntx, G.tw, G.twL, S.bx, S.sx, srcx, clsx, ax, cx, bxx, fx);
+    resolve_axis(byo, G.ty, S.nty, G.th, G.thD, S.by, S.sy, srcy, clsy, ay, cy, byy, fy);
+    if (clsx < 0) clsx = rx;
+    if (clsy < 0) clsy = ry;
+    Seg g;
+    g.tile = srcy * S.ntx + srcx;
+    g.region = clsy * 3 + clsx;
+    g.base = S.rec[cur] + (long long)g.tile * S.tile_slots + S.off[g.region];
+    const int c = S.cnt[cur][g.tile * kCntStride + g.region];
+    g.count = min(c, S.cap[g.region]);
+    g.ax = ax; g.ay = ay; g.cx = cx; g.cy = cy; g.bx = bxx; g.by = byy;
+    g.flip = fx | (fy << 1);
+    return g;
+}
+
 // Phase 1 of a tile: geometry, the 25 source segments (9 own regions, 16
 // halo regions with their periodic or mirror maps), spill matches, and the
-// number m of particles to stage.  Ends with the block synchronised.
+// number m of particles to stage.  The geometry and segments come from the
+// read-ahead of the previous tile when it took this one.  Ends with the
+// block synchronised.
 template <int NT>
 __device__ __forceinline__ void tile_setup(TileCtx &T, const Tables &tb, int cur, int nce_max,
                                            int *spill_e, unsigned char *spill_s, int spill_list_cap)
@@ -145,52 +218,21 @@ __device__ __forceinline__ void tile_setup(TileCtx &T, const Tables &tb, int cur
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const Sys &S = T.S;
-    const int tx = T.tile % S.ntx, ty = T.tile / S.ntx;
-    const int x0 = S.x0tab[tx], y0 = S.y0tab[ty];
-    const int tw = S.x0tab[tx + 1] - x0, th = S.y0tab[ty + 1] - y0;
-    const int txl = tx > 0 ? tx - 1 : S.ntx - 1, txr = tx < S.ntx - 1 ? tx + 1 : 0;
-    const int tyd = ty > 0 ? ty - 1 : S.nty - 1, tyu = ty < S.nty - 1 ? ty + 1 : 0;
-    const int twL = S.x0tab[txl + 1] - S.x0tab[txl], twR = S.x0tab[txr + 1] - S.x0tab[txr];
-    const int thD = S.y0tab[tyd + 1] - S.y0tab[tyd], thU = S.y0tab[tyu + 1] - S.y0tab[tyu];
+    const bool pf = T.pf_tile == T.tile && T.pf_sys == T.sysi;
+    const TileGeo G = pf ? T.pf_geo : tile_geo(S, T.tile);
     if (tid == 0) {
-        T.tx = tx; T.ty = ty; T.tw = tw; T.th = th;
-        T.W2 = tw + 2; T.H2 = th + 2; T.nce = (tw + 2) * (th + 2);
-        T.twL = twL; T.twR = twR; T.thD = thD; T.thU = thU;
+        T.tx = G.tx; T.ty = G.ty; T.tw = G.tw; T.th = G.th;
+        T.W2 = G.tw + 2; T.H2 = G.th + 2; T.nce = (G.tw + 2) * (G.th + 2);
+        T.twL = G.twL; T.twR = G.twR; T.thD = G.thD; T.thU = G.thU;
         T.n_spill = 0;
     }
     for (int i = tid; i < nce_max; i += NT) tb.hist[i] = 0;
     if (T.S.meas_until > 0)
         for (int i = tid; i < S.bins_theta + S.bins_nbr; i += NT) tb.mhist[i] = 0;
-    if (tid < kSegs) {
-        int bxo, byo, rx = -1, ry = -1;
-        if (tid < 9) {
-            bxo = 0; byo = 0; rx = tid % 3; ry = tid / 3;
-        } else {
-            const int h = tid - 9;
-            if (h < 3)       { bxo = -1; byo = 0;  ry = h; }
-            else if (h < 6)  { bxo = 1;  byo = 0;  ry = h - 3; }
-            else if (h < 9)  { bxo = 0;  byo = -1; rx = h - 6; }
-            else if (h < 12) { bxo = 0;  byo = 1;  rx = h - 9; }
-            else { bxo = (h & 1) ? 1 : -1; byo = (h >= 14) ? 1 : -1; }
-        }
-        int srcx, clsx, ax, cx, fx, srcy, clsy, ay, cy, fy;
-        long long bxx, byy;
-        resolve_axis(bxo, tx, S.ntx, tw, twL, S.bx, S.sx, srcx, clsx, ax, cx, bxx, fx);
-        resolve_axis(byo, ty, S.nty, th, thD, S.by, S.sy, srcy, clsy, ay, cy, byy, fy);
-        if (clsx < 0) clsx = rx;
-        if (clsy < 0) clsy = ry;
-        Seg g;
-        g.tile = srcy * S.ntx + srcx;
-        g.region = clsy * 3 + clsx;
-        g.base = S.rec[cur] + (long long)g.tile * S.tile_slots + S.off[g.region];
-        const int c = S.cnt[cur][g.tile * kCntStride + g.region];
-        g.count = min(c, S.cap[g.region]);
-        g.ax = ax; g.ay = ay; g.cx = cx; g.cy = cy; g.bx = bxx; g.by = byy;
-        g.flip = fx | (fy << 1);
-        T.seg[tid] = g;
-    }
-    const int nsp = min(*((volatile int *)&S.spill_cnt[cur]), S.spill_cap);
+    if (tid < kSegs) T.seg[tid] = pf ? T.pf_seg[tid] : make_seg(S, G, tid, cur);
+    const int nsp = pf ? T.pf_nsp : min(*((volatile int *)&S.spill_cnt[cur]), S.spill_cap);
     __syncthreads();
+    if (tid == 0) T.pf_tile = -1;       // consumed (the read-ahead for the next tile comes later)
     if (warp == 0) {
         const int v = lane < kSegs ? T.seg[lane].count : 0;
         const int incl = warp_incl_scan(v);
@@ -543,6 +585,23 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
         }
         warp_insert(S, nxt, act, dtile, region, rec);
     }
+    // --- read ahead: the last warp (often idle in the last round of the
+    //     update) prepares the next tile's geometry and segments, so that the
+    //     next tile_setup starts without its chain of global loads ----------
+    if (warp == NT / 32 - 1 && T.next < T.total) {
+        const int g = T.next;
+        const int si = T.nsys > 1 ? sys_of_tile(T.tile_base, T.nsys, g) : 0;
+        if (si == T.sysi) {
+            const TileGeo G = tile_geo(S, g - (T.nsys > 1 ? T.tile_base[si] : 0));
+            if (lane < kSegs) T.pf_seg[lane] = make_seg(S, G, lane, cur);
+            if (lane == 0) {
+                T.pf_geo = G;
+                T.pf_nsp = min(*((volatile int *)&S.spill_cnt[cur]), S.spill_cap);
+                T.pf_tile = g - (T.nsys > 1 ? T.tile_base[si] : 0);
+                T.pf_sys = si;
+            }
+        }
+    }
     PHASE_MARK(4);
     // --- per-tile integer sums -> the step's accumulators ----------------
     acc_c = warp_sum_ll(acc_c);
@@ -571,15 +630,6 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
     PHASE_MARK(5);
 }
 
-__device__ __forceinline__ int sys_of_tile(const int *tile_base, int nsys, int g)
-{
-    int lo = 0, hi = nsys;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (tile_base[mid] <= g) lo = mid; else hi = mid;
-    }
-    return lo;
-}
 
 // Persistent blocks pull tiles in raster order (so halos are L2-hot) from a
 // device counter; the next tile index is fetched while the current one runs.
@@ -608,6 +658,10 @@ k_step(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_base,
     unsigned char *spill_s = (unsigned char *)(spill_e + spill_list_cap);
     if (threadIdx.x == 0) {
         T.sysi = -1;
+        T.pf_tile = -1;
+        T.total = total;
+        T.nsys = nsys;
+        T.tile_base = tile_base;
         T.next = atomicAdd(&ctl->tile_next, 1);
     }
     __syncthreads();
