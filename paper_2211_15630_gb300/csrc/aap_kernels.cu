@@ -738,15 +738,22 @@ __global__ void k_finish(Sys *sys, int nsys, Ctl *ctl)
     }
     __syncthreads();
     if (!s_last) return;
-    for (int si = threadIdx.x; si < nsys; si += blockDim.x) {
+    // one warp per system: the 64 accumulator slots summed by the lanes
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int si = threadIdx.x >> 5; si < nsys; si += nwarp) {
         Sys &S = sys[si];
         unsigned long long *a = S.acc + (size_t)cur * kAccSlots * kAccWords;
-        long long v[5] = {0, 0, 0, 0, 0};
-        for (int k = 0; k < kAccSlots; ++k)
-            for (int w = 0; w < 5; ++w) {
-                v[w] += (long long)a[k * kAccWords + w];
+        long long v[5];
+#pragma unroll
+        for (int w = 0; w < 5; ++w) {
+            long long x = 0;
+            for (int k = lane; k < kAccSlots; k += 32) {
+                x += (long long)a[k * kAccWords + w];
                 a[k * kAccWords + w] = 0;
             }
+            v[w] = warp_sum_ll(x);           // exact integer sum, lane 0 holds it
+        }
+        if (lane != 0) continue;
         const double n = (double)S.n;
         const double dc = (double)v[0] / kFixStep, ds = (double)v[1] / kFixStep;
         const double dc2 = (double)v[3] / kFixStep, ds2 = (double)v[4] / kFixStep;
