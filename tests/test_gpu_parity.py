@@ -291,3 +291,40 @@ def test_long_run_time_averaged_phi_16_seeds(lib, oracle):
     sigma = np.sqrt(o.var(ddof=1) / len(o) + g.var(ddof=1) / len(g))
     assert abs(o.mean() - g.mean()) < 3 * sigma, (o.mean(), g.mean(), sigma)
     assert 0.05 < g.mean() < 1.0
+
+
+def test_largest_practical_system_keeps_every_particle(lib, oracle):
+    """N = 2^27 (L = 8192, rho = 2; about 20 GB on the device): every record is
+    kept (aap_observe counts them), p stays a valid order parameter, and sampled
+    particles of a later step still match the oracle on a local copy of their
+    neighbourhood."""
+    p = params(n=1 << 27, lx=8192.0, ly=8192.0, eta=0.45, seed=71)
+    h = A.aap_create(p)
+    try:
+        A.aap_step(h, 3)
+        obs = A.aap_observe(h)                   # raises if a record was lost
+        assert obs.step == 3 and 0.0 <= obs.phi < 0.01
+        x, y, th = A.aap_get_state(h, p.n)
+        step = obs.step
+        nb = A.aap_step_neighbours(h, p.n)
+        x1, y1, t1 = A.aap_get_state(h, p.n)
+    finally:
+        A.aap_destroy(h)
+    # neighbour counts of sampled particles: the oracle on the particles of a
+    # 48 x 48 window centred on each (its own periodic box; the centre is far
+    # from the window's edges, so only true neighbours can reach it)
+    rng = np.random.default_rng(3)
+    checked = 0
+    for i in rng.choice(p.n, 12, replace=False):
+        if not (30 < x[i] < p.lx - 30 and 30 < y[i] < p.ly - 30):
+            continue
+        sel = np.nonzero((np.abs(x - x[i]) < 24) & (np.abs(y - y[i]) < 24))[0]
+        k = int(np.nonzero(sel == i)[0][0])
+        m = oracle_model(oracle, params(n=sel.size, lx=48.0, ly=48.0, eta=p.eta, seed=p.seed))
+        xs, ys = x[sel] - (x[i] - 24.0), y[sel] - (y[i] - 24.0)
+        _, _, _, nbo, _, amb = oracle.step(m, xs, ys, th[sel].astype(np.float64), step, idx=np.array([k]))
+        if amb[0]:
+            continue
+        assert nb[i] == nbo[0]
+        checked += 1
+    assert checked >= 8
