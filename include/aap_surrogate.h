@@ -32,7 +32,7 @@ extern "C" {
 #endif
 
 typedef struct aap_sur_params {
-    int32_t  nbx, nby;      /* field grid: nbx a multiple of 16, nby of 8, <= 4096 */
+    int32_t  nbx, nby;      /* field grid: multiples of 16, <= 4096                 */
     int32_t  max_batch;     /* largest batch of a train or predict call (1..4096)  */
     int32_t  conserve;      /* bit 0: one application keeps each sample's mean
                                density (the particle number), bit 1: its mean
@@ -88,7 +88,8 @@ int aap_sur_train_step(aap_sur *s, const float *dev_in, const float *dev_target,
 
 /* ---- the convolution kernels alone (tests, tools) -------------------------
  * BF16 tensors are passed as raw 16-bit words, NHWC (channels fastest).
- * Circular padding; batch >= 1; h a multiple of 8, w of 16. */
+ * Circular padding; batch >= 1; h and w multiples of 16 (a tensor-core tile
+ * is 16 rows x 8 columns). */
 
 /* y[b,y,x,co] = bias[co] + sum_{tap,ci} wt[tap][co][ci] x[b,(y+dy-1)%h,(x+dx-1)%w,ci]
  * (tap = 3 dy + dx), ReLU if relu != 0.  (cin, cout) in

@@ -10,8 +10,9 @@
 // start at zero and receive zero gradient, so they stay zero).
 //
 // Kernels:
-//   k_conv<CIN, COUT, MODE>   implicit-GEMM convolution on mma.sync
-//                             m16n8k16 (BF16 x BF16 -> FP32): forward with
+//   k_conv<CIN, COUT, MODE>   implicit-GEMM convolution on the tcgen05
+//                             tensor cores (BF16 x BF16 -> FP32 accumulator in
+//                             TMEM, M = 128 pixels, N = COUT): forward with
 //                             bias + ReLU, forward with the residual update,
 //                             or the data gradient (flipped, transposed
 //                             weights) masked by the ReLU of the layer input
@@ -37,34 +38,71 @@ namespace aaps {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int kTH = 8, kTW = 16;   // output tile of one block: 8 rows x 16 columns
+// tcgen05 convolution tile: 16 rows x 8 columns = 128 output pixels, the M of
+// one tensor-core MMA (cta_group::1, M = 128), one pixel per TMEM lane.
+constexpr int kTH = 16, kTW = 8;
+constexpr int kHaloPix = (kTH + 2) * (kTW + 2);     // 180 input pixels with the 1-pixel ring
+constexpr int kPlane = kHaloPix * 16;               // bytes of one 8-channel plane of the halo tile
+constexpr int kWaitLimit = 1 << 22;                 // bounded mbarrier wait (then the error flag)
+
+__device__ int g_sur_err;                           // sticky: 1 = a tensor-core wait gave up
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p)
+// tcgen05 shared-memory matrix descriptor, no swizzle, K-major core matrices of
+// 8 rows x 16 bytes: start address, LBO = byte step between core matrices
+// along K, SBO = byte step between core matrices along M (or N); bit 46 is
+// the descriptor version of this tensor-core generation.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_addr(p)));
+    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= 1ull << 46;
+    return d;
 }
 
-__device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, const void *p)
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, BF16 A
+// and B, both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-                 : "=r"(r0), "=r"(r1)
-                 : "r"(smem_addr(p)));
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1)
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate)
 {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
-                 "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                 ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// 16 or 32 FP32 columns of this warp's 32 TMEM lanes (one row each).
+template <int NC>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, uint32_t (&r)[NC])
+{
+    if constexpr (NC == 16) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                       "=r"(r[14]), "=r"(r[15])
+                     : "r"(taddr));
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                       "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                       "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                       "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                     : "r"(taddr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
 enum { MODE_RELU = 0, MODE_RESID = 1, MODE_MASK = 2, MODE_LINEAR = 3 };
@@ -75,74 +113,98 @@ enum { MODE_RELU = 0, MODE_RESID = 1, MODE_MASK = 2, MODE_LINEAR = 3 };
 //   MODE_LINEAR + bias, BF16 NHWC out
 //   MODE_RESID  + bias, FP32: resid_out = resid_in + value (NHWC, 8 channels)
 //   MODE_MASK   value where mask > 0 else 0, BF16 NHWC out (data gradient)
-// Block: 8 x 16 output pixels of one image, 8 warps, warp w owns tile row w.
+// An implicit GEMM on the 5th-generation tensor cores: one block of 128
+// threads computes a 16 x 8 pixel tile (M = 128) for all COUT channels
+// (N = COUT, at least 16) with K = 9 taps x CIN in steps of 16.  The input
+// tile and its ring are staged as 8-channel planes of 16-byte pixels, so the
+// A operand of every tap is a descriptor view of the same planes (start moved
+// by the tap offset; core matrices 8 pixels of a row, LBO one plane, SBO one
+// halo row).  The weights are staged per (tap, K step) as N x 16 core
+// matrices.  One thread issues the MMAs into a TMEM accumulator (32 columns)
+// and commits them to an mbarrier; each warp then reads its 32 pixels' rows.
 template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(256) k_conv(const bf16 *__restrict__ in, int H, int W,
+__global__ void __launch_bounds__(128) k_conv(const bf16 *__restrict__ in, int H, int W,
                                               const bf16 *__restrict__ wt, const float *__restrict__ bias,
                                               bf16 *__restrict__ out, const bf16 *__restrict__ mask,
                                               const float *__restrict__ resid_in, float *__restrict__ resid_out)
 {
-    constexpr int CS = CIN + 8;          // padded pixel stride (bank-conflict free ldmatrix)
-    constexpr int NT = COUT / 8;         // n-tiles of 8 output channels
-    __shared__ __align__(16) bf16 s_in[(kTH + 2) * (kTW + 2) * CS];
-    __shared__ __align__(16) bf16 s_w[9 * COUT * CS];
+    constexpr int NP = COUT < 16 ? 16 : COUT;       // MMA N
+    constexpr int G = CIN / 8;                      // 8-channel groups of the input
+    constexpr int KC = CIN / 16;                    // K steps per tap
+    constexpr int WBLK = (NP / 8) * 2 * 128;        // bytes of one (tap, K step) weight block
+    __shared__ __align__(1024) unsigned char s_in[G * kPlane];
+    __shared__ __align__(1024) unsigned char s_w[9 * KC * WBLK];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = blockIdx.z, y0 = blockIdx.y * kTH, x0 = blockIdx.x * kTW;
-    constexpr int VEC = CIN / 8;         // 16-byte vectors per pixel
-    for (int i = threadIdx.x; i < (kTH + 2) * (kTW + 2) * VEC; i += 256) {
-        const int pix = i / VEC, v = i - pix * VEC;
-        const int hy = pix / (kTW + 2), hx = pix - hy * (kTW + 2);
+    for (int i = tid; i < kHaloPix * G; i += 128) {
+        const int hp = i / G, g = i - hp * G;
+        const int hy = hp / (kTW + 2), hx = hp - hy * (kTW + 2);
         int gy = y0 + hy - 1, gx = x0 + hx - 1;
         gy += (gy < 0) ? H : 0;
         gy -= (gy >= H) ? H : 0;
         gx += (gx < 0) ? W : 0;
         gx -= (gx >= W) ? W : 0;
-        const uint4 *src = reinterpret_cast<const uint4 *>(in + (((size_t)b * H + gy) * W + gx) * CIN) + v;
-        *reinterpret_cast<uint4 *>(s_in + pix * CS + v * 8) = *src;
+        *reinterpret_cast<uint4 *>(s_in + g * kPlane + hp * 16) =
+            *(reinterpret_cast<const uint4 *>(in + (((size_t)b * H + gy) * W + gx) * CIN) + g);
     }
-    for (int i = threadIdx.x; i < 9 * COUT * VEC; i += 256) {
-        const int row = i / VEC, v = i - row * VEC;
-        *reinterpret_cast<uint4 *>(s_w + row * CS + v * 8) =
-            *(reinterpret_cast<const uint4 *>(wt + (size_t)row * CIN) + v);
+    for (int i = tid; i < 9 * NP * G; i += 128) {
+        const int tap = i / (NP * G), rem = i - tap * (NP * G), co = rem / G, g = rem - co * G;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (co < COUT) v = *(reinterpret_cast<const uint4 *>(wt + ((size_t)tap * COUT + co) * CIN) + g);
+        *reinterpret_cast<uint4 *>(s_w + (tap * KC + (g >> 1)) * WBLK + ((co >> 3) * 2 + (g & 1)) * 128 +
+                                   (co & 7) * 16) = v;
     }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_bar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(32));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");   // staged operands visible to the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float acc[NT][4];
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+    if (tid == 0) {
+        constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
+        const uint32_t a0 = smem_addr(s_in), w0 = smem_addr(s_w);
+        uint32_t acc = 0;
 #pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    const int apix = lane & 15, akoff = (lane >> 4) * 8;
-    const int brow = lane & 7, bkoff = ((lane >> 3) & 1) * 8, bnt = lane >> 4;
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap - dy * 3;
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap - dy * 3;
-#pragma unroll
-        for (int kc = 0; kc < CIN / 16; ++kc) {
-            uint32_t a0, a1, a2, a3;
-            ldsm_x4(a0, a1, a2, a3, s_in + ((warp + dy) * (kTW + 2) + apix + dx) * CS + kc * 16 + akoff);
-#pragma unroll
-            for (int n = 0; n + 1 < NT; n += 2) {
-                uint32_t b0, b1, b2, b3;
-                ldsm_x4(b0, b1, b2, b3, s_w + (tap * COUT + (n + bnt) * 8 + brow) * CS + kc * 16 + bkoff);
-                mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
-                mma_bf16(acc[n + 1], a0, a1, a2, a3, b2, b3);
-            }
-            if (NT & 1) {
-                uint32_t b0, b1;
-                ldsm_x2(b0, b1, s_w + (tap * COUT + (NT - 1) * 8 + brow) * CS + kc * 16 + bkoff);
-                mma_bf16(acc[NT - 1], a0, a1, a2, a3, b0, b1);
+            for (int kc = 0; kc < KC; ++kc) {
+                const uint64_t ad = umma_desc(a0 + 2 * kc * kPlane + (dy * (kTW + 2) + dx) * 16, kPlane, (kTW + 2) * 16);
+                const uint64_t bd = umma_desc(w0 + (tap * KC + kc) * WBLK, 128, 256);
+                umma_bf16(tmem, ad, bd, idesc, acc);
+                acc = 1;
             }
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_addr(&s_bar)));
     }
-    // epilogue: acc[n][0,1] -> pixel g, channels 2t, 2t+1; acc[n][2,3] -> pixel g + 8
-    const int g = lane >> 2, t = lane & 3;
-    const int y = y0 + warp;
+    uint32_t done = 0;
+    for (int it = 0; it < kWaitLimit && !done; ++it)
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done) : "r"(smem_addr(&s_bar)), "r"(0));
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!done) {
+        if (tid == 0) atomicOr(&g_sur_err, 1);
+    } else {
+        uint32_t r[NP];
+        tmem_load<NP>(tmem + ((uint32_t)(warp * 32) << 16), r);
+        const int m = warp * 32 + lane;
+        const int y = y0 + m / kTW, x = x0 + m % kTW;
+        const size_t pix = ((size_t)b * H + y) * W + x;
 #pragma unroll
-    for (int n = 0; n < NT; ++n) {
-        const int co = n * 8 + 2 * t;
-#pragma unroll
-        for (int hp = 0; hp < 2; ++hp) {
-            const int x = x0 + g + hp * 8;
-            const size_t pix = ((size_t)b * H + y) * W + x;
-            float v0 = acc[n][2 * hp], v1 = acc[n][2 * hp + 1];
+        for (int co = 0; co < COUT; co += 2) {
+            float v0 = __uint_as_float(r[co]), v1 = __uint_as_float(r[co + 1]);
             if (MODE != MODE_MASK) {
                 v0 += bias[co];
                 v1 += bias[co + 1];
@@ -152,9 +214,9 @@ __global__ void __launch_bounds__(256) k_conv(const bf16 *__restrict__ in, int H
                 v1 = fmaxf(v1, 0.f);
             }
             if (MODE == MODE_MASK) {
-                const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * COUT + co);
-                if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
-                if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
+                const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * COUT + co);
+                if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
             }
             if (MODE == MODE_RESID) {
                 resid_out[pix * 8 + co] = resid_in[pix * 8 + co] + v0;
@@ -164,6 +226,10 @@ __global__ void __launch_bounds__(256) k_conv(const bf16 *__restrict__ in, int H
             }
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
 }
 
 // Weight / bias gradient: dw[co][tap][ci] = sum_p dy[p][co] x[p + tap - 1][ci],
@@ -455,6 +521,16 @@ int sfail(int code, const std::string &m)
     return code;
 }
 
+// The sticky flag of the tensor-core waits (AAP_ETIMEOUT once set).
+int check_tc(cudaStream_t st)
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbolAsync(&v, g_sur_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return sfail(AAP_ECUDA, "reading the tensor-core wait flag");
+    return v ? sfail(AAP_ETIMEOUT, "a tensor-core completion wait gave up") : AAP_OK;
+}
+
 #define SCK(call)                                                                          \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
@@ -467,7 +543,7 @@ cudaError_t conv(const bf16 *in, int B, int H, int W, const bf16 *w, const float
                  const float *rin, float *rout, cudaStream_t st)
 {
     dim3 grid(W / kTW, H / kTH, B);
-    k_conv<CIN, COUT, MODE><<<grid, 256, 0, st>>>(in, H, W, w, bias, out, mask, rin, rout);
+    k_conv<CIN, COUT, MODE><<<grid, 128, 0, st>>>(in, H, W, w, bias, out, mask, rin, rout);
     return cudaGetLastError();
 }
 
@@ -497,7 +573,7 @@ cudaError_t conv_dw(const bf16 *x, const bf16 *dy, int dy_stride, int B, int H, 
     return cudaGetLastError();
 }
 
-bool valid_shape(int H, int W) { return H >= 8 && W >= 16 && H % 8 == 0 && W % 16 == 0 && H <= 4096 && W <= 4096; }
+bool valid_shape(int H, int W) { return H >= 16 && W >= 16 && H % 16 == 0 && W % 16 == 0 && H <= 4096 && W <= 4096; }
 
 }  // namespace
 
@@ -616,7 +692,7 @@ int aap_sur_create(const aap_sur_params *p, void *stream, aap_sur **out)
     s_err.clear();
     if (!p || !out) return sfail(AAP_EINVAL, "NULL argument");
     *out = nullptr;
-    if (!valid_shape(p->nby, p->nbx)) return sfail(AAP_EINVAL, "nby must be a multiple of 8 and nbx of 16 (<= 4096)");
+    if (!valid_shape(p->nby, p->nbx)) return sfail(AAP_EINVAL, "nby and nbx must be multiples of 16 (<= 4096)");
     if (p->max_batch < 1 || p->max_batch > 4096) return sfail(AAP_EINVAL, "max_batch must be in [1, 4096]");
     if (!(p->rho0 > 0) || !(p->eta_scale > 0) || !(p->lr > 0) || !(p->eps > 0))
         return sfail(AAP_EINVAL, "rho0, eta_scale, lr and eps must be positive");
@@ -823,6 +899,7 @@ int aap_sur_train_step(aap_sur *s, const float *dev_in, const float *dev_target,
         double tot = 0.0;
         for (float v : lp) tot += v;
         *loss_out = tot / (3.0 * (double)npix);
+        return check_tc(st);
     }
     return AAP_OK;
 }
@@ -833,7 +910,7 @@ int aap_sur_get_grads(aap_sur *s, float *host, int64_t count)
     if (!s || !host || count != s->nparam) return sfail(AAP_EINVAL, "bad arguments");
     SCK(cudaMemcpyAsync(host, s->g, (size_t)count * 4, cudaMemcpyDeviceToHost, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
-    return AAP_OK;
+    return check_tc(s->stream);
 }
 
 // ---- the convolution kernels alone (device buffers, BF16 as raw 16-bit) ----

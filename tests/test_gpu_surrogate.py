@@ -153,7 +153,7 @@ def test_network_loss_and_gradient(lib, conserve):
 
 
 def test_predict_zero_and_one_application(lib):
-    B, H, W = 2, 8, 16
+    B, H, W = 2, 16, 16
     s = A.aap_sur_create(A.aap_sur_params_default(nbx=W, nby=H, max_batch=B, seed=3))
     try:
         g = np.random.default_rng(4)
