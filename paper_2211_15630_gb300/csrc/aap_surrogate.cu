@@ -80,11 +80,16 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint6
                  ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
-// 16 or 32 FP32 columns of this warp's 32 TMEM lanes (one row each).
+// 8, 16 or 32 FP32 columns of this warp's 32 TMEM lanes (one row each).
 template <int NC>
 __device__ __forceinline__ void tmem_load(uint32_t taddr, uint32_t (&r)[NC])
 {
-    if constexpr (NC == 16) {
+    if constexpr (NC == 8) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7])
+                     : "r"(taddr));
+    } else if constexpr (NC == 16) {
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
                      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
@@ -107,38 +112,18 @@ __device__ __forceinline__ void tmem_load(uint32_t taddr, uint32_t (&r)[NC])
 
 enum { MODE_RELU = 0, MODE_RESID = 1, MODE_MASK = 2, MODE_LINEAR = 3 };
 
-// out[b, y, x, co] = sum_{tap, ci} w[tap][co][ci] * in[b, (y+dy-1) mod H, (x+dx-1) mod W, ci]
-// (tap = 3 dy + dx), then per MODE:
-//   MODE_RELU   + bias, ReLU, BF16 NHWC out
-//   MODE_LINEAR + bias, BF16 NHWC out
-//   MODE_RESID  + bias, FP32: resid_out = resid_in + value (NHWC, 8 channels)
-//   MODE_MASK   value where mask > 0 else 0, BF16 NHWC out (data gradient)
-// An implicit GEMM on the 5th-generation tensor cores: one block of 128
-// threads computes a 16 x 8 pixel tile (M = 128) for all COUT channels
-// (N = COUT, at least 16) with K = 9 taps x CIN in steps of 16.  The input
-// tile and its ring are staged as 8-channel planes of 16-byte pixels, so the
-// A operand of every tap is a descriptor view of the same planes (start moved
-// by the tap offset; core matrices 8 pixels of a row, LBO one plane, SBO one
-// halo row).  The weights are staged per (tap, K step) as N x 16 core
-// matrices.  One thread issues the MMAs into a TMEM accumulator (32 columns)
-// and commits them to an mbarrier; each warp then reads its 32 pixels' rows.
-template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(128) k_conv(const bf16 *__restrict__ in, int H, int W,
-                                              const bf16 *__restrict__ wt, const float *__restrict__ bias,
-                                              bf16 *__restrict__ out, const bf16 *__restrict__ mask,
-                                              const float *__restrict__ resid_in, float *__restrict__ resid_out)
+constexpr int kConvThreads = 256;
+
+// The 16 x 8 tile t (tiles ordered by image, then row, then column) with its
+// one-pixel ring, as 8-channel planes of 16-byte pixels (circular padding).
+template <int CIN>
+__device__ __forceinline__ void stage_halo(unsigned char *s_in, const bf16 *__restrict__ in, int H, int W, int t)
 {
-    constexpr int NP = COUT < 16 ? 16 : COUT;       // MMA N
-    constexpr int G = CIN / 8;                      // 8-channel groups of the input
-    constexpr int KC = CIN / 16;                    // K steps per tap
-    constexpr int WBLK = (NP / 8) * 2 * 128;        // bytes of one (tap, K step) weight block
-    __shared__ __align__(1024) unsigned char s_in[G * kPlane];
-    __shared__ __align__(1024) unsigned char s_w[9 * KC * WBLK];
-    __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_bar;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int b = blockIdx.z, y0 = blockIdx.y * kTH, x0 = blockIdx.x * kTW;
-    for (int i = tid; i < kHaloPix * G; i += 128) {
+    constexpr int G = CIN / 8;
+    const int tx = W / kTW, ty = H / kTH;
+    const int b = t / (tx * ty), r = t - b * (tx * ty);
+    const int y0 = (r / tx) * kTH, x0 = (r % tx) * kTW;
+    for (int i = threadIdx.x; i < kHaloPix * G; i += kConvThreads) {
         const int hp = i / G, g = i - hp * G;
         const int hy = hp / (kTW + 2), hx = hp - hy * (kTW + 2);
         int gy = y0 + hy - 1, gx = x0 + hx - 1;
@@ -149,20 +134,69 @@ __global__ void __launch_bounds__(128) k_conv(const bf16 *__restrict__ in, int H
         *reinterpret_cast<uint4 *>(s_in + g * kPlane + hp * 16) =
             *(reinterpret_cast<const uint4 *>(in + (((size_t)b * H + gy) * W + gx) * CIN) + g);
     }
-    for (int i = tid; i < 9 * NP * G; i += 128) {
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < kWaitLimit && !done; ++it)
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done) : "r"(bar), "r"(parity));
+    return done != 0;
+}
+
+// out[b, y, x, co] = sum_{tap, ci} w[tap][co][ci] * in[b, (y+dy-1) mod H, (x+dx-1) mod W, ci]
+// (tap = 3 dy + dx), then per MODE:
+//   MODE_RELU   + bias, ReLU, BF16 NHWC out
+//   MODE_LINEAR + bias, BF16 NHWC out
+//   MODE_RESID  + bias, FP32: resid_out = resid_in + value (NHWC, 8 channels)
+//   MODE_MASK   value where mask > 0 else 0, BF16 NHWC out (data gradient)
+// An implicit GEMM on the 5th-generation tensor cores.  Each 16 x 8 pixel
+// tile is one MMA row block (M = 128) for all COUT channels (N = COUT, at
+// least 16) with K = 9 taps x CIN in steps of 16.  The input tile and its
+// ring are staged as 8-channel planes of 16-byte pixels, so the A operand of
+// every tap is a descriptor view of the same planes (start moved by the tap
+// offset; core matrices 8 pixels of a row, LBO one plane, SBO one halo row).
+// The weights are staged once per block, per (tap, K step) as N x 16 core
+// matrices.  A block walks tiles with two halo buffers and two TMEM
+// accumulators (2 x 32 columns): thread 0 issues the MMAs of tile i and
+// commits them to that buffer's mbarrier while all threads stage tile i+1;
+// then the 8 warps read tile i's accumulator (warp w: TMEM lane quarter
+// w % 4, half of the columns) for the epilogue.
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ in, int H, int W, int ntiles,
+                                                       const bf16 *__restrict__ wt, const float *__restrict__ bias,
+                                                       bf16 *__restrict__ out, const bf16 *__restrict__ mask,
+                                                       const float *__restrict__ resid_in,
+                                                       float *__restrict__ resid_out)
+{
+    constexpr int NP = COUT < 16 ? 16 : COUT;       // MMA N
+    constexpr int NH = NP / 2;                      // accumulator columns read by one warp
+    constexpr int G = CIN / 8;                      // 8-channel groups of the input
+    constexpr int KC = CIN / 16;                    // K steps per tap
+    constexpr int WBLK = (NP / 8) * 2 * 128;        // bytes of one (tap, K step) weight block
+    __shared__ __align__(1024) unsigned char s_in[2][G * kPlane];
+    __shared__ __align__(1024) unsigned char s_w[9 * KC * WBLK];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < 9 * NP * G; i += kConvThreads) {
         const int tap = i / (NP * G), rem = i - tap * (NP * G), co = rem / G, g = rem - co * G;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (co < COUT) v = *(reinterpret_cast<const uint4 *>(wt + ((size_t)tap * COUT + co) * CIN) + g);
         *reinterpret_cast<uint4 *>(s_w + (tap * KC + (g >> 1)) * WBLK + ((co >> 3) * 2 + (g & 1)) * 128 +
                                    (co & 7) * 16) = v;
     }
+    if (blockIdx.x < ntiles) stage_halo<CIN>(s_in[0], in, H, W, blockIdx.x);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_bar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_bar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_bar[1])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                     "r"(32));
+                     "r"(64));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("fence.proxy.async.shared::cta;");   // staged operands visible to the tensor core
@@ -170,66 +204,80 @@ __global__ void __launch_bounds__(128) k_conv(const bf16 *__restrict__ in, int H
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = s_tmem;
-    if (tid == 0) {
-        constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
-        const uint32_t a0 = smem_addr(s_in), w0 = smem_addr(s_w);
-        uint32_t acc = 0;
+    const int tx = W / kTW, ty = H / kTH;
+    bool ok = true;
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int buf = it & 1;
+        if (tid == 0) {
+            constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
+            const uint32_t a0 = smem_addr(s_in[buf]), w0 = smem_addr(s_w);
+            uint32_t acc = 0;
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap - dy * 3;
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap - dy * 3;
 #pragma unroll
-            for (int kc = 0; kc < KC; ++kc) {
-                const uint64_t ad = umma_desc(a0 + 2 * kc * kPlane + (dy * (kTW + 2) + dx) * 16, kPlane, (kTW + 2) * 16);
-                const uint64_t bd = umma_desc(w0 + (tap * KC + kc) * WBLK, 128, 256);
-                umma_bf16(tmem, ad, bd, idesc, acc);
-                acc = 1;
+                for (int kc = 0; kc < KC; ++kc) {
+                    const uint64_t ad =
+                        umma_desc(a0 + 2 * kc * kPlane + (dy * (kTW + 2) + dx) * 16, kPlane, (kTW + 2) * 16);
+                    const uint64_t bd = umma_desc(w0 + (tap * KC + kc) * WBLK, 128, 256);
+                    umma_bf16(tmem + buf * 32, ad, bd, idesc, acc);
+                    acc = 1;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_addr(&s_bar[buf])));
+        }
+        // the next tile's input while the tensor core works (its buffer's
+        // previous MMAs were waited for in the previous iteration)
+        if (t + (int)gridDim.x < ntiles) stage_halo<CIN>(s_in[buf ^ 1], in, H, W, t + gridDim.x);
+        // every thread waits with a bound; the block then agrees on the outcome
+        const bool done = __syncthreads_and(mbar_wait(smem_addr(&s_bar[buf]), (uint32_t)(it >> 1) & 1u)) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!done) {
+            ok = false;
+            if (tid == 0) atomicOr(&g_sur_err, 1);
+        } else {
+            const int q = warp & 3, h = warp >> 2;
+            uint32_t r[NH];
+            tmem_load<NH>(tmem + buf * 32 + h * NH + ((uint32_t)(q * 32) << 16), r);
+            const int m = q * 32 + lane;
+            const int b = t / (tx * ty), rr = t - b * (tx * ty);
+            const int y = (rr / tx) * kTH + m / kTW, x = (rr % tx) * kTW + m % kTW;
+            const size_t pix = ((size_t)b * H + y) * W + x;
+#pragma unroll
+            for (int j = 0; j < NH; j += 2) {
+                const int co = h * NH + j;
+                if (co >= COUT) break;
+                float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+                if (MODE != MODE_MASK) {
+                    v0 += bias[co];
+                    v1 += bias[co + 1];
+                }
+                if (MODE == MODE_RELU) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                if (MODE == MODE_MASK) {
+                    const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * COUT + co);
+                    if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                    if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                }
+                if (MODE == MODE_RESID) {
+                    resid_out[pix * 8 + co] = resid_in[pix * 8 + co] + v0;
+                    resid_out[pix * 8 + co + 1] = resid_in[pix * 8 + co + 1] + v1;
+                } else {
+                    *reinterpret_cast<__nv_bfloat162 *>(out + pix * COUT + co) = __floats2bfloat162_rn(v0, v1);
+                }
             }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     ::"r"(smem_addr(&s_bar)));
+        asm volatile("fence.proxy.async.shared::cta;");   // the next tile's staged input
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!ok) break;                                   // block-uniform (from __syncthreads_and)
     }
-    uint32_t done = 0;
-    for (int it = 0; it < kWaitLimit && !done; ++it)
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}\n"
-                     : "=r"(done) : "r"(smem_addr(&s_bar)), "r"(0));
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!done) {
-        if (tid == 0) atomicOr(&g_sur_err, 1);
-    } else {
-        uint32_t r[NP];
-        tmem_load<NP>(tmem + ((uint32_t)(warp * 32) << 16), r);
-        const int m = warp * 32 + lane;
-        const int y = y0 + m / kTW, x = x0 + m % kTW;
-        const size_t pix = ((size_t)b * H + y) * W + x;
-#pragma unroll
-        for (int co = 0; co < COUT; co += 2) {
-            float v0 = __uint_as_float(r[co]), v1 = __uint_as_float(r[co + 1]);
-            if (MODE != MODE_MASK) {
-                v0 += bias[co];
-                v1 += bias[co + 1];
-            }
-            if (MODE == MODE_RELU) {
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
-            }
-            if (MODE == MODE_MASK) {
-                const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * COUT + co);
-                if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
-                if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
-            }
-            if (MODE == MODE_RESID) {
-                resid_out[pix * 8 + co] = resid_in[pix * 8 + co] + v0;
-                resid_out[pix * 8 + co + 1] = resid_in[pix * 8 + co + 1] + v1;
-            } else {
-                *reinterpret_cast<__nv_bfloat162 *>(out + pix * COUT + co) = __floats2bfloat162_rn(v0, v1);
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
 }
 
 // Weight / bias gradient: dw[co][tap][ci] = sum_p dy[p][co] x[p + tap - 1][ci],
@@ -538,12 +586,21 @@ int check_tc(cudaStream_t st)
             return sfail(AAP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
     } while (0)
 
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 148;
+    return n;
+}
+
 template <int CIN, int COUT, int MODE>
 cudaError_t conv(const bf16 *in, int B, int H, int W, const bf16 *w, const float *bias, bf16 *out, const bf16 *mask,
                  const float *rin, float *rout, cudaStream_t st)
 {
-    dim3 grid(W / kTW, H / kTH, B);
-    k_conv<CIN, COUT, MODE><<<grid, 128, 0, st>>>(in, H, W, w, bias, out, mask, rin, rout);
+    const int ntiles = (W / kTW) * (H / kTH) * B;
+    k_conv<CIN, COUT, MODE><<<std::min(ntiles, 4 * sm_count()), kConvThreads, 0, st>>>(in, H, W, ntiles, w, bias, out,
+                                                                                       mask, rin, rout);
     return cudaGetLastError();
 }
 
