@@ -327,6 +327,10 @@ def _bench_surrogate(A, W, torch, stream, train_traj=32, iters=300, horizon=100,
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     area = (512.0 / nb) ** 2
     held_out = np.linspace(0.3, 0.5, 16)          # 16 held-out seeds 20000..20015 over the eta range
+    ed = torch.zeros(1, device="cuda")
+    # the first call captures the predict graph for these buffers; later calls replay it
+    A.aap_sur_predict(s, f0.data_ptr(), ed.data_ptr(), 1, apps, fp.data_ptr())
+    torch.cuda.synchronize()
     for j, eta in enumerate(held_out):
         p = W.surrogate_training(eta=float(eta), seed=20000 + j)
         h = A.aap_create(p, stream.cuda_stream)
@@ -339,7 +343,7 @@ def _bench_surrogate(A, W, torch, stream, train_traj=32, iters=300, horizon=100,
         ev1.record(stream)
         torch.cuda.synchronize()
         t_part += ev0.elapsed_time(ev1)
-        ed = torch.full((1,), float(eta), device="cuda")
+        ed.fill_(float(eta))
         ev0.record(stream)
         A.aap_sur_predict(s, f0.data_ptr(), ed.data_ptr(), 1, apps, fp.data_ptr())
         ev1.record(stream)

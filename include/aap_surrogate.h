@@ -75,7 +75,11 @@ int aap_sur_get_grads(aap_sur *s, float *host, int64_t count);
 
 /* Apply the network `applications` times (10 particle steps each) to `batch`
  * field samples dev_in with per-sample noise strengths dev_eta (device,
- * batch floats); the result goes to dev_out (may alias dev_in). */
+ * batch floats); the result goes to dev_out (may alias dev_in).  The call's
+ * kernels are captured once as a CUDA graph on a private stream and replayed
+ * on the handle's stream while dev_in, dev_eta, dev_out, batch and
+ * applications stay the same (the weights are read when it runs, so training
+ * in between is seen). */
 int aap_sur_predict(aap_sur *s, const float *dev_in, const float *dev_eta, int32_t batch, int32_t applications,
                     float *dev_out);
 

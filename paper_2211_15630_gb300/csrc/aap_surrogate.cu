@@ -651,6 +651,12 @@ struct aap_sur {
     float *part = nullptr, *loss_part = nullptr;
     float *dmean = nullptr;                                            // [max_batch * 3] projected gradient means
     float *cpart = nullptr;                                            // chunk sums of the projection
+    // the last predict call, captured as a CUDA graph (replayed while the
+    // buffers, batch and number of applications stay the same)
+    cudaGraphExec_t pexec = nullptr;
+    cudaStream_t pstream = nullptr;
+    const void *pkey[3] = {nullptr, nullptr, nullptr};
+    int pbatch = -1, papps = -1;
     size_t part_floats = 0;
     int loss_blocks = 0;
     long long t = 0;                                                   // Adam step
@@ -674,6 +680,10 @@ int salloc(aap_sur *s, T **p, size_t bytes)
 
 void sfree(aap_sur *s)
 {
+    if (s->pexec) cudaGraphExecDestroy(s->pexec);
+    s->pexec = nullptr;
+    if (s->pstream) cudaStreamDestroy(s->pstream);
+    s->pstream = nullptr;
     for (void *q : s->allocs) cudaFree(q);
     s->allocs.clear();
 }
@@ -710,6 +720,31 @@ int forward(aap_sur *s, int batch)
         k_center_apply<<<batch * nchunk, 256, 0, st>>>(s->state2, s->cpart, H * W, nchunk, s->p.conserve);
         SCK(cudaGetLastError());
     }
+    return AAP_OK;
+}
+
+// The kernels of one predict call on s->stream: normalise, `applications`
+// forward passes, denormalise into dev_out.
+int enqueue_predict(aap_sur *s, const float *dev_in, const float *dev_eta, int batch, int applications, float *dev_out)
+{
+    const int H = s->H, W = s->W;
+    const int grid = 1024;
+    SCK(cudaMemcpyAsync(s->eta, dev_eta, (size_t)batch * 4, cudaMemcpyDeviceToDevice, s->stream));
+    k_fields_in<<<grid, 256, 0, s->stream>>>(dev_in, s->eta, batch, H, W, (float)s->p.rho0, (float)s->p.eta_center,
+                                             (float)s->p.eta_scale, s->state, s->x0);
+    SCK(cudaGetLastError());
+    for (int k = 0; k < applications; ++k) {
+        if (k > 0) {
+            k_state_to_input<<<grid, 256, 0, s->stream>>>(s->state, s->eta, batch, H, W, (float)s->p.eta_center,
+                                                          (float)s->p.eta_scale, s->x0);
+            SCK(cudaGetLastError());
+        }
+        int rc = forward(s, batch);
+        if (rc) return rc;
+        std::swap(s->state, s->state2);
+    }
+    k_fields_out<<<grid, 256, 0, s->stream>>>(s->state, batch, H, W, (float)s->p.rho0, dev_out);
+    SCK(cudaGetLastError());
     return AAP_OK;
 }
 
@@ -879,24 +914,44 @@ int aap_sur_predict(aap_sur *s, const float *dev_in, const float *dev_eta, int32
     Range range_("aap_sur_predict");
     if (!s || !dev_in || !dev_eta || !dev_out) return sfail(AAP_EINVAL, "NULL argument");
     if (batch < 1 || batch > s->maxb || applications < 0) return sfail(AAP_EINVAL, "bad batch or applications");
-    const int H = s->H, W = s->W;
-    const int grid = 1024;
-    SCK(cudaMemcpyAsync(s->eta, dev_eta, (size_t)batch * 4, cudaMemcpyDeviceToDevice, s->stream));
-    k_fields_in<<<grid, 256, 0, s->stream>>>(dev_in, s->eta, batch, H, W, (float)s->p.rho0, (float)s->p.eta_center,
-                                             (float)s->p.eta_scale, s->state, s->x0);
-    SCK(cudaGetLastError());
-    for (int k = 0; k < applications; ++k) {
-        if (k > 0) {
-            k_state_to_input<<<grid, 256, 0, s->stream>>>(s->state, s->eta, batch, H, W, (float)s->p.eta_center,
-                                                          (float)s->p.eta_scale, s->x0);
-            SCK(cudaGetLastError());
+    // a call is tens of short launches (4 convolutions per application): it
+    // is captured once as a graph on a private stream and replayed on the
+    // caller's stream while the buffers, batch and applications stay the same
+    const bool same = s->pexec && s->pkey[0] == dev_in && s->pkey[1] == dev_eta && s->pkey[2] == dev_out &&
+                      s->pbatch == batch && s->papps == applications;
+    if (!same) {
+        if (s->pexec) cudaGraphExecDestroy(s->pexec);
+        s->pexec = nullptr;
+        if (!s->pstream) SCK(cudaStreamCreateWithFlags(&s->pstream, cudaStreamNonBlocking));
+        cudaStream_t user = s->stream;
+        s->stream = s->pstream;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s->pstream, cudaStreamCaptureModeThreadLocal);
+        int rc = e == cudaSuccess ? enqueue_predict(s, dev_in, dev_eta, batch, applications, dev_out) : AAP_OK;
+        cudaError_t e2 = cudaStreamEndCapture(s->pstream, &g);
+        s->stream = user;
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
         }
-        int rc = forward(s, batch);
-        if (rc) return rc;
-        std::swap(s->state, s->state2);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return sfail(AAP_ECUDA, std::string("capturing the predict call: ") +
+                                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&s->pexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            s->pexec = nullptr;
+            return sfail(AAP_ECUDA, std::string("instantiating the predict graph: ") + cudaGetErrorString(e));
+        }
+        s->pkey[0] = dev_in;
+        s->pkey[1] = dev_eta;
+        s->pkey[2] = dev_out;
+        s->pbatch = batch;
+        s->papps = applications;
     }
-    k_fields_out<<<grid, 256, 0, s->stream>>>(s->state, batch, H, W, (float)s->p.rho0, dev_out);
-    SCK(cudaGetLastError());
+    SCK(cudaGraphLaunch(s->pexec, s->stream));
     return AAP_OK;
 }
 

@@ -254,3 +254,33 @@ def test_conserving_predict_keeps_grid_means(lib):
     ref = f.astype(np.float64).sum(axis=(2, 3))
     assert np.allclose(sums[3], ref, rtol=1e-4, atol=1e-3 * H * W)
     assert not np.allclose(sums[0], ref, rtol=1e-4, atol=1e-3 * H * W)
+
+
+def test_predict_replays_its_graph(lib):
+    """A predict call is captured as a CUDA graph and replayed while its buffers,
+    batch and number of applications stay the same: the replay gives the same
+    fields bit for bit, and six applications in one call match six chained
+    one-application calls (which re-normalise the fields in between)."""
+    B, H, W = 2, 16, 32
+    s = A.aap_sur_create(A.aap_sur_params_default(nbx=W, nby=H, max_batch=B, seed=21))
+    try:
+        A.aap_sur_set_params(s, _random_params(A.aap_sur_param_count(s), 22))
+        g = np.random.default_rng(23)
+        f = (np.abs(g.normal(size=(B, 3, H, W))) + 1.0).astype(np.float32)
+        fin, eta = _dev_f32(f), _dev_f32([0.38, 0.46])
+        out1, out2 = torch.zeros_like(fin), torch.zeros_like(fin)
+        A.aap_sur_predict(s, fin.data_ptr(), eta.data_ptr(), B, 6, out1.data_ptr())
+        torch.cuda.synchronize()
+        first = out1.clone()
+        out1.zero_()
+        A.aap_sur_predict(s, fin.data_ptr(), eta.data_ptr(), B, 6, out1.data_ptr())   # replay
+        torch.cuda.synchronize()
+        assert torch.equal(first, out1)
+        x, y = fin.clone(), out2
+        for _ in range(6):
+            A.aap_sur_predict(s, x.data_ptr(), eta.data_ptr(), B, 1, y.data_ptr())
+            torch.cuda.synchronize()
+            x, y = y, x
+        assert np.allclose(x.cpu().numpy(), first.cpu().numpy(), rtol=1e-4, atol=1e-4)
+    finally:
+        A.aap_sur_destroy(s)
