@@ -277,6 +277,7 @@ int set_capacity_mf(aap_handle *h)
     L.knn = p.kn;
     L.mf_n = p.n;
     L.mf_ncell = (long long)S.ncx * S.ncy;
+    AAP_CK(aapk::configure_mf_kernels(p.model, p.kn, L.hist_words, sm_count(), &L.mf_grid));
     return AAP_OK;
 }
 
@@ -565,8 +566,8 @@ int alloc_all(aap_handle *h)
         if ((rc = dev_alloc(h, &S.mf_cs, n * sizeof(int2)))) return rc;
         if ((rc = dev_alloc(h, &S.mf_sorted, n * sizeof(int4)))) return rc;
         if ((rc = dev_alloc(h, &S.mf_fix, n * sizeof(int2)))) return rc;
-        if ((rc = dev_alloc(h, &S.mf_nfix, sizeof(int)))) return rc;
-        AAP_CK(cudaMemsetAsync(S.mf_nfix, 0, sizeof(int), h->stream));
+        if ((rc = dev_alloc(h, &S.mf_nfix, 2 * sizeof(int)))) return rc;
+        AAP_CK(cudaMemsetAsync(S.mf_nfix, 0, 2 * sizeof(int), h->stream));
         AAP_CK(cudaMemsetAsync(S.mf_cnt, 0, (size_t)ncell * sizeof(int), h->stream));
     }
     if (!h->member) {

@@ -97,7 +97,7 @@ struct Sys {
     int2 *mf_cs;                // [n] cell and arrival rank of each record
     int4 *mf_sorted;            // [n] records in cell order
     int2 *mf_fix;               // [n] particles left to the exact pass: sorted index, rings or -1
-    int *mf_nfix;               // queue length
+    int *mf_nfix;               // [2]: queue length, next warp task of the update
     // species (Sec. 2.5): ids in [sp_end[s-1], sp_end[s]) are species s; with
     // one species, entry 0 repeats the scalar parameters above
     int nsp;

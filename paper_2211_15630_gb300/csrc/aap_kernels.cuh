@@ -27,6 +27,7 @@ struct LaunchCfg {
     // metric-free step (knn > 0): cell count, scan, scatter, k-nearest update
     int knn;
     long long mf_n, mf_ncell;
+    int mf_grid;                 // persistent blocks of the k-nearest update
 };
 
 size_t step_smem_bytes(int stage_cap, int nce_max, int hist_words);
@@ -37,6 +38,9 @@ cudaError_t configure_step_kernel(int model, int threads, size_t smem_bytes, int
 // One full step: k_step then k_finish.  With ev != nullptr, ev[0..2] are
 // recorded before k_step, after k_step and after k_finish.
 cudaError_t launch_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev = nullptr);
+
+// Blocks of the metric-free update that are resident at once on sm_count SMs.
+cudaError_t configure_mf_kernels(int model, int knn, int hist_words, int sm_count, int *grid);
 
 // The metric-free step (knn > 0): the kernels of launch_step for a flat system.
 cudaError_t launch_mf_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev);

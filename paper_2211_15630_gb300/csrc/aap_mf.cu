@@ -57,7 +57,10 @@ __global__ void k_mf_count(const Sys *__restrict__ sys, const Ctl *__restrict__ 
     const int cur = (int)(ctl->step & 1);
     const int ncx = S.ncx, ncy = S.ncy, sx = S.sx, sy = S.sy;
     const int4 *__restrict__ rec = S.rec[cur];
-    if (blockIdx.x == 0 && threadIdx.x == 0) *S.mf_nfix = 0;      // queue of k_mf_exact
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S.mf_nfix[0] = 0;       // queue of k_mf_exact
+        S.mf_nfix[1] = 0;       // next warp task of k_mf_update
+    }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S.n;
          i += (long long)gridDim.x * blockDim.x) {
         const int4 r = rec[i];
@@ -261,19 +264,60 @@ __device__ __forceinline__ void for_ring(const MfGeo &G, const int4 *__restrict_
     }
 }
 
+// Rings 0 .. kWin of a particle whose window of (2 kWin + 1)^2 cells lies
+// inside the box (no image, no mirror) are visited by rows: cells x0 .. x1
+// (offsets from the particle's cell) of one row are one contiguous range of
+// the cell order, so a warp of particles from neighbouring cells walks a few
+// ranges in step instead of one cell at a time.  d2 is formed exactly as
+// for_cell forms it for an untransformed cell, so both see bit-identical
+// distances.
+constexpr int kWin = 2;
+
+template <class F>
+__device__ __forceinline__ void for_row(const MfGeo &G, const int4 *__restrict__ srt, const int *__restrict__ st,
+                                        const int *__restrict__ blk, int c, int x0, int x1, int X, int Y,
+                                        long long q, F &&f)
+{
+    if (x0 > x1) return;
+    const int b = cell_begin(st, blk, c + x0), e = cell_begin(st, blk, c + x1 + 1);
+#pragma unroll 2
+    for (int j = b; j < e; ++j) {
+        const int4 rj = srt[j];
+        const float dx = (float)(rj.x - X) * G.ux;
+        const float dy = (float)(rj.y - Y) * G.uy;
+        if (j != q) f(fmaf(dx, dx, dy * dy), rj, j, 4u, 0u);
+    }
+}
+
+// Cell offsets lo .. hi (clamped to the window) along one axis that a disc of
+// squared radius tau around the coordinate X of cell cx can reach.  The disc is
+// widened by 1e-4 relative and 2 units, so every candidate left out lies
+// strictly farther than tau even after the rounding of d2; an infinite tau
+// gives the whole window.
+__device__ __forceinline__ void window_span(float tau, int X, int cx, int s, float u, int &lo, int &hi)
+{
+    const float r = sqrtf(tau) * 1.0001f / u + 2.0f;
+    const int ru = r < (float)(3 << s) ? (int)r : (3 << s);
+    lo = max(((X - ru) >> s) - cx, -kWin);
+    hi = min(((X + ru) >> s) - cx, kWin);
+}
+
+__device__ __forceinline__ bool window_inside(const MfGeo &G, int cx, int cy)
+{
+    return cx >= kWin && cx < G.ncx - kWin && cy >= kWin && cy < G.ncy - kWin;
+}
+
 // The k-th smallest distance so far: an ascending list whose first KMAX - k
-// entries hold -1, updated by a min/max pass (no branches, no indices).
+// entries hold -1.  Inserting x into the sorted list sets entry s to
+// max(d[s-1], min(d[s], x)): every entry comes from the old list alone, so
+// the KMAX updates are independent (no dependency chain, no indices).
 template <int KMAX>
 __device__ __forceinline__ void kth_offer(float (&d)[KMAX], float d2)
 {
     if (d2 < d[KMAX - 1]) {
-        float x = d2;
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) {
-            const float lo = fminf(d[s], x);
-            x = fmaxf(d[s], x);
-            d[s] = lo;
-        }
+        for (int s = KMAX - 1; s > 0; --s) d[s] = fmaxf(d[s - 1], fminf(d[s], d2));
+        d[0] = fminf(d[0], d2);
     }
 }
 
@@ -574,14 +618,16 @@ __device__ __forceinline__ void mf_flush(const Sys &S, int cur, MfAcc acc, long 
             if (s_hist[i]) atomicAdd(S.hist + i, (unsigned long long)s_hist[i]);
 }
 
-// One thread per record in cell order.  Pass 1 finds the k-th smallest
+// One thread per record in cell order; each warp takes tasks of 32
+// consecutive records from a counter until none are left (persistent blocks,
+// so that no warp idles behind a slow one of its block).  Pass 1 finds the k-th smallest
 // distance tau by the ring search (Sec. 3.3); pass 2 sums over the candidates
 // below tau and at tau in 2^32 fixed point, so that the sums do not depend on
 // the arrival order inside a cell.  Particles whose window cannot certify the
 // list, or with several candidates at exactly tau, are queued for
 // k_mf_exact and left to it.
 template <int NT, int MODEL, int KMAX>
-__global__ void __launch_bounds__(NT) k_mf_update(const Sys *__restrict__ sys, const Ctl *__restrict__ ctl)
+__global__ void __launch_bounds__(NT, KMAX > 16 ? 2 : 4) k_mf_update(const Sys *__restrict__ sys, const Ctl *__restrict__ ctl)
 {
     extern __shared__ int s_hist[];                 // [bins_theta + bins_nbr] while measuring
     __shared__ long long s_red[5][NT / 32];
@@ -599,69 +645,106 @@ __global__ void __launch_bounds__(NT) k_mf_update(const Sys *__restrict__ sys, c
         for (int i = threadIdx.x; i < S.bins_theta + S.bins_nbr; i += NT) s_hist[i] = 0;
     __syncthreads();
     MfAcc acc = {0, 0, 0, 0, 0};
-    const long long q = blockIdx.x * (long long)NT + threadIdx.x;
-    if (q < n) {
-        const MfSelf P = mf_self<MODEL>(S, G, srt[q]);
-        float d[KMAX];
+    const long long ntask = (n + 31) >> 5;
+    for (;;) {
+        int task = 0;
+        if ((threadIdx.x & 31) == 0) task = atomicAdd(S.mf_nfix + 1, 1);
+        task = __shfl_sync(0xffffffffu, task, 0);
+        if (task >= ntask) break;
+        const long long q = ((long long)task << 5) + (threadIdx.x & 31);
+        if (q < n) {
+            const MfSelf P = mf_self<MODEL>(S, G, srt[q]);
+            float d[KMAX];
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) d[s] = s < KMAX - k ? -1.0f : __int_as_float(0x7f800000);
-        bool certified = false;
-        int rfin = 0;
-        for (int ring = 0;; ++ring) {
-            for_ring(G, srt, st, blk, ring, P.rmx, P.rmy, P.cx, P.cy, P.X, P.Y, q,
-                     [&](float d2, const int4 &, int, unsigned, unsigned) { kth_offer<KMAX>(d, d2); });
-            // every unvisited candidate lies at least this far away
-            const int rx = min(ring, P.rmx), ry = min(ring, P.rmy);
-            float gx = __int_as_float(0x7f800000), gy = gx;
-            const int lo = P.cx - rx, hi = P.cx + rx, lo2 = P.cy - ry, hi2 = P.cy + ry;
-            if (!(G.bx && lo <= -G.ncx)) gx = (float)(P.X - lo * (1 << sx)) * G.ux;
-            if (!(G.bx && hi >= 2 * G.ncx - 1)) gx = fminf(gx, (float)((hi + 1) * (1 << sx) - P.X) * G.ux);
-            if (!(G.by && lo2 <= -G.ncy)) gy = (float)(P.Y - lo2 * (1 << sy)) * G.uy;
-            if (!(G.by && hi2 >= 2 * G.ncy - 1)) gy = fminf(gy, (float)((hi2 + 1) * (1 << sy) - P.Y) * G.uy);
-            const float g = fminf(gx, gy);
-            if (d[KMAX - 1] <= g * g * 0.99999f) {
-                certified = true;
-                rfin = ring;
-                break;
+            for (int s = 0; s < KMAX; ++s) d[s] = s < KMAX - k ? -1.0f : __int_as_float(0x7f800000);
+            bool certified = false;
+            int rfin = 0;
+            const bool win = window_inside(G, P.cx, P.cy);
+            const int crow = P.cy * G.ncx + P.cx;       // cell index of the particle's cell
+            for (int ring = win ? kWin : 0;; ++ring) {
+                const auto offer = [&](float d2, const int4 &, int, unsigned, unsigned) { kth_offer<KMAX>(d, d2); };
+                if (win && ring == kWin) {
+                    // rings 0 and 1, then the cells of ring 2 that the k-th
+                    // distance found so far still reaches (the others hold
+                    // only candidates beyond it, which can never enter the list)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for_row(G, srt, st, blk, crow + dy * G.ncx, -1, 1, P.X, P.Y, q, offer);
+                    int xl, xh, yl, yh;
+                    window_span(d[KMAX - 1], P.X, P.cx, sx, G.ux, xl, xh);
+                    window_span(d[KMAX - 1], P.Y, P.cy, sy, G.uy, yl, yh);
+                    for (int dy = yl; dy <= yh; ++dy) {
+                        const int c = crow + dy * G.ncx;
+                        if (dy == -kWin || dy == kWin) {
+                            for_row(G, srt, st, blk, c, xl, xh, P.X, P.Y, q, offer);
+                        } else {
+                            if (xl == -kWin) for_row(G, srt, st, blk, c, -kWin, -kWin, P.X, P.Y, q, offer);
+                            if (xh == kWin) for_row(G, srt, st, blk, c, kWin, kWin, P.X, P.Y, q, offer);
+                        }
+                    }
+                } else {
+                    for_ring(G, srt, st, blk, ring, P.rmx, P.rmy, P.cx, P.cy, P.X, P.Y, q, offer);
+                }
+                // every unvisited candidate lies at least this far away
+                const int rx = min(ring, P.rmx), ry = min(ring, P.rmy);
+                float gx = __int_as_float(0x7f800000), gy = gx;
+                const int lo = P.cx - rx, hi = P.cx + rx, lo2 = P.cy - ry, hi2 = P.cy + ry;
+                if (!(G.bx && lo <= -G.ncx)) gx = (float)(P.X - lo * (1 << sx)) * G.ux;
+                if (!(G.bx && hi >= 2 * G.ncx - 1)) gx = fminf(gx, (float)((hi + 1) * (1 << sx) - P.X) * G.ux);
+                if (!(G.by && lo2 <= -G.ncy)) gy = (float)(P.Y - lo2 * (1 << sy)) * G.uy;
+                if (!(G.by && hi2 >= 2 * G.ncy - 1)) gy = fminf(gy, (float)((hi2 + 1) * (1 << sy) - P.Y) * G.uy);
+                const float g = fminf(gx, gy);
+                if (d[KMAX - 1] <= g * g * 0.99999f) {
+                    certified = true;
+                    rfin = ring;
+                    break;
+                }
+                if (ring >= P.rmx && ring >= P.rmy) break;
             }
-            if (ring >= P.rmx && ring >= P.rmy) break;
-        }
-        bool queued = !certified;
-        if (certified) {
-            const float tau = d[KMAX - 1];
-            long long a0 = 0, a1 = 0;
-            int nlt = 0, neq = 0;
-            const int order = S.order;
-            for (int ring = 0; ring <= rfin; ++ring)
-                for_ring(G, srt, st, blk, ring, P.rmx, P.rmy, P.cx, P.cy, P.X, P.Y, q,
-                         [&](float d2, const int4 &rj, int, unsigned, unsigned flips) {
-                             if (d2 > tau) return;
-                             float cs, sn;
-                             image_cos_sin<MODEL>(__int_as_float(rj.z), flips, order, cs, sn);
-                             if (MODEL == 1) {
-                                 float t = P.osi * -cs + P.oci * sn;      // sin(o (theta_j - theta_i))
-                                 if (P.grow) t *= P.grow[species_of(S, (unsigned)rj.w)];
-                                 a0 += __float2ll_rn(t * kFix32F);
-                             } else {
-                                 if (MODEL == 2 && fmaf(P.ci, cs, P.si * sn) < 0.f) {   // Eq. (collision_NVM)
-                                     cs = -cs;
-                                     sn = -sn;
-                                 }
-                                 a0 += __float2ll_rn(cs * kFix32F);
-                                 a1 += __float2ll_rn(sn * kFix32F);
-                             }
-                             if (d2 < tau) ++nlt; else ++neq;
-                         });
-            if (nlt + neq <= k) {
-                const float f0 = (float)a0 * (1.0f / kFix32F), f1 = (float)a1 * (1.0f / kFix32F);
-                mf_finish<MODEL>(S, G, P, step, nxt, q, P.ci + f0, P.si + f1, f0, nlt + neq, measure, s_hist, acc);
-            } else {
-                queued = true;                       // several candidates at exactly tau
+            bool queued = !certified;
+            if (certified) {
+                const float tau = d[KMAX - 1];
+                long long a0 = 0, a1 = 0;
+                int nlt = 0, neq = 0;
+                const int order = S.order;
+                const auto sum = [&](float d2, const int4 &rj, int, unsigned, unsigned flips) {
+                    if (d2 > tau) return;
+                    float cs, sn;
+                    image_cos_sin<MODEL>(__int_as_float(rj.z), flips, order, cs, sn);
+                    if (MODEL == 1) {
+                        float t = P.osi * -cs + P.oci * sn;      // sin(o (theta_j - theta_i))
+                        if (P.grow) t *= P.grow[species_of(S, (unsigned)rj.w)];
+                        a0 += __float2ll_rn(t * kFix32F);
+                    } else {
+                        if (MODEL == 2 && fmaf(P.ci, cs, P.si * sn) < 0.f) {   // Eq. (collision_NVM)
+                            cs = -cs;
+                            sn = -sn;
+                        }
+                        a0 += __float2ll_rn(cs * kFix32F);
+                        a1 += __float2ll_rn(sn * kFix32F);
+                    }
+                    if (d2 < tau) ++nlt; else ++neq;
+                };
+                if (win) {
+                    // the window's cells that a disc of squared radius tau reaches
+                    int xl, xh, yl, yh;
+                    window_span(tau, P.X, P.cx, sx, G.ux, xl, xh);
+                    window_span(tau, P.Y, P.cy, sy, G.uy, yl, yh);
+                    for (int dy = yl; dy <= yh; ++dy)
+                        for_row(G, srt, st, blk, crow + dy * G.ncx, xl, xh, P.X, P.Y, q, sum);
+                }
+                for (int ring = win ? kWin + 1 : 0; ring <= rfin; ++ring)
+                    for_ring(G, srt, st, blk, ring, P.rmx, P.rmy, P.cx, P.cy, P.X, P.Y, q, sum);
+                if (nlt + neq <= k) {
+                    const float f0 = (float)a0 * (1.0f / kFix32F), f1 = (float)a1 * (1.0f / kFix32F);
+                    mf_finish<MODEL>(S, G, P, step, nxt, q, P.ci + f0, P.si + f1, f0, nlt + neq, measure, s_hist, acc);
+                } else {
+                    queued = true;                       // several candidates at exactly tau
+                }
             }
-        }
-        if (queued) {
-            const int e = atomicAdd(S.mf_nfix, 1);
-            S.mf_fix[e] = make_int2((int)q, certified ? rfin : -1);
+            if (queued) {
+                const int e = atomicAdd(S.mf_nfix, 1);
+                S.mf_fix[e] = make_int2((int)q, certified ? rfin : -1);
+            }
         }
     }
     mf_flush<NT>(S, cur, acc, s_red, measure, s_hist);
@@ -708,9 +791,10 @@ __global__ void __launch_bounds__(NT) k_mf_exact(const Sys *__restrict__ sys, co
 template <int MODEL, int KMAX>
 cudaError_t launch_update(const LaunchCfg &L, cudaStream_t st)
 {
-    const long long blocks = (L.mf_n + kMfThreads - 1) / kMfThreads;
+    const long long blocks = std::min<long long>((L.mf_n + kMfThreads - 1) / kMfThreads, L.mf_grid);
     const size_t smem = (size_t)L.hist_words * sizeof(int);
-    k_mf_update<kMfThreads, MODEL, KMAX><<<(unsigned)blocks, kMfThreads, smem, st>>>(L.sys, L.ctl);
+    k_mf_update<kMfThreads, MODEL, KMAX><<<(unsigned)std::max<long long>(blocks, 1), kMfThreads, smem, st>>>(L.sys,
+                                                                                                        L.ctl);
     k_mf_exact<64, MODEL, KMAX><<<(unsigned)std::min<long long>((L.mf_n + 63) / 64, 1024), 64, smem, st>>>(L.sys,
                                                                                                            L.ctl);
     return cudaGetLastError();
@@ -724,7 +808,37 @@ cudaError_t launch_update_m(const LaunchCfg &L, cudaStream_t st)
     return launch_update<MODEL, kMaxKnn>(L, st);
 }
 
+template <int MODEL, int KMAX>
+cudaError_t update_blocks_per_sm(size_t smem, int *bps)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_mf_update<kMfThreads, MODEL, KMAX>, kMfThreads, smem);
+}
+
+template <int MODEL>
+cudaError_t update_blocks_per_sm_m(int knn, size_t smem, int *bps)
+{
+    if (knn <= 8) return update_blocks_per_sm<MODEL, 8>(smem, bps);
+    if (knn <= 16) return update_blocks_per_sm<MODEL, 16>(smem, bps);
+    return update_blocks_per_sm<MODEL, kMaxKnn>(smem, bps);
+}
+
 }  // namespace
+
+cudaError_t configure_mf_kernels(int model, int knn, int hist_words, int sm_count, int *grid)
+{
+    const size_t smem = (size_t)hist_words * sizeof(int);
+    int bps = 0;
+    cudaError_t e;
+    switch (model) {
+    case 0: e = update_blocks_per_sm_m<0>(knn, smem, &bps); break;
+    case 1: e = update_blocks_per_sm_m<1>(knn, smem, &bps); break;
+    case 2: e = update_blocks_per_sm_m<2>(knn, smem, &bps); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    *grid = std::max(1, bps) * std::max(1, sm_count);
+    return cudaSuccess;
+}
 
 cudaError_t launch_mf_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev)
 {
