@@ -49,7 +49,20 @@ namespace aapk {
 namespace {
 
 constexpr int kMfThreads = 256;
-constexpr float kFix32F = 4294967296.0f;    // 2^32: order-free neighbour sums
+constexpr float kFix32F = 4294967296.0f;    // 2^32: order-free weighted sums (several species)
+
+// x in units of 2^-22, rounded to the nearest integer (ties to even), as the
+// bits of x 2^22 + 1.5 2^23: one FFMA whose single rounding lands on an
+// integer because the float spacing there is 1.  For |x| <= 1 the integer is
+// the bits minus 0x4B400000, so a sum of n such words minus n 0x4B400000
+// (mod 2^32) is the exact integer sum as long as it fits int32 -- here at
+// most 32 terms of |x| <= 1, below 2^28.  No float-to-int conversion
+// instruction is needed.
+__device__ __forceinline__ unsigned fix22_word(float x)
+{
+    return __float_as_uint(fmaf(x, 4194304.0f, 12582912.0f));
+}
+constexpr unsigned kFix22Bias = 0x4B400000u;
 
 __global__ void k_mf_count(const Sys *__restrict__ sys, const Ctl *__restrict__ ctl)
 {
@@ -703,7 +716,8 @@ __global__ void __launch_bounds__(NT, KMAX > 16 ? 2 : 4) k_mf_update(const Sys *
             bool queued = !certified;
             if (certified) {
                 const float tau = d[KMAX - 1];
-                long long a0 = 0, a1 = 0;
+                long long g0 = 0;                    // several species (weights beyond 1): 2^-32 units
+                unsigned w0 = 0, w1 = 0;             // otherwise fix22 words, bias removed below
                 int nlt = 0, neq = 0;
                 const int order = S.order;
                 const auto sum = [&](float d2, const int4 &rj, int, unsigned, unsigned flips) {
@@ -712,15 +726,15 @@ __global__ void __launch_bounds__(NT, KMAX > 16 ? 2 : 4) k_mf_update(const Sys *
                     image_cos_sin<MODEL>(__int_as_float(rj.z), flips, order, cs, sn);
                     if (MODEL == 1) {
                         float t = P.osi * -cs + P.oci * sn;      // sin(o (theta_j - theta_i))
-                        if (P.grow) t *= P.grow[species_of(S, (unsigned)rj.w)];
-                        a0 += __float2ll_rn(t * kFix32F);
+                        if (P.grow) g0 += __float2ll_rn(t * P.grow[species_of(S, (unsigned)rj.w)] * kFix32F);
+                        else w0 += fix22_word(t);
                     } else {
                         if (MODEL == 2 && fmaf(P.ci, cs, P.si * sn) < 0.f) {   // Eq. (collision_NVM)
                             cs = -cs;
                             sn = -sn;
                         }
-                        a0 += __float2ll_rn(cs * kFix32F);
-                        a1 += __float2ll_rn(sn * kFix32F);
+                        w0 += fix22_word(cs);
+                        w1 += fix22_word(sn);
                     }
                     if (d2 < tau) ++nlt; else ++neq;
                 };
@@ -735,7 +749,10 @@ __global__ void __launch_bounds__(NT, KMAX > 16 ? 2 : 4) k_mf_update(const Sys *
                 for (int ring = win ? kWin + 1 : 0; ring <= rfin; ++ring)
                     for_ring(G, srt, st, blk, ring, P.rmx, P.rmy, P.cx, P.cy, P.X, P.Y, q, sum);
                 if (nlt + neq <= k) {
-                    const float f0 = (float)a0 * (1.0f / kFix32F), f1 = (float)a1 * (1.0f / kFix32F);
+                    const unsigned bias = kFix22Bias * (unsigned)(nlt + neq);
+                    const float f0 = (MODEL == 1 && P.grow) ? (float)g0 * (1.0f / kFix32F)
+                                                            : (float)(int)(w0 - bias) * (1.0f / kFixNbF);
+                    const float f1 = (float)(int)(w1 - bias) * (1.0f / kFixNbF);
                     mf_finish<MODEL>(S, G, P, step, nxt, q, P.ci + f0, P.si + f1, f0, nlt + neq, measure, s_hist, acc);
                 } else {
                     queued = true;                       // several candidates at exactly tau
