@@ -922,7 +922,9 @@ int ens_combine(aap_ens *e)
     if (bps < 1) return fail(AAP_EINVAL, "step kernel does not fit on an SM for this ensemble");
     const int nsm = sm_count();
     L.grid_step = (int)std::max<long long>(1, std::min<long long>(total, (long long)bps * nsm));
-    L.grid_finish = (int)std::max<long long>(1, std::min<long long>(256, (total * aapk::kCntStride + 255) / 256));
+    // one warp per replica for the sums, and about one counter word per thread
+    L.grid_finish = (int)std::max<long long>(std::max<long long>(1, ((long long)e->m.size() + 7) / 8),
+                                             std::min<long long>(256, (total * aapk::kCntStride + 255) / 256));
     L.scratch_per_block = aapk::stage_bytes(L.scratch_cap) + aapk::spill_list_bytes(L.spill_list_cap);
     L.scratch_per_block = (L.scratch_per_block + 255) / 256 * 256;
     const size_t need = L.scratch_per_block * L.grid_step;

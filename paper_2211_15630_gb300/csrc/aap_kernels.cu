@@ -717,42 +717,42 @@ k_step(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_base,
 }
 
 // Close the step: p(t+1) from the integer sums, clear the consumed buffer's
-// counters, advance the step.  The last block to arrive does the per-system
-// work; every block clears a share of the counters.
-__global__ void k_finish(Sys *sys, int nsys, Ctl *ctl)
+// counters, advance the step.  Every thread clears counter words of the flat
+// range over all systems' tiles; the warps of all blocks take one system each
+// for the sums (its 64 accumulator slots loaded at once, then cleared); the
+// last block to arrive advances the step.
+__global__ void k_finish(Sys *sys, int nsys, const int *__restrict__ tile_base, Ctl *ctl)
 {
+    static_assert(kAccSlots == 64, "two accumulator slots per lane");
     __shared__ int s_last;
     const long long step = ctl->step;
     const int cur = (int)(step & 1);
-    for (int si = 0; si < nsys; ++si) {
-        int *c = sys[si].cnt[cur];
-        const long long nw = (long long)sys[si].ntiles * kCntStride;
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw;
-             i += (long long)gridDim.x * blockDim.x)
-            c[i] = 0;
+    const long long nw = (long long)tile_base[nsys] * kCntStride;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i / kCntStride);
+        const int si = nsys > 1 ? sys_of_tile(tile_base, nsys, g) : 0;
+        sys[si].cnt[cur][(long long)(g - tile_base[si]) * kCntStride + (int)(i % kCntStride)] = 0;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = (atomicAdd(&ctl->finish_ticket, 1) == (int)gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    // one warp per system: the 64 accumulator slots summed by the lanes
-    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    for (int si = threadIdx.x >> 5; si < nsys; si += nwarp) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int si = gw; si < nsys; si += nwarps) {
         Sys &S = sys[si];
         unsigned long long *a = S.acc + (size_t)cur * kAccSlots * kAccWords;
-        long long v[5];
+        unsigned long long x0[5], x1[5];
 #pragma unroll
         for (int w = 0; w < 5; ++w) {
-            long long x = 0;
-            for (int k = lane; k < kAccSlots; k += 32) {
-                x += (long long)a[k * kAccWords + w];
-                a[k * kAccWords + w] = 0;
-            }
-            v[w] = warp_sum_ll(x);           // exact integer sum, lane 0 holds it
+            x0[w] = a[lane * kAccWords + w];
+            x1[w] = a[(lane + 32) * kAccWords + w];
         }
+#pragma unroll
+        for (int w = 0; w < 5; ++w) {
+            a[lane * kAccWords + w] = 0;
+            a[(lane + 32) * kAccWords + w] = 0;
+        }
+        long long v[5];
+#pragma unroll
+        for (int w = 0; w < 5; ++w) v[w] = warp_sum_ll((long long)(x0[w] + x1[w]));   // exact, lane 0 holds it
         if (lane != 0) continue;
         const double n = (double)S.n;
         const double dc = (double)v[0] / kFixStep, ds = (double)v[1] / kFixStep;
@@ -788,6 +788,11 @@ __global__ void k_finish(Sys *sys, int nsys, Ctl *ctl)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = (atomicAdd(&ctl->finish_ticket, 1) == (int)gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
         ctl->tile_next = 0;
         ctl->finish_ticket = 0;
         ctl->step = step + 1;
@@ -982,7 +987,7 @@ static cudaError_t launch_step_t(const LaunchCfg &L, cudaStream_t st, cudaEvent_
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-    k_finish<<<L.grid_finish, 256, 0, st>>>(L.sys, L.nsys, L.ctl);
+    k_finish<<<L.grid_finish, 256, 0, st>>>(L.sys, L.nsys, L.tile_base, L.ctl);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
@@ -1004,7 +1009,7 @@ cudaError_t launch_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev)
     if (L.knn > 0) {
         cudaError_t e = launch_mf_step(L, st, ev);
         if (e != cudaSuccess) return e;
-        k_finish<<<L.grid_finish, 256, 0, st>>>(L.sys, L.nsys, L.ctl);
+        k_finish<<<L.grid_finish, 256, 0, st>>>(L.sys, L.nsys, L.tile_base, L.ctl);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
