@@ -84,8 +84,9 @@ class aap_sur_params(C.Structure):
                 ("beta2", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64)]
 
 
-# launch policies tried by aap_ens_autotune: (threads, nominal tile w, h)
-ENS_POLICIES = ((512, 32, 16), (256, 32, 16), (512, 16, 16), (256, 16, 16),
+# launch policies tried by aap_ens_autotune: (threads, nominal tile w, h);
+# 0 x 0 picks each replica's tile by its density (about 1024 particles a tile)
+ENS_POLICIES = ((512, 32, 16), (256, 32, 16), (512, 16, 16), (512, 0, 0),
                 (512, 32, 32), (256, 16, 8), (512, 64, 16), (512, 16, 8))
 
 _lib = None

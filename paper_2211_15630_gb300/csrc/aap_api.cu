@@ -834,13 +834,28 @@ int read_results(aap_handle *h, aap_results *out)
 
 // ------------------------------------------------------------ ensembles --
 // Candidate launch policies of the ensemble autotuner: threads per block and
-// the nominal tile shape of every replica (clipped to the replica's box).
+// the nominal tile shape of every replica (clipped to the replica's box); a
+// shape of 0 x 0 picks each replica's tile by its density (density_tile).
 struct EnsPolicy {
     int threads, tw, th;
 };
-constexpr EnsPolicy kPolicies[8] = {{512, 32, 16}, {256, 32, 16}, {512, 16, 16}, {256, 16, 16},
+constexpr EnsPolicy kPolicies[8] = {{512, 32, 16}, {256, 32, 16}, {512, 16, 16}, {512, 0, 0},
                                     {512, 32, 32}, {256, 16, 8},  {512, 64, 16}, {512, 16, 8}};
 constexpr int kNumPolicies = 8;
+
+// A tile of about 1024 particles (the load that suits one block of 512
+// threads at rho = 2 with 32 x 16 cells): fewer cells at high density, more
+// at low density, so that the staging area (sized by the densest replica)
+// still allows two blocks per SM.
+void density_tile(const aap_params &p, int *tw, int *th)
+{
+    const double ncx = std::max(1.0, std::floor(p.lx / p.r)), ncy = std::max(1.0, std::floor(p.ly / p.r));
+    const double mu = (double)p.n / (ncx * ncy);
+    if (mu <= 1.25) { *tw = 32; *th = 32; }
+    else if (mu <= 2.5) { *tw = 32; *th = 16; }
+    else if (mu <= 5.0) { *tw = 16; *th = 16; }
+    else { *tw = 16; *th = 8; }
+}
 
 }  // namespace
 
@@ -964,6 +979,7 @@ int ens_build(aap_ens *e, int pol)
         h->stream = e->stream;
         h->nom_tw = kPolicies[pol].tw;
         h->nom_th = kPolicies[pol].th;
+        if (h->nom_tw == 0) density_tile(h->p, &h->nom_tw, &h->nom_th);
         if (!h->p.threads) h->p.threads = kPolicies[pol].threads;
         h->d_sys = e->d_sys + r;
         h->d_ctl = e->d_ctl;
