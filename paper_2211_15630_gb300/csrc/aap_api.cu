@@ -931,9 +931,25 @@ int ens_combine(aap_ens *e)
     }
     if (total >= (1ll << 30)) return fail(AAP_EINVAL, "too many tiles in the ensemble");
     AAP_CK(cudaMemcpy(e->d_tile_base, tb.data(), tb.size() * sizeof(int), cudaMemcpyHostToDevice));
-    const size_t smem = aapk::step_smem_bytes(L.stage_cap, L.nce_max, L.hist_words);
     int bps = 0;
-    AAP_CK(aapk::configure_step_kernel(L.model, L.threads, smem, &bps));
+    {
+        // a second block per SM is worth more than staging the densest
+        // replicas' tiles in shared memory: lower the staging capacity while
+        // that gains it (denser tiles then take the global-scratch path)
+        int cap = L.stage_cap;
+        for (;;) {
+            AAP_CK(aapk::configure_step_kernel(L.model, L.threads,
+                                               aapk::step_smem_bytes(cap, L.nce_max, L.hist_words), &bps));
+            if (bps >= 2 || cap <= 1024) break;
+            cap -= 64;
+        }
+        if (bps >= 2) {
+            L.stage_cap = cap;
+        } else {
+            AAP_CK(aapk::configure_step_kernel(L.model, L.threads,
+                                               aapk::step_smem_bytes(L.stage_cap, L.nce_max, L.hist_words), &bps));
+        }
+    }
     if (bps < 1) return fail(AAP_EINVAL, "step kernel does not fit on an SM for this ensemble");
     const int nsm = sm_count();
     L.grid_step = (int)std::max<long long>(1, std::min<long long>(total, (long long)bps * nsm));

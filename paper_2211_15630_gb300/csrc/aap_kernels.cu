@@ -19,6 +19,7 @@
 //              of the buffer just consumed and advances the step counter.
 #include <algorithm>
 
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include "aap_device.cuh"
@@ -1026,7 +1027,15 @@ cudaError_t launch_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev)
 template <int NT, int MODEL>
 static cudaError_t config_t(size_t smem, int *bps)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_step<NT, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The limit belongs to the kernel, not to a handle: raise it to the
+    // largest size any handle of this process asked for, so that creating a
+    // smaller system never breaks the launches of a larger one.
+    static std::atomic<int> limit{0};
+    int want = (int)smem, prev = limit.load();
+    while (want > prev && !limit.compare_exchange_weak(prev, want)) {
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_step<NT, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         std::max(want, limit.load()));
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_step<NT, MODEL>, NT, smem);
 }

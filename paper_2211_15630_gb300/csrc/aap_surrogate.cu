@@ -21,6 +21,7 @@
 //                             fixed order (deterministic)
 //   k_adam                    Adam step on the FP32 master weights
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -619,7 +620,14 @@ cudaError_t conv_dw(const bf16 *x, const bf16 *dy, int dy_stride, int B, int H, 
 {
     const int rows = dw_rows(H);
     const size_t smem = dw_smem<CIN, COUT>(H, W);
-    cudaError_t e = cudaFuncSetAttribute(k_conv_dw<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the limit only ever grows, so that a captured graph of a wider field
+    // still launches after a narrower one was configured
+    static std::atomic<int> limit{0};
+    int prev = limit.load();
+    while ((int)smem > prev && !limit.compare_exchange_weak(prev, (int)smem)) {
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_conv_dw<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         std::max((int)smem, limit.load()));
     if (e != cudaSuccess) return e;
     dim3 grid(H / rows, B);
     k_conv_dw<CIN, COUT><<<grid, 256, smem, st>>>(x, dy, dy_stride, H, W, rows, part);

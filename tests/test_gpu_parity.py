@@ -178,6 +178,31 @@ def test_deterministic_and_resume_bitwise(lib):
         A.aap_destroy(h2)
 
 
+def test_handles_of_different_staging_sizes_coexist(lib):
+    """A dense system (large shared-memory staging) keeps stepping after a
+    sparse one (small staging) was created, and its trajectory is the one it
+    has alone: the kernel's shared-memory limit is a per-process maximum."""
+    dense = params(n=40000, lx=100.0, ly=100.0, eta=0.3, seed=41)       # rho = 4
+    sparse = params(n=2000, lx=60.0, ly=60.0, eta=0.3, seed=42)         # rho = 0.56
+    ref = A.aap_create(dense)
+    try:
+        A.aap_step(ref, 10)
+        want = A.aap_get_state(ref, dense.n)
+    finally:
+        A.aap_destroy(ref)
+    h1 = A.aap_create(dense)
+    h2 = A.aap_create(sparse)
+    try:
+        assert A.aap_get_layout(h1).stage_cap > A.aap_get_layout(h2).stage_cap
+        A.aap_step(h2, 5)
+        A.aap_step(h1, 10)
+        for u, v in zip(A.aap_get_state(h1, dense.n), want):
+            assert np.array_equal(u, v)
+    finally:
+        A.aap_destroy(h1)
+        A.aap_destroy(h2)
+
+
 def test_translation_by_whole_tiles_bitwise(lib):
     """Periodic box, shift every particle by whole tiles: the trajectory is the
     shifted trajectory bit for bit (the noise is keyed on id, not position)."""
