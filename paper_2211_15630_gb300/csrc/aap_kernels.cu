@@ -338,7 +338,7 @@ __device__ __forceinline__ void neighbour_sum_sp(const float4 *__restrict__ P, c
 // Phase 2 of a tile, staged in A (shared memory or the block's scratch).
 template <int NT, int MODEL>
 __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tables &tb, long long step,
-                                          const int *spill_e, const unsigned char *spill_s)
+                                          const int *spill_e, const unsigned char *spill_s, int next_g)
 {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -389,6 +389,9 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
         A.cell[k] = (unsigned short)(ec | (g.flip << 14));
         A.slot[k] = (unsigned short)atomicAdd(&tb.hist[ec], 1);
     }
+    // the next tile's index, fetched by thread 0 at the start of this tile:
+    // published only now, so that no warp waited for the atomic's round trip
+    if (tid == 0) T.next = next_g;
     __syncthreads();
     PHASE_MARK(0);
 
@@ -677,10 +680,11 @@ k_step(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_base,
             for (int i = threadIdx.x; i < words; i += NT) dst[i] = src[i];
         }
         __syncthreads();
+        int next_g = 0;         // thread 0: the tile after this one (published in tile_body)
         if (threadIdx.x == 0) {
             T.sysi = si;
             T.tile = g - tile_base[si];
-            T.next = atomicAdd(&ctl->tile_next, 1);
+            next_g = atomicAdd(&ctl->tile_next, 1);
         }
         __syncthreads();
 #ifdef AAP_PHASE_TIMING
@@ -699,15 +703,16 @@ k_step(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_base,
         const long long tb0 = clock64();
 #endif
         if (T.m <= stage_cap) {
-            tile_body<NT, MODEL>(T, As, tb, step, spill_e, spill_s);
+            tile_body<NT, MODEL>(T, As, tb, step, spill_e, spill_s, next_g);
         } else if (T.m <= scratch_cap) {
             // a dense tile: staged in global scratch, except the records the
             // candidate loops read, which still fit the shared staging area
             Stage Ah = Ag;
             if ((size_t)T.m * sizeof(float4) <= stage_bytes(stage_cap)) Ah.P = reinterpret_cast<float4 *>(smem);
-            tile_body<NT, MODEL>(T, Ah, tb, step, spill_e, spill_s);
+            tile_body<NT, MODEL>(T, Ah, tb, step, spill_e, spill_s, next_g);
         } else if (threadIdx.x == 0) {
             atomicOr(T.S.err, ERR_STAGE | ERR_LOST);
+            T.next = next_g;
         }
 #ifdef AAP_PHASE_TIMING
         if (threadIdx.x == 0)
