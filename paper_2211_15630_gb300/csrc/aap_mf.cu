@@ -820,6 +820,7 @@ cudaError_t launch_update(const LaunchCfg &L, cudaStream_t st)
 template <int MODEL>
 cudaError_t launch_update_m(const LaunchCfg &L, cudaStream_t st)
 {
+    if (L.knn <= 6) return launch_update<MODEL, 6>(L, st);       // k = 6: the common metric-free choice
     if (L.knn <= 8) return launch_update<MODEL, 8>(L, st);
     if (L.knn <= 16) return launch_update<MODEL, 16>(L, st);
     return launch_update<MODEL, kMaxKnn>(L, st);
@@ -834,6 +835,7 @@ cudaError_t update_blocks_per_sm(size_t smem, int *bps)
 template <int MODEL>
 cudaError_t update_blocks_per_sm_m(int knn, size_t smem, int *bps)
 {
+    if (knn <= 6) return update_blocks_per_sm<MODEL, 6>(smem, bps);
     if (knn <= 8) return update_blocks_per_sm<MODEL, 8>(smem, bps);
     if (knn <= 16) return update_blocks_per_sm<MODEL, 16>(smem, bps);
     return update_blocks_per_sm<MODEL, kMaxKnn>(smem, bps);
