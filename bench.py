@@ -196,6 +196,34 @@ def _bench_brownian(A, W, torch, stream, steps):
             "ms_per_step": ms / steps, "steps": steps}
 
 
+def _bench_coarse(A, W, torch, stream, peak, frames=50):
+    """Coarse-grained fields (density, polarisation per bin): the surrogate's
+    N = 524,288, L = 512 state into 128 x 128 bins, and an N = 2^24, L = 2896
+    state into 724 x 724 bins; whole calls (clear, bin, finish) timed with
+    events over back-to-back frames.  Algorithmic bytes: the 16 B record of
+    every particle read once (the fields themselves are small)."""
+    out = {}
+    for name, p, nb in (("sur_N524288_L512_128x128", W.surrogate_training(eta=0.4, seed=3), 128),
+                        ("vicsek_N2^24_L2896_724x724", W.vicsek_large(seed=5), 724)):
+        h = A.aap_create(p, stream.cuda_stream)
+        A.aap_step(h, 20)
+        f = torch.empty(3 * nb * nb, device="cuda", dtype=torch.float32)
+        A.aap_coarse_grain(h, nb, nb, f.data_ptr())
+        A.aap_sync(h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(frames):
+            A.aap_coarse_grain(h, nb, nb, f.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / frames
+        gbs = 16.0 * p.n / (us * 1e-6) / 1e9
+        out[name] = {"us_per_frame": us, "particles_per_s": p.n / (us * 1e-6), "achieved_gbs": gbs,
+                     "frac_of_hbm": gbs / peak}
+        A.aap_destroy(h)
+    return out
+
+
 def _bench_metric_free(A, W, torch, stream, steps, kn=6):
     """mfVM (k nearest neighbours, Sec. 2.3) at N = 2^24, L = 2896: whole
     steps timed with events, then the kernel split from the library's timers."""
@@ -514,6 +542,7 @@ def main():
         extras["brownian"] = _bench_brownian(A, W, torch, stream, 500)
         extras["metric_free"] = _bench_metric_free(A, W, torch, stream, 100)
         extras["ensemble"] = _bench_ensemble(A, W, torch, stream, 200)
+        extras["coarse_grain"] = _bench_coarse(A, W, torch, stream, _peaks()[0])
         with torch.cuda.stream(stream):     # torch copies and library calls share one stream
             # conserving (grid means of density and polarisation kept) and free
             extras["surrogate"] = _bench_surrogate(A, W, torch, stream, conserve=3)

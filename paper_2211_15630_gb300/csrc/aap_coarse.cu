@@ -1,0 +1,134 @@
+// aap_coarse.cu -- coarse-grained fields of a state: density and
+// polarisation per bin (the fields the learned surrogate advances), in exact
+// 64-bit integer sums so that they are reproducible bit for bit.
+#include <algorithm>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "aap_internal.cuh"
+#include "aap_kernels.cuh"
+
+namespace aapk {
+
+namespace {
+
+// Bin of a fixed-point coordinate u (units of the box axis): the definition is
+// the FP64 product (int)(u * (cs / 2^s) * (nb / L)) clamped to [0, nb).  It is
+// evaluated in FP32 and taken from there unless the FP32 value lies within its
+// error bound (3 roundings of 2^-24 relative, widened to 2.5e-7 t + 1e-6) of a
+// bin edge, where the FP64 product decides; so the result is the FP64 one for
+// every particle, with FP64 work (slow on this GPU) for a few in a million.
+struct BinAxis {
+    double cs_unit, f;          // cs / 2^s, nb / L
+    float f_unit;               // bins per unit
+    int nb;
+};
+
+__device__ __forceinline__ int coarse_bin(long long u, const BinAxis &a)
+{
+    const float t = (float)u * a.f_unit;
+    const float fl = floorf(t), fr = t - fl, m = fmaf(t, 2.5e-7f, 1e-6f);
+    int i = (int)fl;
+    if (fr < m || fr > 1.0f - m) i = (int)(((double)u * a.cs_unit) * a.f);
+    return min(max(i, 0), a.nb - 1);
+}
+
+// cos or sin times 2^32 rounded to a 64-bit integer, equal to __float2ll_rn
+// of it, from 32-bit conversions: below 2^31 in magnitude one conversion;
+// above, |x| >= 1/2 carries at most 24 significant bits, so x 2^32 is a
+// multiple of 2^8 and x 2^24 converts exactly.
+__device__ __forceinline__ long long fix32_ll(float x)
+{
+    const float v = x * 4294967296.0f;
+    if (fabsf(v) < 2147483648.0f) return (long long)__float2int_rn(v);
+    return (long long)__float2int_rn(x * 16777216.0f) * 256;
+}
+
+__device__ __forceinline__ void coarse_add(unsigned long long *acc, long long nb, long long bin, float th)
+{
+    float sn, cs;
+    sincosf(th, &sn, &cs);
+    atomicAdd(acc + bin, 1ull);
+    atomicAdd(acc + nb + bin, (unsigned long long)fix32_ll(cs));
+    atomicAdd(acc + 2 * nb + bin, (unsigned long long)fix32_ll(sn));
+}
+
+// Counts and sums of cos theta, sin theta per bin of the state in buffer b,
+// in exact 64-bit integers (cos scaled by 2^32), so that the fields are
+// reproducible bit for bit.  acc: [3][nbx*nby], zeroed by the caller.  Blocks
+// take whole tiles and read only the stored records (the valid slots of the
+// nine regions), then the spilled records, shared out over the blocks.  The
+// sums go straight to acc: the lanes of a warp that hit one bin are merged
+// by the memory system (a shared-memory window of the tile's bins was slower:
+// same-address shared atomics serialise).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_coarse_tiles(Sys S, int b, BinAxis ax, BinAxis ay, unsigned long long *acc)
+{
+    const long long nb = (long long)ax.nb * ay.nb;
+    for (int tile = blockIdx.x; tile < S.ntiles; tile += gridDim.x) {
+        const int tx = tile % S.ntx, ty = tile / S.ntx;
+        const long long ux0 = (long long)S.x0tab[tx] << S.sx, uy0 = (long long)S.y0tab[ty] << S.sy;
+        const int4 *base = S.rec[b] + (long long)tile * S.tile_slots;
+        for (int r = 0; r < kRegions; ++r) {
+            const int cnt = min(S.cnt[b][tile * kCntStride + r], S.cap[r]);
+            const int4 *reg = base + S.off[r];
+            for (int k = threadIdx.x; k < cnt; k += NT) {
+                const int4 rec = reg[k];
+                const int ix = coarse_bin(ux0 + rec.x, ax), iy = coarse_bin(uy0 + rec.y, ay);
+                coarse_add(acc, nb, (long long)iy * ax.nb + ix, __int_as_float(rec.z));
+            }
+        }
+    }
+    const int nsp = min(S.spill_cnt[b], S.spill_cap);
+    for (int e = blockIdx.x * NT + threadIdx.x; e < nsp; e += gridDim.x * NT) {
+        const int4 rec = S.spill_rec[b][e];
+        const int tile = S.spill_key[b][e] / kCntStride;
+        const int tx = tile % S.ntx, ty = tile / S.ntx;
+        const int ix = coarse_bin(((long long)S.x0tab[tx] << S.sx) + rec.x, ax);
+        const int iy = coarse_bin(((long long)S.y0tab[ty] << S.sy) + rec.y, ay);
+        coarse_add(acc, nb, (long long)iy * ax.nb + ix, __int_as_float(rec.z));
+    }
+}
+
+// Fields per unit area: density, polarisation x, polarisation y (planes of
+// nbx*nby floats, row-major with x fastest).
+__global__ void k_coarse_finish(const unsigned long long *acc, int nbx, int nby, double inv_area, float *out)
+{
+    const long long nb = (long long)nbx * nby;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        out[i] = (float)((double)acc[i] * inv_area);
+        out[nb + i] = (float)((double)(long long)acc[nb + i] / kFix * inv_area);
+        out[2 * nb + i] = (float)((double)(long long)acc[2 * nb + i] / kFix * inv_area);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_coarse(const Sys &S, int b, int nbx, int nby, unsigned long long *acc, float *out,
+                          cudaStream_t st)
+{
+    const long long nb = (long long)nbx * nby;
+    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)nb * 3 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    BinAxis ax, ay;
+    ax.cs_unit = S.csx_d / (double)(1ll << S.sx);
+    ax.f = (double)nbx / S.lx;
+    ax.f_unit = (float)(ax.cs_unit * ax.f);
+    ax.nb = nbx;
+    ay.cs_unit = S.csy_d / (double)(1ll << S.sy);
+    ay.f = (double)nby / S.ly;
+    ay.f_unit = (float)(ay.cs_unit * ay.f);
+    ay.nb = nby;
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(S.ntiles, 8 * nsm));
+    k_coarse_tiles<256><<<grid, 256, 0, st>>>(S, b, ax, ay, acc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const double inv_area = (double)nbx * nby / (S.lx * S.ly);
+    k_coarse_finish<<<(unsigned)std::min<long long>((nb + 255) / 256, 4096), 256, 0, st>>>(acc, nbx, nby, inv_area, out);
+    return cudaGetLastError();
+}
+
+}  // namespace aapk

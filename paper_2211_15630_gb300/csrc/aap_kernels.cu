@@ -934,47 +934,6 @@ __global__ void k_observe(Sys S, int b, unsigned long long *out)
     }
 }
 
-// ------------------------------------------------------- coarse graining --
-// Bin the particles of buffer b into nbx x nby cells of the box: counts and
-// sums of cos theta, sin theta, in exact 64-bit integers (cos scaled by 2^32)
-// so that the fields are reproducible bit for bit.  acc: [3][nbx*nby].
-__global__ void k_coarse_accumulate(Sys S, int b, int nbx, int nby, unsigned long long *acc)
-{
-    const long long total = (long long)S.ntiles * S.tile_slots + S.spill_cap;
-    const long long nb = (long long)nbx * nby;
-    const double fx = (double)nbx / S.lx, fy = (double)nby / S.ly;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
-         g += (long long)gridDim.x * blockDim.x) {
-        int4 r;
-        int tile;
-        if (!fetch_record(S, b, g, r, tile)) continue;
-        const int tx = tile % S.ntx, ty = tile / S.ntx;
-        const double gx = ((double)((long long)tile_x0(S, tx) << S.sx) + (double)r.x) * (S.csx_d / (double)(1ll << S.sx));
-        const double gy = ((double)((long long)tile_y0(S, ty) << S.sy) + (double)r.y) * (S.csy_d / (double)(1ll << S.sy));
-        const int ix = min(max((int)(gx * fx), 0), nbx - 1);
-        const int iy = min(max((int)(gy * fy), 0), nby - 1);
-        const long long bin = (long long)iy * nbx + ix;
-        float sn, cs;
-        sincosf(__int_as_float(r.z), &sn, &cs);
-        atomicAdd(acc + bin, 1ull);
-        atomicAdd(acc + nb + bin, (unsigned long long)__float2ll_rn(cs * 4294967296.0f));
-        atomicAdd(acc + 2 * nb + bin, (unsigned long long)__float2ll_rn(sn * 4294967296.0f));
-    }
-}
-
-// Fields per unit area: density, polarisation x, polarisation y (planes of
-// nbx*nby floats, row-major with x fastest).
-__global__ void k_coarse_finish(const unsigned long long *acc, int nbx, int nby, double inv_area, float *out)
-{
-    const long long nb = (long long)nbx * nby;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb;
-         i += (long long)gridDim.x * blockDim.x) {
-        out[i] = (float)((double)acc[i] * inv_area);
-        out[nb + i] = (float)((double)(long long)acc[nb + i] / kFix * inv_area);
-        out[2 * nb + i] = (float)((double)(long long)acc[2 * nb + i] / kFix * inv_area);
-    }
-}
-
 // --------------------------------------------------------------- launchers --
 size_t step_smem_bytes(int stage_cap, int nce_max, int hist_words)
 {
@@ -1083,18 +1042,6 @@ cudaError_t launch_observe(const Sys &S, int b, unsigned long long *out, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_coarse(const Sys &S, int b, int nbx, int nby, unsigned long long *acc, float *out,
-                          cudaStream_t st)
-{
-    const long long nb = (long long)nbx * nby;
-    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)nb * 3 * sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    k_coarse_accumulate<<<1024, 256, 0, st>>>(S, b, nbx, nby, acc);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const double inv_area = (double)nbx * nby / (S.lx * S.ly);
-    k_coarse_finish<<<(unsigned)std::min<long long>((nb + 255) / 256, 4096), 256, 0, st>>>(acc, nbx, nby, inv_area, out);
-    return cudaGetLastError();
-}
 
 #ifdef AAP_PHASE_TIMING
 cudaError_t read_phase_times(unsigned long long *out16)

@@ -167,6 +167,69 @@ def test_coarse_grain_conserves(lib, oracle):
         A.aap_destroy(h)
 
 
+@pytest.mark.parametrize("lx,ly,nbx,nby,bx", [(300.0, 210.0, 77, 53, 0), (150.0, 97.0, 211, 13, 1)])
+def test_coarse_grain_exact_bins_odd_geometry(lib, lx, ly, nbx, nby, bx):
+    """Bin widths that are not powers of two (and, second case, bins finer
+    than the cells in x, reflecting walls): every particle's bin is
+    floor(x nbx / L) of its FP64 position, so the counts equal numpy's exactly;
+    the polarisation sums agree with FP64 cos / sin to FP32 rounding."""
+    torch = pytest.importorskip("torch")
+    p = params(n=int(2 * lx * ly), lx=lx, ly=ly, eta=0.4, seed=17, bx=bx, by=bx)
+    h = A.aap_create(p)
+    try:
+        A.aap_step(h, 6)
+        out = torch.zeros(3 * nbx * nby, dtype=torch.float32, device="cuda")
+        A.aap_coarse_grain(h, nbx, nby, out.data_ptr())
+        A.aap_sync(h)
+        f = out.cpu().numpy().reshape(3, nby, nbx).astype(np.float64)
+        area = (lx / nbx) * (ly / nby)
+        x, y, th = A.aap_get_state(h, p.n)
+        ix = np.clip((x * (nbx / lx)).astype(np.int64), 0, nbx - 1)
+        iy = np.clip((y * (nby / ly)).astype(np.int64), 0, nby - 1)
+        counts = np.zeros((nby, nbx))
+        np.add.at(counts, (iy, ix), 1.0)
+        assert np.array_equal(np.round(f[0] * area), counts)
+        cs = np.zeros((nby, nbx))
+        sn = np.zeros((nby, nbx))
+        np.add.at(cs, (iy, ix), np.cos(th.astype(np.float64)))
+        np.add.at(sn, (iy, ix), np.sin(th.astype(np.float64)))
+        tol = 1e-6 * (counts + 1.0)
+        assert np.all(np.abs(f[1] * area - cs) < tol) and np.all(np.abs(f[2] * area - sn) < tol)
+    finally:
+        A.aap_destroy(h)
+
+
+def test_coarse_grain_with_spilled_records(lib):
+    """A clustered state with an explicit capacity keeps particles in the spill
+    list: the fields still count every particle in its FP64 bin."""
+    torch = pytest.importorskip("torch")
+    from tests import inputs
+    n, L, nb = 3000, 24.0, 6
+    x, y, th = inputs.clustered_state(n, L, L, 3, 12.2, 11.7, 2.5)
+    p = params(n=n, lx=L, ly=L, eta=0.2, v=0.3, seed=23, tile_w=8, tile_h=8, capacity=1.0)
+    h = A.aap_create(p)
+    try:
+        A.aap_set_state(h, x, y, th.astype(np.float32), step=0)
+        A.aap_step(h, 1)
+        assert A.aap_observe(h).flags & A.AAP_FLAG_SPILLED
+        out = torch.zeros(3 * nb * nb, dtype=torch.float32, device="cuda")
+        A.aap_coarse_grain(h, nb, nb, out.data_ptr())
+        A.aap_sync(h)
+        f = out.cpu().numpy().reshape(3, nb, nb).astype(np.float64)
+        xs, ys, ts = A.aap_get_state(h, n)
+        ix = np.clip((xs * (nb / L)).astype(np.int64), 0, nb - 1)
+        iy = np.clip((ys * (nb / L)).astype(np.int64), 0, nb - 1)
+        counts = np.zeros((nb, nb))
+        np.add.at(counts, (iy, ix), 1.0)
+        area = (L / nb) ** 2
+        assert np.array_equal(np.round(f[0] * area), counts)
+        cs = np.zeros((nb, nb))
+        np.add.at(cs, (iy, ix), np.cos(ts.astype(np.float64)))
+        assert np.all(np.abs(f[1] * area - cs) < 1e-6 * (counts + 1.0))
+    finally:
+        A.aap_destroy(h)
+
+
 def test_brownian_workload_one_step(lib, oracle):
     """The Brownian workload (N = 2^20, 724 x 724, reflecting walls, dt = 0.01):
     sampled one-step parity in the launch configuration of the benchmark."""

@@ -55,6 +55,19 @@ def test_noalloc_coarse_grain_matches_two_calls_in_a_row(lib):
         A.aap_destroy(h)
 
 
+def test_noalloc_matches_on_odd_bin_widths(lib):
+    """Bin widths that are not powers of two: both entry points bin each
+    particle at floor(x nb / L) of its FP64 position and sum the same integers."""
+    p = A.aap_params_default(n=90000, lx=300.0, ly=300.0, eta=0.4, seed=23)
+    h = A.aap_create(p)
+    try:
+        A.aap_step(h, 5)
+        ref, got = _fields_both_ways(h, p, 97, 0)
+        assert np.array_equal(got, ref)
+    finally:
+        A.aap_destroy(h)
+
+
 def test_noalloc_rejects_too_many_bins(lib):
     with pytest.raises(A.AapError) as e:
         A.aap_coarse_grain_noalloc(0, 0, 0, 0, 10.0, 10.0, 512, 512, 1, 0)
