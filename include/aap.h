@@ -191,7 +191,11 @@ int aap_destroy(aap_handle *h);
 /* Advance nsteps >= 0 time steps: for the VM and NVM one collision followed by
  * streaming (Sec. 2.1); for the Langevin model one Euler-Maruyama step of
  * length dt (Sec. 2.2); then the boundary rule of Sec. 2.4.  Every step also
- * measures p and the mean neighbour number on the fly.  Enqueues work only.
+ * measures p and the mean neighbour number on the fly.  Enqueues work; every
+ * 128 steps (counted across calls) the device error word is copied, and the
+ * call waits for the copy taken 128 steps before, so that tile regions
+ * overflowed by growing clusters are enlarged in time (the state is kept bit
+ * for bit) while the GPU keeps at least 128 steps queued.
  * Mirrors <model>_update_timesteps (Sec. 4). */
 int aap_step(aap_handle *h, int64_t nsteps);
 
@@ -233,7 +237,8 @@ int aap_get_layout(aap_handle *h, aap_layout *out);
 
 /* Advance nsteps steps measuring on the fly (like
  * <model>_measurement_timesteps, Sec. 4): the states t0 .. t0+nsteps-1 are
- * added to the running sums read by aap_get_results.  Enqueues work only. */
+ * added to the running sums read by aap_get_results.  Queues and waits like
+ * aap_step. */
 int aap_measure(aap_handle *h, int64_t nsteps);
 
 /* Normalised measurement results accumulated since creation or the last

@@ -94,8 +94,12 @@ struct aap_handle {
     long long launches[3] = {0, 0, 0};
     // capacity management
     double factor = 4.0;            // region slots over the mean occupancy
-    int *pinned_err = nullptr;      // error word copied after each aap_step
+    int *pinned_err = nullptr;      // [3]: error word copied after each aap_step; two batch slots
     cudaEvent_t err_event = nullptr;
+    cudaEvent_t batch_ev[2] = {nullptr, nullptr};   // error words taken every kAdaptSteps steps
+    int batch_prev = -1;            // slot of the newest copy not yet read (-1: none)
+    int batch_slot = 0;             // slot of the next copy
+    long long since_copy = 0;       // steps queued since the last copy
     bool err_pending = false;
     int relayouts = 0;
     // ensemble membership: steps are launched by the ensemble for all members
@@ -139,6 +143,10 @@ void free_all(aap_handle *h)
     h->events.clear();
     if (h->err_event) cudaEventDestroy(h->err_event);
     h->err_event = nullptr;
+    for (cudaEvent_t &e : h->batch_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
     if (h->pinned_err) cudaFreeHost(h->pinned_err);
     h->pinned_err = nullptr;
     for (void *p : h->allocs) cudaFree(p);
@@ -245,6 +253,19 @@ void layout_regions(Sys &S, double mu, double factor)
         off += cap;
     }
     S.tile_slots = aapk::round_up(off, 4);
+}
+
+// Whether regions sized by `factor` keep a tile's staged set (own slots, the
+// facing halo regions, the spill matches) within the 16-bit staged indices.
+bool capacity_fits(const aap_handle *h, double factor)
+{
+    if (h->p.kn > 0) return true;
+    Sys S = h->hs;
+    layout_regions(S, (double)h->p.n / ((double)S.ncx * S.ncy), factor);
+    const long long spill_cap = std::max<long long>(4096, h->p.n / 8);
+    const long long own = S.tile_slots;
+    const long long halo = 2 * (2 * S.cap[0] + S.cap[1]) + 2 * (2 * S.cap[0] + S.cap[3]) + 4 * S.cap[0];
+    return own + halo + std::min<long long>(16384, 4 * spill_cap) <= 65472;
 }
 
 // Region capacities, spill list, staging capacities and launch shapes for a
@@ -533,6 +554,9 @@ int free_regions(aap_handle *h)
 int clear_buffers(aap_handle *h)
 {
     Sys &S = h->hs;
+    h->batch_prev = -1;
+    h->batch_slot = 0;
+    h->since_copy = 0;
     for (int b = 0; b < 2; ++b)
         AAP_CK(cudaMemsetAsync(S.cnt[b], 0, (size_t)S.ntiles * aapk::kCntStride * sizeof(int), h->stream));
     AAP_CK(cudaMemsetAsync(S.spill_cnt, 0, 2 * sizeof(int), h->stream));
@@ -588,8 +612,9 @@ int alloc_all(aap_handle *h)
     }
     if ((rc = dev_alloc(h, &h->d_obs, 8 * sizeof(unsigned long long)))) return rc;
     if ((rc = dev_alloc(h, &h->d_seen, sizeof(int)))) return rc;
-    AAP_CK(cudaMallocHost(&h->pinned_err, sizeof(int)));
+    AAP_CK(cudaMallocHost(&h->pinned_err, 3 * sizeof(int)));
     AAP_CK(cudaEventCreateWithFlags(&h->err_event, cudaEventDisableTiming));
+    for (cudaEvent_t &e : h->batch_ev) AAP_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if ((rc = clear_buffers(h))) return rc;
     AAP_CK(cudaMemsetAsync(S.last, 0, 4 * sizeof(double), h->stream));
     AAP_CK(cudaMemsetAsync(S.stats, 0, 16 * sizeof(double), h->stream));
@@ -685,6 +710,45 @@ int launch_steps(const LaunchCfg &L, cudaStream_t st, long long nsteps, cudaStre
     return AAP_OK;
 }
 
+int run_steps(aap_handle *h, long long nsteps);
+int act_on_error(aap_handle *h, int err, bool *relaid);
+
+// Steps between capacity checks inside one long call.
+constexpr long long kAdaptSteps = 128;
+
+// nsteps steps, with the device error word copied to the host after every
+// kAdaptSteps steps (counted across calls).  When a copy is taken the host
+// waits for the one before it (kAdaptSteps older, so the GPU still has that
+// many steps queued) and reads it: regions overflowed by growing clusters are
+// then re-laid out within a long call, or within a loop of short calls,
+// before the spill list that absorbs the overflow fills up (and every tile
+// scans it meanwhile).  A re-layout keeps the state bit for bit.
+int run_steps_adaptive(aap_handle *h, long long nsteps)
+{
+    int rc;
+    long long left = nsteps;
+    while (left > 0) {
+        const long long k = std::min(left, kAdaptSteps - h->since_copy);
+        if ((rc = run_steps(h, k))) return rc;
+        left -= k;
+        h->since_copy += k;
+        if (h->since_copy < kAdaptSteps) continue;
+        h->since_copy = 0;
+        const int slot = h->batch_slot;
+        AAP_CK(cudaMemcpyAsync(h->pinned_err + 1 + slot, h->hs.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        AAP_CK(cudaEventRecord(h->batch_ev[slot], h->stream));
+        h->batch_slot ^= 1;
+        const int prev = h->batch_prev;
+        h->batch_prev = slot;
+        if (prev >= 0) {
+            AAP_CK(cudaEventSynchronize(h->batch_ev[prev]));
+            // a re-layout resets the copies (the newer one predates it)
+            if ((rc = act_on_error(h, h->pinned_err[1 + prev], nullptr))) return rc;
+        }
+    }
+    return AAP_OK;
+}
+
 int run_steps(aap_handle *h, long long nsteps)
 {
     if (!h->timing) {
@@ -742,7 +806,9 @@ int reinsert(aap_handle *h, double factor, int mode)
         AAP_CK(cudaMemcpyAsync(&err, h->hs.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         AAP_CK(cudaStreamSynchronize(h->stream));
         const bool spilled = err & (aapk::ERR_SPILL | aapk::ERR_LOST);
-        if (!spilled || (h->p.capacity > 0 && !(err & aapk::ERR_LOST))) {
+        // spilled particles are kept exactly: accepted with an explicit
+        // capacity, or when doubling the regions would exceed the staged indices
+        if (!spilled || (!(err & aapk::ERR_LOST) && (h->p.capacity > 0 || !capacity_fits(h, factor * 2.0)))) {
             h->factor = factor;
             return AAP_OK;
         }
@@ -773,6 +839,28 @@ int relayout(aap_handle *h, double factor)
     return reinsert(h, factor, 0);
 }
 
+// React to an error word copied from the device: lost particles make the
+// handle unusable; spilled ones (an automatic capacity) grow the regions, and
+// *relaid (if given) reports that.
+int act_on_error(aap_handle *h, int err, bool *relaid)
+{
+    if (err & aapk::ERR_SPILL) h->flags |= AAP_FLAG_SPILLED;
+    if (err & (aapk::ERR_LOST | aapk::ERR_STAGE)) {
+        h->broken = true;
+        return fail(AAP_EOVERFLOW, "particles were lost: a tile overflowed its spill capacity");
+    }
+    if ((err & aapk::ERR_SPILL) && h->p.capacity == 0) {
+        // grow by 1.5, or by as much as the staged indices allow; at the limit
+        // the overflow stays in the spill list (exact, only slower)
+        double f = h->factor * 1.5;
+        for (int k = 0; k < 8 && !capacity_fits(h, f); ++k) f = 0.5 * (f + h->factor);
+        if (f < h->factor * 1.05 || !capacity_fits(h, f)) return AAP_OK;
+        if (relaid) *relaid = true;
+        return relayout(h, f);
+    }
+    return AAP_OK;
+}
+
 // At the start of aap_step: look at the error word copied after the previous
 // batch (without waiting); grow the regions if particles spilled.
 int poll_capacity(aap_handle *h)
@@ -782,14 +870,7 @@ int poll_capacity(aap_handle *h)
     if (q == cudaErrorNotReady) return AAP_OK;
     if (q != cudaSuccess) return fail(AAP_ECUDA, std::string("error event: ") + cudaGetErrorString(q));
     h->err_pending = false;
-    const int err = *h->pinned_err;
-    if (err & aapk::ERR_SPILL) h->flags |= AAP_FLAG_SPILLED;
-    if (err & (aapk::ERR_LOST | aapk::ERR_STAGE)) {
-        h->broken = true;
-        return fail(AAP_EOVERFLOW, "particles were lost: a tile overflowed its spill capacity");
-    }
-    if ((err & aapk::ERR_SPILL) && h->p.capacity == 0) return relayout(h, h->factor * 1.5);
-    return AAP_OK;
+    return act_on_error(h, *h->pinned_err, nullptr);
 }
 
 
@@ -1138,7 +1219,7 @@ int aap_step(aap_handle *h, int64_t nsteps)
     if (h->broken) return fail(AAP_ESTATE, "handle is unusable after an earlier fault");
     int rc = poll_capacity(h);
     if (rc) return rc;
-    if ((rc = run_steps(h, nsteps))) return rc;
+    if ((rc = run_steps_adaptive(h, nsteps))) return rc;
     AAP_CK(cudaMemcpyAsync(h->pinned_err, h->hs.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     AAP_CK(cudaEventRecord(h->err_event, h->stream));
     h->err_pending = true;
@@ -1208,7 +1289,7 @@ int aap_phi_trace(aap_handle *h, int64_t nsteps, double *phi_out)
     h->hs.trace_base = h->step;
     h->hs.trace_cap = nsteps + 1;
     if ((rc = push_sys(h))) return rc;
-    if ((rc = run_steps(h, nsteps))) return rc;
+    if ((rc = run_steps_adaptive(h, nsteps))) return rc;
     AAP_CK(cudaMemcpyAsync(phi_out + 1, h->d_trace + 1, (size_t)nsteps * sizeof(double),
                            cudaMemcpyDeviceToHost, h->stream));
     h->hs.trace = nullptr;

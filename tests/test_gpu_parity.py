@@ -203,6 +203,27 @@ def test_handles_of_different_staging_sizes_coexist(lib):
         A.aap_destroy(h2)
 
 
+def test_long_call_grows_regions_within_the_call(lib):
+    """Clustering (low noise) overflows the tile regions: one long aap_step
+    call re-lays them out between its batches, and its trajectory equals the
+    one of many short calls bit for bit."""
+    p = params(n=1 << 18, lx=362.0, ly=362.0, eta=0.1, v=0.5, seed=61)
+    h1, h2 = A.aap_create(p), A.aap_create(p)
+    try:
+        slots0 = A.aap_get_layout(h1).tile_slots
+        A.aap_step(h1, 1536)
+        A.aap_sync(h1)
+        assert A.aap_get_layout(h1).tile_slots > slots0          # grown inside the one call
+        assert A.aap_observe(h1).flags & A.AAP_FLAG_SPILLED
+        for _ in range(12):
+            A.aap_step(h2, 128)
+        for u, v in zip(A.aap_get_state(h1, p.n), A.aap_get_state(h2, p.n)):
+            assert np.array_equal(u, v)
+    finally:
+        A.aap_destroy(h1)
+        A.aap_destroy(h2)
+
+
 def test_translation_by_whole_tiles_bitwise(lib):
     """Periodic box, shift every particle by whole tiles: the trajectory is the
     shifted trajectory bit for bit (the noise is keyed on id, not position)."""
