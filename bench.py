@@ -514,6 +514,10 @@ def main():
     px = torch.from_numpy(xs).pin_memory().numpy()
     py = torch.from_numpy(ys).pin_memory().numpy()
     pt = torch.from_numpy(ts).pin_memory().numpy()
+    # page-locked host buffers for the state read back at the end
+    ox = torch.empty(args.n, dtype=torch.float64).pin_memory().numpy()
+    oy = torch.empty(args.n, dtype=torch.float64).pin_memory().numpy()
+    ot = torch.empty(args.n, dtype=torch.float32).pin_memory().numpy()
     ke = args.e2e_steps
     torch.cuda.synchronize()
     if dist:
@@ -521,7 +525,7 @@ def main():
     t0 = time.perf_counter()
     A.aap_set_state(h, px, py, pt, step=obs.step)
     phi = A.aap_phi_trace(h, ke)
-    xs2, ys2, ts2 = A.aap_get_state(h, args.n)
+    xs2, ys2, ts2 = A.aap_get_state(h, args.n, out=(ox, oy, ot))
     e2e_s = time.perf_counter() - t0
     e2e_val, _ = replica_throughput(e2e_s * 1e3, args.n * ke, world, dist, "cuda")
     state_bytes = args.n * (8 + 8 + 4)

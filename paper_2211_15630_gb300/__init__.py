@@ -259,8 +259,17 @@ def aap_phi_trace(h, nsteps: int) -> np.ndarray:
     return out
 
 
-def aap_get_state(h, n: int):
-    x = np.zeros(n, np.float64); y = np.zeros(n, np.float64); th = np.zeros(n, np.float32)
+def aap_get_state(h, n: int, out=None):
+    """State by particle id; out = (x, y, theta) writes into caller arrays
+    (float64, float64, float32, contiguous; page-locked ones copy fastest)."""
+    if out is None:
+        x = np.zeros(n, np.float64); y = np.zeros(n, np.float64); th = np.zeros(n, np.float32)
+    else:
+        x, y, th = out
+        if (x.dtype != np.float64 or y.dtype != np.float64 or th.dtype != np.float32 or
+                not (x.flags.c_contiguous and y.flags.c_contiguous and th.flags.c_contiguous) or
+                min(x.size, y.size, th.size) < n):
+            raise ValueError("out must be contiguous float64, float64, float32 arrays of at least n elements")
     _check(load().aap_get_state(h, _p(x), _p(y), _p(th), int(n)))
     return x, y, th
 

@@ -70,6 +70,7 @@ struct aap_handle {
     unsigned char *d_scratch = nullptr;
     unsigned long long *d_obs = nullptr;
     int *d_seen = nullptr;
+    unsigned long long *d_bad = nullptr;     // [2] first invalid position / orientation of aap_set_state
     double *d_trace = nullptr, *d_trace_nbar = nullptr;
     long long trace_alloc = 0;
     int *d_nbr = nullptr;
@@ -796,9 +797,38 @@ int reinsert(aap_handle *h, double factor, int mode)
 {
     int rc;
     for (int attempt = 0; attempt < 12; ++attempt) {
-        if ((rc = free_regions(h))) return rc;
-        if ((rc = set_capacity(h, factor))) return rc;
-        if ((rc = alloc_regions(h))) return rc;
+        // new layout; the buffers are kept when their sizes do not change
+        // (aap_set_state, aap_load at the same capacity), else replaced
+        const Sys old_s = h->hs;
+        const LaunchCfg old_l = h->L;
+        if ((rc = set_capacity(h, factor))) {
+            h->hs = old_s;
+            h->L = old_l;
+            return rc;
+        }
+        const bool same = old_s.rec[0] && region_bytes(old_s) == region_bytes(h->hs) &&
+                          old_s.spill_cap == h->hs.spill_cap &&
+                          (h->member || old_l.scratch_per_block * old_l.grid_step ==
+                                            h->L.scratch_per_block * h->L.grid_step);
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        if (!same) {
+            Sys new_s = h->hs;
+            LaunchCfg new_l = h->L;
+            h->hs = old_s;
+            h->L = old_l;
+            if ((rc = free_regions(h))) return rc;      // the old buffers, with their sizes
+            for (int b = 0; b < 2; ++b) {
+                new_s.rec[b] = nullptr;
+                new_s.spill_rec[b] = nullptr;
+                new_s.spill_key[b] = nullptr;
+            }
+            h->hs = new_s;
+            h->L = new_l;
+            if ((rc = alloc_regions(h))) return rc;
+        }
         if ((rc = clear_buffers(h))) return rc;
         if ((rc = push_sys(h))) return rc;
         AAP_CK(aapk::launch_insert(h->hs, (int)(h->step & 1), h->d_x, h->d_y, h->d_th, mode, h->stream));
@@ -1332,27 +1362,34 @@ int aap_set_state(aap_handle *h, const double *x, const double *y, const float *
     if (!h || (n > 0 && (!x || !y || !theta))) return fail(AAP_EINVAL, "NULL argument");
     if (n != h->p.n) return fail(AAP_EINVAL, "n must equal the particle number");
     if (step < 0) return fail(AAP_EINVAL, "step < 0");
-    for (int64_t i = 0; i < n; ++i) {
-        if (!(x[i] >= 0.0 && x[i] <= h->p.lx) || !(y[i] >= 0.0 && y[i] <= h->p.ly))
-            return fail(AAP_EINVAL, "position " + std::to_string(i) + " outside the box");
-        if (!std::isfinite(theta[i])) return fail(AAP_EINVAL, "non-finite orientation " + std::to_string(i));
-    }
     int rc = ensure_xfer(h);
     if (rc) return rc;
+    if (!h->d_bad && (rc = dev_alloc(h, &h->d_bad, 2 * sizeof(unsigned long long)))) return rc;
     AAP_CK(cudaStreamSynchronize(h->stream));
     h->err_pending = false;
-    Ctl c{};
-    c.step = step;
-    AAP_CK(cudaMemcpyAsync(h->d_ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+    // copy in, then check every value on the device (the state and step are
+    // untouched until the check has passed)
     if (n > 0) {
         AAP_CK(cudaMemcpyAsync(h->d_x, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         AAP_CK(cudaMemcpyAsync(h->d_y, y, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         AAP_CK(cudaMemcpyAsync(h->d_th, theta, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     }
+    AAP_CK(aapk::launch_validate(h->d_x, h->d_y, h->d_th, n, h->p.lx, h->p.ly, h->d_bad, h->stream));
+    unsigned long long bad[2];
+    AAP_CK(cudaMemcpyAsync(bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
+    AAP_CK(cudaStreamSynchronize(h->stream));
+    if (bad[0] != ~0ull && bad[0] <= bad[1])
+        return fail(AAP_EINVAL, "position " + std::to_string(bad[0]) + " outside the box");
+    if (bad[1] != ~0ull) return fail(AAP_EINVAL, "non-finite orientation " + std::to_string(bad[1]));
+    Ctl c{};
+    c.step = step;
+    AAP_CK(cudaMemcpyAsync(h->d_ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
     h->step = step;
     h->flags = 0;
     h->broken = false;
-    if ((rc = reinsert(h, h->p.capacity > 0 ? h->p.capacity : 4.0, 0))) return rc;
+    // an automatic capacity keeps the size it has grown to (a restored state
+    // of the same system needs it again; the re-insert doubles it if not)
+    if ((rc = reinsert(h, h->p.capacity > 0 ? h->p.capacity : h->factor, 0))) return rc;
     return read_errors(h);
 }
 

@@ -851,6 +851,17 @@ __global__ void k_insert(Sys S, int b, const double *x, const double *y, const f
 
 // Visit every stored record of buffer b: slots [0, tiles * tile_slots) then
 // the spill list.  Returns false for empty slots.
+// The lowest index whose position lies outside [0, lx] x [0, ly] (bad[0])
+// and whose orientation is not finite (bad[1]); both start at all ones.
+__global__ void k_validate_state(const double *x, const double *y, const float *th, long long n, double lx,
+                                 double ly, unsigned long long *bad)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (!(x[i] >= 0.0 && x[i] <= lx) || !(y[i] >= 0.0 && y[i] <= ly)) atomicMin(bad, (unsigned long long)i);
+        if (!isfinite(th[i])) atomicMin(bad + 1, (unsigned long long)i);
+    }
+}
+
 __device__ __forceinline__ bool fetch_record(const Sys &S, int b, long long g, int4 &r, int &tile)
 {
     const long long nslot = (long long)S.ntiles * S.tile_slots;
@@ -1026,6 +1037,15 @@ cudaError_t launch_insert(const Sys &S, int b, const double *x, const double *y,
     const int bs = 256;
     const long long grid = (n + bs - 1) / bs;
     k_insert<<<(unsigned)grid, bs, 0, st>>>(S, b, x, y, th, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const double *x, const double *y, const float *th, long long n, double lx, double ly,
+                            unsigned long long *bad, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(bad, 0xff, 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess || n == 0) return e;
+    k_validate_state<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(x, y, th, n, lx, ly, bad);
     return cudaGetLastError();
 }
 

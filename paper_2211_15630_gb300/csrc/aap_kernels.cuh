@@ -47,6 +47,10 @@ cudaError_t launch_mf_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev)
 
 cudaError_t launch_insert(const Sys &S, int b, const double *x, const double *y, const float *th,
                           int mode, cudaStream_t st);
+// bad[0]: the lowest index with a position outside [0, lx] x [0, ly]; bad[1]:
+// the lowest with a non-finite orientation; ~0 where there is none.
+cudaError_t launch_validate(const double *x, const double *y, const float *th, long long n, double lx, double ly,
+                            unsigned long long *bad, cudaStream_t st);
 cudaError_t launch_gather(const Sys &S, int b, double *x, double *y, float *th, int *seen,
                           cudaStream_t st);
 cudaError_t launch_observe(const Sys &S, int b, unsigned long long *out, cudaStream_t st);

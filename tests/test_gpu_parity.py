@@ -295,6 +295,34 @@ def test_full_size_sampled(lib, oracle):
         A.aap_destroy(h)
 
 
+def test_set_state_rejects_invalid_values_and_keeps_the_state(lib):
+    """Positions outside the box and non-finite orientations are found on the
+    device; the lowest offending index is named and the state stays as it was."""
+    p = params(n=50000, lx=160.0, ly=160.0, seed=43)
+    h = A.aap_create(p)
+    try:
+        A.aap_step(h, 3)
+        before = A.aap_get_state(h, p.n)
+        step = A.aap_observe(h).step
+        x, y, th = (a.copy() for a in before)
+        x[31337] = p.lx + 0.5
+        th[777] = np.nan
+        with pytest.raises(A.AapError) as e:
+            A.aap_set_state(h, x, y, th, step=0)
+        assert e.value.code == A.AAP_EINVAL and "orientation 777" in str(e.value)
+        th[777] = 0.25
+        with pytest.raises(A.AapError) as e:
+            A.aap_set_state(h, x, y, th, step=0)
+        assert e.value.code == A.AAP_EINVAL and "position 31337" in str(e.value)
+        assert A.aap_observe(h).step == step
+        for u, v in zip(A.aap_get_state(h, p.n), before):
+            assert np.array_equal(u, v)
+        A.aap_step(h, 2)
+        assert np.isfinite(A.aap_observe(h).phi)
+    finally:
+        A.aap_destroy(h)
+
+
 def test_invalid_parameters_rejected(lib):
     for kw in [dict(lx=2.5), dict(n=-1), dict(v=1.5), dict(model=7), dict(eta=float("nan")),
                dict(model=A.AAP_LANGEVIN, dt=0.0), dict(threads=100), dict(tile_w=3)]:
