@@ -984,8 +984,12 @@ struct aap_ens {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
     int policy = 0;
-    int *pinned_err = nullptr;
+    int *pinned_err = nullptr;      // [3][count]: after each aap_ens_step; two batch slots
     cudaEvent_t err_event = nullptr;
+    cudaEvent_t batch_ev[2] = {nullptr, nullptr};   // error words taken every kAdaptSteps steps
+    int batch_prev = -1;
+    int batch_slot = 0;
+    long long since_copy = 0;
     bool err_pending = false;
 };
 
@@ -1090,6 +1094,9 @@ int ens_combine(aap_ens *e)
 int ens_build(aap_ens *e, int pol)
 {
     e->policy = pol;
+    e->batch_prev = -1;
+    e->batch_slot = 0;
+    e->since_copy = 0;
     const int count = (int)e->params.size();
     if (cudaMalloc(&e->d_sys, (size_t)count * sizeof(Sys)) != cudaSuccess ||
         cudaMalloc(&e->d_tile_base, (size_t)(count + 1) * sizeof(int)) != cudaSuccess ||
@@ -1121,6 +1128,29 @@ int ens_build(aap_ens *e, int pol)
     return ens_combine(e);
 }
 
+// React to the replicas' error words: lost particles fail the call; spilled
+// ones (an automatic capacity) grow that replica's regions (as far as the
+// staged indices allow), after which the ensemble's launch is rebuilt.
+int ens_act(aap_ens *e, const int *words)
+{
+    bool regrow = false;
+    for (size_t r = 0; r < e->m.size(); ++r) {
+        aap_handle *h = e->m[r];
+        const int err = words[r];
+        if (err & (aapk::ERR_LOST | aapk::ERR_STAGE))
+            return fail(AAP_EOVERFLOW, "replica " + std::to_string(r) + " lost particles");
+        bool relaid = false;
+        int rc = act_on_error(h, err, &relaid);
+        if (rc) return rc;
+        regrow = regrow || relaid;
+    }
+    if (!regrow) return AAP_OK;
+    e->batch_prev = -1;             // the copies in flight predate the re-layout
+    e->batch_slot = 0;
+    e->since_copy = 0;
+    return ens_combine(e);
+}
+
 int ens_poll(aap_ens *e)
 {
     if (!e->err_pending) return AAP_OK;
@@ -1128,20 +1158,7 @@ int ens_poll(aap_ens *e)
     if (q == cudaErrorNotReady) return AAP_OK;
     if (q != cudaSuccess) return fail(AAP_ECUDA, std::string("error event: ") + cudaGetErrorString(q));
     e->err_pending = false;
-    bool regrow = false;
-    for (size_t r = 0; r < e->m.size(); ++r) {
-        aap_handle *h = e->m[r];
-        const int err = e->pinned_err[r];
-        if (err & aapk::ERR_SPILL) h->flags |= AAP_FLAG_SPILLED;
-        if (err & (aapk::ERR_LOST | aapk::ERR_STAGE))
-            return fail(AAP_EOVERFLOW, "replica " + std::to_string(r) + " lost particles");
-        if ((err & aapk::ERR_SPILL) && h->p.capacity == 0) {
-            int rc = relayout(h, h->factor * 1.5);
-            if (rc) return rc;
-            regrow = true;
-        }
-    }
-    return regrow ? ens_combine(e) : AAP_OK;
+    return ens_act(e, e->pinned_err);
 }
 
 }  // namespace
@@ -1597,8 +1614,10 @@ int aap_ens_create(const aap_params *params, int32_t count, void *stream, aap_en
     e->stream = static_cast<cudaStream_t>(stream);
     int rc = ens_build(e, 0);
     if (rc == AAP_OK) {
-        if (cudaMallocHost(&e->pinned_err, (size_t)count * sizeof(int)) != cudaSuccess ||
-            cudaEventCreateWithFlags(&e->err_event, cudaEventDisableTiming) != cudaSuccess) {
+        if (cudaMallocHost(&e->pinned_err, (size_t)3 * count * sizeof(int)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e->err_event, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e->batch_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e->batch_ev[1], cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             rc = fail(AAP_ECUDA, "ensemble host buffers");
         }
@@ -1606,6 +1625,9 @@ int aap_ens_create(const aap_params *params, int32_t count, void *stream, aap_en
     if (rc) {
         ens_free(e);
         if (e->pinned_err) cudaFreeHost(e->pinned_err);
+        for (cudaEvent_t ev : e->batch_ev)
+            if (ev) cudaEventDestroy(ev);
+        if (e->err_event) cudaEventDestroy(e->err_event);
         delete e;
         return rc;
     }
@@ -1620,6 +1642,8 @@ int aap_ens_destroy(aap_ens *e)
     ens_free(e);
     if (e->cap) cudaStreamDestroy(e->cap);
     if (e->err_event) cudaEventDestroy(e->err_event);
+    for (cudaEvent_t ev : e->batch_ev)
+        if (ev) cudaEventDestroy(ev);
     if (e->pinned_err) cudaFreeHost(e->pinned_err);
     delete e;
     return AAP_OK;
@@ -1632,9 +1656,32 @@ int aap_ens_step(aap_ens *e, int64_t nsteps)
     if (nsteps < 0) return fail(AAP_EINVAL, "nsteps < 0");
     int rc = ens_poll(e);
     if (rc) return rc;
-    if ((rc = launch_steps(e->L, e->stream, nsteps, e->cap, e->exec))) return rc;
-    e->step += nsteps;
-    for (aap_handle *h : e->m) h->step += nsteps;
+    // in pieces, with every replica's error word copied every kAdaptSteps
+    // steps and the copy before it read (as run_steps_adaptive does)
+    const size_t count = e->m.size();
+    long long left = nsteps;
+    while (left > 0) {
+        const long long k = std::min(left, kAdaptSteps - e->since_copy);
+        if ((rc = launch_steps(e->L, e->stream, k, e->cap, e->exec))) return rc;
+        e->step += k;
+        for (aap_handle *h : e->m) h->step += k;
+        left -= k;
+        e->since_copy += k;
+        if (e->since_copy < kAdaptSteps) continue;
+        e->since_copy = 0;
+        const int slot = e->batch_slot;
+        for (size_t r = 0; r < count; ++r)
+            AAP_CK(cudaMemcpyAsync(e->pinned_err + (1 + slot) * count + r, e->m[r]->hs.err, sizeof(int),
+                                   cudaMemcpyDeviceToHost, e->stream));
+        AAP_CK(cudaEventRecord(e->batch_ev[slot], e->stream));
+        e->batch_slot ^= 1;
+        const int prev = e->batch_prev;
+        e->batch_prev = slot;
+        if (prev >= 0) {
+            AAP_CK(cudaEventSynchronize(e->batch_ev[prev]));
+            if ((rc = ens_act(e, e->pinned_err + (1 + prev) * count))) return rc;
+        }
+    }
     for (size_t r = 0; r < e->m.size(); ++r)
         AAP_CK(cudaMemcpyAsync(e->pinned_err + r, e->m[r]->hs.err, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
     AAP_CK(cudaEventRecord(e->err_event, e->stream));
