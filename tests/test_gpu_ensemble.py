@@ -43,6 +43,35 @@ def test_graph_replay_equals_single_steps(lib):
         A.aap_destroy(h2)
 
 
+def test_ensemble_grows_replica_regions_within_a_call(lib):
+    """Low-noise replicas cluster and overflow their regions during one long
+    aap_ens_step call: the ensemble re-lays them out between its batches
+    (the replica's slots grow) and still follows the standalone trajectories
+    bit for bit."""
+    ps = []
+    for r in range(4):
+        q = params(n=1 << 16, lx=181.0, ly=181.0, eta=0.1 + 0.05 * r, v=0.5, seed=300 + r)
+        q.tile_w, q.tile_h = 32, 16
+        ps.append(q)
+    e = A.aap_ens_create(ps)
+    try:
+        slots0 = [A.aap_ens_get_layout(e, r).tile_slots for r in range(4)]
+        A.aap_ens_step(e, 1024)          # re-layouts happen on the host inside this call
+        grown = [A.aap_ens_get_layout(e, r).tile_slots > slots0[r] for r in range(4)]
+        assert any(grown)
+        for r in range(4):
+            q = _standalone_like(e, r, ps[r])
+            h = A.aap_create(q)
+            try:
+                A.aap_step(h, 1024)
+                for u, v in zip(A.aap_get_state(h, q.n), A.aap_ens_get_state(e, r, q.n)):
+                    assert np.array_equal(u, v)
+            finally:
+                A.aap_destroy(h)
+    finally:
+        A.aap_ens_destroy(e)
+
+
 def test_ensemble_replicas_bitwise_equal_standalone(lib):
     """Every replica of the batched launch follows the standalone trajectory
     bit for bit (same parameters, same tile shape)."""
