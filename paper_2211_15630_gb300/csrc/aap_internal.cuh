@@ -143,9 +143,8 @@ struct Seg {
 // the block's slice of global scratch for tiles that do not fit.
 struct Stage {
     float4 *P;                  // in cell order: x, y rel. tile centre, then cos, sin as int32 in units of 2^-22
-    int *rX, *rY;               // staged, in the tile's extended frame (fixed point)
-    float *rth;                 // orientation
-    unsigned *id;
+    int4 *R;                    // staged record: X, Y in the tile's extended frame (fixed
+                                // point), orientation bits, id
     unsigned short *cell;       // extended cell | flip << 14
     unsigned short *slot;       // rank of arrival in the cell
     unsigned short *gidx;       // species by sorted position (several species only)
@@ -165,10 +164,7 @@ __host__ __device__ inline void carve_stage(Stage &st, unsigned char *p, int cap
 {
     st.cap = cap;
     st.P = (float4 *)p;               p += (size_t)cap * 16;
-    st.rX = (int *)p;                 p += (size_t)cap * 4;
-    st.rY = (int *)p;                 p += (size_t)cap * 4;
-    st.rth = (float *)p;              p += (size_t)cap * 4;
-    st.id = (unsigned *)p;            p += (size_t)cap * 4;
+    st.R = (int4 *)p;                 p += (size_t)cap * 16;
     st.cell = (unsigned short *)p;    p += (size_t)cap * 2;
     st.slot = (unsigned short *)p;    p += (size_t)cap * 2;
     st.gidx = (unsigned short *)p;    p += (size_t)cap * 2;

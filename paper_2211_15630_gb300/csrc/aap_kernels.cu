@@ -382,10 +382,7 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             ey = min(max(ey, 0), H2 - 1);
         }
         const int ec = ey * W2 + ex;
-        A.rX[k] = (int)(g.ax * (long long)r.x + g.bx);
-        A.rY[k] = (int)(g.ay * (long long)r.y + g.by);
-        A.rth[k] = __int_as_float(r.z);
-        A.id[k] = (unsigned)r.w;
+        A.R[k] = make_int4((int)(g.ax * (long long)r.x + g.bx), (int)(g.ay * (long long)r.y + g.by), r.z, r.w);
         A.cell[k] = (unsigned short)(ec | (g.flip << 14));
         A.slot[k] = (unsigned short)atomicAdd(&tb.hist[ec], 1);
     }
@@ -427,7 +424,8 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
         const unsigned short cf = A.cell[k];
         const int c = cf & 0x3fff;
         const int q = tb.cstart[c] + A.slot[k];
-        float thv = A.rth[k];
+        const int4 rk = A.R[k];
+        float thv = __int_as_float(rk.z);
         float sn, cs;
         if (MODEL == 1 && S.order != 1) {
             thv *= (float)S.order;
@@ -441,10 +439,10 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             if (MODEL != 1 || (S.order & 1)) cs = -cs; else sn = -sn;
         }
         if (flip & 2) sn = -sn;
-        A.P[q] = make_float4((float)(A.rX[k] - xc) * S.ux, (float)(A.rY[k] - yc) * S.uy,
+        A.P[q] = make_float4((float)(rk.x - xc) * S.ux, (float)(rk.y - yc) * S.uy,
                              __int_as_float(__float2int_rn(cs * kFixNbF)), __int_as_float(__float2int_rn(sn * kFixNbF)));
         A.sk[q] = (unsigned short)k;
-        if (S.nsp > 1) A.gidx[q] = (unsigned short)species_of(S, A.id[k]);   // species by sorted position
+        if (S.nsp > 1) A.gidx[q] = (unsigned short)species_of(S, (unsigned)rk.w);   // species by sorted position
     }
     if (warp == NT / 32 - 1) {
         int carry = 0;
@@ -485,9 +483,10 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             }
             const int q = tb.cstart[(rlo + 1) * W2 + 1] + (o - tb.rowpre[rlo]);
             const int k = A.sk[q];
-            const int X = A.rX[k], Y = A.rY[k];
-            const float thi = A.rth[k];
-            const unsigned id = A.id[k];
+            const int4 rk = A.R[k];
+            const int X = rk.x, Y = rk.y;
+            const float thi = __int_as_float(rk.z);
+            const unsigned id = (unsigned)rk.w;
             const int ec = A.cell[k] & 0x3fff;
             const float4 pi = A.P[q];
             float sc, ss;                    // neighbour sums in units of 2^-22
