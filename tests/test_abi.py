@@ -86,3 +86,19 @@ def test_load_rejects_missing_and_foreign_files(lib, tmp_path):
     with pytest.raises(A.AapError) as e:
         A.aap_load(str(trunc))
     assert e.value.code == A.AAP_EIO
+
+
+def test_get_state_out_buffers_checked_before_the_call():
+    """aap_get_state(h, n, out=...) rejects buffers of the wrong type or size
+    before anything reaches the library (so no handle or GPU is needed)."""
+    import numpy as np
+    import paper_2211_15630_gb300 as A
+
+    good = (np.zeros(4, np.float64), np.zeros(4, np.float64), np.zeros(4, np.float32))
+    for bad in ((np.zeros(4, np.float32),) + good[1:],            # x not float64
+                good[:2] + (np.zeros(4, np.float64),),            # theta not float32
+                (np.zeros(3, np.float64),) + good[1:],            # too short
+                (np.zeros(8, np.float64)[::2],) + good[1:]):      # not contiguous
+        with pytest.raises(ValueError):
+            A.aap_get_state(None, 4, out=bad)
+
