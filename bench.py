@@ -100,6 +100,76 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, by ctypes) every couple of milliseconds, so that a timed
+    region of a few tens of milliseconds still gets a dozen samples.  Reads
+    only; changes no setting.  start() returns False when NVML is not there
+    (the caller then falls back to the nvidia-smi sampler)."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid: str | None, index: int, period_s: float = 0.002):
+        self.uuid, self.index, self.period = uuid, index, period_s
+        self.lines = []
+        self.stop_flag = threading.Event()
+        self.t = None
+
+    def start(self) -> bool:
+        import ctypes as C
+
+        try:
+            nv = C.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return False
+            dev = C.c_void_p()
+            rc = 1
+            if self.uuid:
+                u = self.uuid if self.uuid.startswith("GPU-") else "GPU-" + self.uuid
+                rc = nv.nvmlDeviceGetHandleByUUID(u.encode(), C.byref(dev))
+            if rc != 0:
+                rc = nv.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.index), C.byref(dev))
+            if rc != 0:
+                return False
+            mx = C.c_uint(0)
+            nv.nvmlDeviceGetMaxClockInfo(dev, 1, C.byref(mx))          # NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        except (OSError, AttributeError):
+            return False
+        self.nv, self.dev, self.get_reasons = nv, dev, get_reasons
+
+        def run():
+            clk, rs = C.c_uint(0), C.c_ulonglong(0)
+            while not self.stop_flag.is_set():
+                if self.nv.nvmlDeviceGetClockInfo(self.dev, 1, C.byref(clk)) == 0 and \
+                        self.get_reasons(self.dev, C.byref(rs)) == 0:
+                    self.lines.append((time.perf_counter(), float(clk.value), int(rs.value)))
+                time.sleep(self.period)
+
+        self.t = threading.Thread(target=run, daemon=True)
+        self.t.start()
+        return True
+
+    def stop(self):
+        self.stop_flag.set()
+        if self.t:
+            self.t.join(timeout=5)
+
+    def summary(self, t0, t1):
+        sm, reasons = [], set()
+        for ts, mhz, bits in self.lines:
+            if t0 <= ts <= t1:
+                sm.append(mhz)
+                for b, name in self.REASONS.items():
+                    if bits & b:
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvml"}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -494,9 +564,15 @@ def main():
     lay = A.aap_get_layout(h)
     A.aap_step(h, args.warmup)
     A.aap_sync(h)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except (AttributeError, RuntimeError):
+        uuid = None
+    clocks = NvmlClockSampler(uuid, local)
+    if not clocks.start():
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
     A.aap_set_timing(h, True)
     t_begin = time.perf_counter()
     ms = timed(h, args.steps)

@@ -294,11 +294,17 @@ int aap_coarse_grain(aap_handle *h, int32_t nbx, int32_t nby, float *dev_out);
  * Same fields as aap_coarse_grain, from caller-owned DEVICE arrays x, y
  * (FP64, in [0,lx] x [0,ly]) and theta (FP32) of n particles, into the
  * caller-owned DEVICE buffer dev_out (3 * nbx * nby floats), on `stream`.
+ * Positions are not checked: a coordinate below 0 or NaN is counted in the
+ * first bin of its axis, one beyond the box in the last; a non-finite theta
+ * adds to the density but not to the polarisation.  lx and ly must be finite
+ * and positive (AAP_EINVAL otherwise).
  * The integer sums live in a fixed file-scope device array of 3 x 65,536
  * 64-bit words (1.5 MiB, held by every device that loads the library until
  * the process exits): nbx * nby must not exceed 65,536 (AAP_EINVAL
  * otherwise).  The first call on a device looks up that array's address
- * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * (cudaGetSymbolAddress), so make it before any stream capture; that address
+ * is kept until the process exits and does not survive cudaDeviceReset, after
+ * which the entry point must not be called on that device.  All calls
  * share the array, which keeps the last call's sums and is cleared at the
  * start of each call: calls whose work overlaps on the GPU (other streams or
  * threads) race; calls ordered on one stream are safe.  Calls no cudaMalloc

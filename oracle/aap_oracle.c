@@ -8,7 +8,7 @@
  *
  * Every routine follows the model statement of Kuersten, "Aligning Active
  * Particles Py Package" (CPC); the section or equation is cited at each one.
- * Readings taken where the paper is silent (each also listed in the design doc):
+ * Readings taken where the paper is silent:
  *   - a particle's own mirror image at a reflecting wall is a neighbour when
  *     it lies within R (self_image = 1; Sec. 2.4 gives every real particle
  *     image particles that interact "in the same way");

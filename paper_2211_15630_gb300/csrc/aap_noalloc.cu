@@ -15,8 +15,12 @@
 // device with cudaGetSymbolAddress, on the first call made on that device.
 // Every call shares the one array, so calls whose work overlaps on the GPU
 // (different streams, or different host threads) race; calls ordered on one
-// stream are safe.  The array is cleared at the start of each call.
+// stream are safe.  The array is cleared at the start of each call.  The
+// looked-up address is kept for the life of the process: it does not survive
+// cudaDeviceReset (or any other teardown of the device's primary context),
+// after which this entry point must not be called again on that device.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -49,18 +53,31 @@ __global__ void k_na_clear(unsigned long long *acc, long long n)
         acc[i] = 0ull;
 }
 
-// Same binning and the same exact integer sums as aap_coarse_grain.
+// Bin floor(u f) of one coordinate, clamped to [0, nb): a position below 0
+// or a NaN goes to bin 0, one at or beyond the far edge to bin nb - 1 (the
+// comparisons decide before any conversion, so no value is converted out of
+// the int range).
+__device__ __forceinline__ int na_bin(double u, double f, int nb)
+{
+    const double t = u * f;
+    if (!(t >= 0.0)) return 0;
+    if (t >= (double)nb) return nb - 1;
+    return min((int)t, nb - 1);
+}
+
+// Same binning and the same exact integer sums as aap_coarse_grain.  A
+// non-finite orientation adds to the count of its bin but nothing to the
+// polarisation sums.
 __global__ void k_na_accumulate(const double *__restrict__ x, const double *__restrict__ y,
                                 const float *__restrict__ th, long long n, double fx, double fy, int nbx, int nby,
                                 unsigned long long *acc)
 {
     const long long nb = (long long)nbx * nby;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int ix = min(max((int)(x[i] * fx), 0), nbx - 1);
-        const int iy = min(max((int)(y[i] * fy), 0), nby - 1);
-        const long long bin = (long long)iy * nbx + ix;
-        float sn, cs;
-        sincosf(th[i], &sn, &cs);
+        const long long bin = (long long)na_bin(y[i], fy, nby) * nbx + na_bin(x[i], fx, nbx);
+        const float t = th[i];
+        float sn = 0.f, cs = 0.f;
+        if (isfinite(t)) sincosf(t, &sn, &cs);
         atomicAdd(acc + bin, 1ull);
         atomicAdd(acc + nb + bin, (unsigned long long)__float2ll_rn(cs * 4294967296.0f));
         atomicAdd(acc + 2 * nb + bin, (unsigned long long)__float2ll_rn(sn * 4294967296.0f));
@@ -108,7 +125,8 @@ int aap_coarse_grain_noalloc(const double *x, const double *y, const float *thet
     g_na_err.clear();
     if (!dev_out || (n > 0 && (!x || !y || !theta))) return na_fail(AAP_EINVAL, "NULL argument");
     if (n < 0) return na_fail(AAP_EINVAL, "n < 0");
-    if (!(lx > 0) || !(ly > 0)) return na_fail(AAP_EINVAL, "lx and ly must be positive");
+    if (!std::isfinite(lx) || !std::isfinite(ly) || !(lx > 0) || !(ly > 0))
+        return na_fail(AAP_EINVAL, "lx and ly must be finite and positive");
     if (nbx < 1 || nby < 1) return na_fail(AAP_EINVAL, "nbx and nby must be >= 1");
     const long long nb = (long long)nbx * nby;
     if (nb > kNoAllocMaxBins)

@@ -236,8 +236,15 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ 
         const bool done = __syncthreads_and(mbar_wait(smem_addr(&s_bar[buf]), (uint32_t)(it >> 1) & 1u)) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!done) {
+            // Give-up path.  The MMAs of this buffer may still be running and
+            // writing its TMEM columns (reading s_in / s_w), so the block waits
+            // a second bounded time for that commit before it frees TMEM and
+            // exits; the other buffer's MMAs were already waited for.  Should
+            // the second wait also run out, the tensor core has stopped, and
+            // the block frees its columns all the same (nothing else can end).
             ok = false;
             if (tid == 0) atomicOr(&g_sur_err, 1);
+            mbar_wait(smem_addr(&s_bar[buf]), (uint32_t)(it >> 1) & 1u);
         } else {
             const int q = warp & 3, h = warp >> 2;
             uint32_t r[NH];

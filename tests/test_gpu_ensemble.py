@@ -5,6 +5,7 @@ import pytest
 
 import paper_2211_15630_gb300 as A
 from paper_2211_15630_gb300 import workloads as W
+from oracle import coarse as CG
 from tests.gpu_helpers import compare_one_step, oracle_model, params
 
 pytestmark = pytest.mark.gpu
@@ -185,11 +186,9 @@ def test_coarse_grain_conserves(lib, oracle):
         sn = np.sin(th.astype(np.float64)).sum()
         assert abs(f[1].sum() * area - cs) < 1e-3 * np.sqrt(p.n)
         assert abs(f[2].sum() * area - sn) < 1e-3 * np.sqrt(p.n)
-        ix = np.minimum((x / (p.lx / 128)).astype(int), 127)
-        iy = np.minimum((y / (p.ly / 128)).astype(int), 127)
-        counts = np.zeros((128, 128))
-        np.add.at(counts, (iy, ix), 1.0)
-        assert np.array_equal(np.round(f[0] * area), counts)
+        assert np.array_equal(np.round(f[0] * area), CG.counts(x, y, p.lx, p.ly, 128, 128))
+        ref = CG.coarse_grain(x, y, th, p.lx, p.ly, 128, 128)
+        assert np.all(np.abs(f[1:] - ref[1:]) * area < 1e-6 * (np.round(ref[0] * area) + 1.0))
         phi_f = np.hypot(f[1].sum(), f[2].sum()) * area / p.n
         assert abs(phi_f - oracle.polar(th.astype(np.float64))) < 1e-6
     finally:
@@ -213,17 +212,11 @@ def test_coarse_grain_exact_bins_odd_geometry(lib, lx, ly, nbx, nby, bx):
         f = out.cpu().numpy().reshape(3, nby, nbx).astype(np.float64)
         area = (lx / nbx) * (ly / nby)
         x, y, th = A.aap_get_state(h, p.n)
-        ix = np.clip((x * (nbx / lx)).astype(np.int64), 0, nbx - 1)
-        iy = np.clip((y * (nby / ly)).astype(np.int64), 0, nby - 1)
-        counts = np.zeros((nby, nbx))
-        np.add.at(counts, (iy, ix), 1.0)
+        ref = CG.coarse_grain(x, y, th, lx, ly, nbx, nby)
+        counts = CG.counts(x, y, lx, ly, nbx, nby)
         assert np.array_equal(np.round(f[0] * area), counts)
-        cs = np.zeros((nby, nbx))
-        sn = np.zeros((nby, nbx))
-        np.add.at(cs, (iy, ix), np.cos(th.astype(np.float64)))
-        np.add.at(sn, (iy, ix), np.sin(th.astype(np.float64)))
         tol = 1e-6 * (counts + 1.0)
-        assert np.all(np.abs(f[1] * area - cs) < tol) and np.all(np.abs(f[2] * area - sn) < tol)
+        assert np.all(np.abs(f[1:] - ref[1:]) * area < tol)
     finally:
         A.aap_destroy(h)
 
@@ -246,15 +239,11 @@ def test_coarse_grain_with_spilled_records(lib):
         A.aap_sync(h)
         f = out.cpu().numpy().reshape(3, nb, nb).astype(np.float64)
         xs, ys, ts = A.aap_get_state(h, n)
-        ix = np.clip((xs * (nb / L)).astype(np.int64), 0, nb - 1)
-        iy = np.clip((ys * (nb / L)).astype(np.int64), 0, nb - 1)
-        counts = np.zeros((nb, nb))
-        np.add.at(counts, (iy, ix), 1.0)
+        counts = CG.counts(xs, ys, L, L, nb, nb)
         area = (L / nb) ** 2
         assert np.array_equal(np.round(f[0] * area), counts)
-        cs = np.zeros((nb, nb))
-        np.add.at(cs, (iy, ix), np.cos(ts.astype(np.float64)))
-        assert np.all(np.abs(f[1] * area - cs) < 1e-6 * (counts + 1.0))
+        ref = CG.coarse_grain(xs, ys, ts, L, L, nb, nb)
+        assert np.all(np.abs(f[1:] - ref[1:]) * area < 1e-6 * (counts + 1.0))
     finally:
         A.aap_destroy(h)
 

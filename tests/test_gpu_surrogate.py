@@ -107,6 +107,51 @@ def test_conv_backward_weight(lib, cin, cout, stride):
     assert torch.equal(dw, dw2)
 
 
+# The convolution runs persistent blocks (at most 4 per SM, 608 on a GB300)
+# over tiles of 16 x 8 pixels with two halo buffers, two TMEM accumulators and
+# two mbarriers whose wait parity flips every second tile of a block.  At
+# 128 x 128 and batch 20 there are 2560 tiles, so every block runs at least
+# four of them: both buffers and both parities of each mbarrier, the path
+# every full-size call of the surrogate (128 x 128 fields) takes.
+FULL_B, FULL_H, FULL_W = 20, 128, 128
+
+
+@pytest.mark.parametrize("cin,cout,relu", [(16, 32, 1), (32, 32, 1), (32, 8, 0)])
+def test_conv_forward_full_size(lib, cin, cout, relu):
+    g = np.random.default_rng(100 + cin + cout + relu)
+    B, H, W = FULL_B, FULL_H, FULL_W
+    assert (H // 16) * (W // 8) * B >= 4 * 608
+    x = S.bf16_round(g.normal(size=(B, H, W, cin)))
+    w = S.bf16_round(g.normal(size=(cout, 9, cin)) * 0.2)
+    b = g.normal(size=cout).astype(np.float32).astype(np.float64)
+    y = torch.zeros(B * H * W * cout, dtype=torch.int16, device="cuda")
+    xd, wd, bd = _dev_bf16(x), _dev_bf16(w.transpose(1, 0, 2)), _dev_f32(b)
+    A.aap_conv3x3_forward(xd.data_ptr(), B, H, W, cin, cout, wd.data_ptr(), bd.data_ptr(), relu, y.data_ptr())
+    torch.cuda.synchronize()
+    ref = S.conv_forward(x, w, b)
+    if relu:
+        ref = np.maximum(ref, 0)
+    _close_bf16(_host_bf16(y).reshape(ref.shape), ref)
+
+
+def test_conv_backward_data_full_size(lib):
+    cin, cout = 32, 32
+    g = np.random.default_rng(207)
+    B, H, W = FULL_B, FULL_H, FULL_W
+    dy = S.bf16_round(g.normal(size=(B, H, W, cout)))
+    w = S.bf16_round(g.normal(size=(cout, 9, cin)) * 0.2)
+    mask = S.bf16_round(g.normal(size=(B, H, W, cin)))
+    wt_t = np.zeros((9, cin, cout))
+    for tap in range(9):
+        wt_t[tap] = w[:, 8 - tap, :].T
+    dx = torch.zeros(B * H * W * cin, dtype=torch.int16, device="cuda")
+    dyd, wtd, md = _dev_bf16(dy), _dev_bf16(wt_t), _dev_bf16(mask)
+    A.aap_conv3x3_backward_data(dyd.data_ptr(), B, H, W, cin, cout, wtd.data_ptr(), md.data_ptr(), dx.data_ptr())
+    torch.cuda.synchronize()
+    ref = S.conv_backward_data(dy, w) * (mask > 0)
+    _close_bf16(_host_bf16(dx).reshape(ref.shape), ref)
+
+
 def _random_params(n, seed):
     g = np.random.default_rng(seed)
     layers = S.unpack(g.normal(size=n) * 0.1)
@@ -148,6 +193,65 @@ def test_network_loss_and_gradient(lib, conserve):
         p1 = A.aap_sur_get_params(s).astype(np.float64)
         e1, _, _ = S.adam(params.astype(np.float64), grad, np.zeros(n), np.zeros(n), 1)
         assert np.abs(p1 - e1).max() < 1e-6
+    finally:
+        A.aap_sur_destroy(s)
+
+
+def test_network_gradient_full_size(lib):
+    """One train step at the surrogate's own field size (128 x 128) and batch
+    20: every convolution of the forward and backward pass runs its blocks
+    over several tiles.  Loss and gradient against the oracle network."""
+    B, H, W = FULL_B, FULL_H, FULL_W
+    s = A.aap_sur_create(A.aap_sur_params_default(nbx=W, nby=H, max_batch=B))
+    try:
+        n = A.aap_sur_param_count(s)
+        params = _random_params(n, 41)
+        A.aap_sur_set_params(s, params)
+        g = np.random.default_rng(42)
+        fields = np.abs(g.normal(size=(B, 3, H, W))) + 1.0
+        fields[:, 1:] -= 1.5
+        target = fields + 0.2 * g.normal(size=fields.shape)
+        eta = g.uniform(0.3, 0.5, B)
+        fd, td, ed = _dev_f32(fields), _dev_f32(target), _dev_f32(eta)
+        loss = A.aap_sur_train_step(s, fd.data_ptr(), td.data_ptr(), ed.data_ptr(), B)
+        grad = A.aap_sur_get_grads(s).astype(np.float64)
+        st, x0 = S.normalise(fields.astype(np.float32), eta.astype(np.float32), 2.0, 0.4, 0.1)
+        tg, _ = S.normalise(target.astype(np.float32), eta.astype(np.float32), 2.0, 0.4, 0.1)
+        pw = S.pack([(S.bf16_round(w), b) for w, b in S.unpack(params.astype(np.float64))])
+        rloss, rgrad = S.loss_and_grad(pw, st, S.bf16_round(x0), tg, round_act=S.bf16_round)
+        assert abs(loss - rloss) <= 1e-2 * rloss
+        rel = np.linalg.norm(grad - rgrad) / np.linalg.norm(rgrad)
+        cos = grad @ rgrad / (np.linalg.norm(grad) * np.linalg.norm(rgrad))
+        assert rel < 3e-2 and cos > 0.999, (rel, cos)
+    finally:
+        A.aap_sur_destroy(s)
+
+
+def test_adam_over_several_steps(lib):
+    """Five train steps on one batch: after each, the parameters equal the
+    oracle's Adam recursion fed the library's own gradients, with the moments
+    carried over and the bias correction of step t (a one-step check cannot
+    tell a moment that restarts every step from one that is kept)."""
+    B, H, W = 2, 16, 32
+    s = A.aap_sur_create(A.aap_sur_params_default(nbx=W, nby=H, max_batch=B, lr=1e-3))
+    try:
+        n = A.aap_sur_param_count(s)
+        params = _random_params(n, 51)
+        A.aap_sur_set_params(s, params)
+        g = np.random.default_rng(52)
+        fields = np.abs(g.normal(size=(B, 3, H, W))) + 1.0
+        target = fields + 0.2 * g.normal(size=fields.shape)
+        fd, td, ed = _dev_f32(fields), _dev_f32(target), _dev_f32([0.35, 0.45])
+        p_ref = params.astype(np.float64)
+        m = np.zeros(n)
+        v = np.zeros(n)
+        for t in range(1, 6):
+            A.aap_sur_train_step(s, fd.data_ptr(), td.data_ptr(), ed.data_ptr(), B)
+            grad = A.aap_sur_get_grads(s).astype(np.float64)
+            p_ref, m, v = S.adam(p_ref, grad, m, v, t, lr=1e-3)
+            got = A.aap_sur_get_params(s).astype(np.float64)
+            assert np.abs(got - p_ref).max() < 2e-6, (t, np.abs(got - p_ref).max())
+            p_ref = got                      # the next step starts from the library's FP32 weights
     finally:
         A.aap_sur_destroy(s)
 

@@ -82,6 +82,39 @@ def test_adam_first_step_closed_form():
     assert np.allclose(p1, p - 0.01 * np.sign(gr), atol=1e-15)
 
 
+def test_adam_constant_gradient_every_step():
+    """A constant gradient g gives bias-corrected moments m^ = g and v^ = g^2 at
+    every step t, so each step moves a parameter by exactly lr g / (|g| + eps).
+    A moment that is not carried over between steps, or a bias correction with
+    the wrong t, breaks this from t = 2 on."""
+    p = np.array([1.0, -2.0, 0.5, 3.0])
+    gr = np.array([0.3, -4.0, 1e-3, 2.5e-6])
+    lr, eps = 0.01, 1e-8
+    m = v = np.zeros(4)
+    for t in range(1, 8):
+        p_new, m, v = S.adam(p, gr, m, v, t, lr=lr, eps=eps)
+        assert np.allclose(p_new - p, -lr * gr / (np.abs(gr) + eps), rtol=1e-10, atol=1e-16), t
+        p = p_new
+
+
+def test_adam_alternating_gradient_closed_form():
+    """g_t = (-1)^t c: the first moment is the geometric sum
+    m_t = (1 - b1) c (-1)^t (1 - (-b1)^t) / (1 + b1) and the second
+    v_t = (1 - b2^t) c^2, so the step is known in closed form for every t."""
+    c, lr, b1, b2, eps = np.array([0.7, -1.3]), 0.05, 0.9, 0.999, 1e-8
+    p = np.array([0.2, 0.4])
+    m = v = np.zeros(2)
+    for t in range(1, 9):
+        g = (-1.0) ** t * c
+        p_new, m, v = S.adam(p, g, m, v, t, lr=lr, b1=b1, b2=b2, eps=eps)
+        mt = (1 - b1) * c * (-1.0) ** t * (1 - (-b1) ** t) / (1 + b1)
+        vt = (1 - b2 ** t) * c * c
+        assert np.allclose(m, mt, rtol=1e-12) and np.allclose(v, vt, rtol=1e-12)
+        step = lr * (mt / (1 - b1 ** t)) / (np.sqrt(vt / (1 - b2 ** t)) + eps)
+        assert np.allclose(p - p_new, step, rtol=1e-10), t
+        p = p_new
+
+
 def test_bf16_rounding():
     vals = np.array([1.0, 1.00390625, 1.005859375, -3.0e-5, 65280.0, 1.0 + 2 ** -9])
     r = S.bf16_round(vals)
