@@ -181,7 +181,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for fn in ("aap_kernels.cu", "aap_internal.cuh", "aap_device.cuh"):
+    for fn in ("aap_kernels.cu", "aap_pipe.cu", "aap_tile.cuh", "aap_internal.cuh", "aap_device.cuh"):
         with open(os.path.join(ROOT, "paper_2211_15630_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -641,7 +641,8 @@ def main():
     workload = ("vicsek_N2^24_L2896_rho2" if default_size else f"vicsek_N{args.n}_L{args.L:g}")
     if args.kn:
         workload = "mf" + workload + f"_k{args.kn}"
-    step_kernel = "k_step" if args.kn == 0 else "k_mf_count+scan+scatter+update+exact"
+    step_kernel = ("k_step_pipe" if lay.threads == 1024 else "k_step") if args.kn == 0 else \
+        "k_mf_count+scan+scatter+update+exact"
     launches_per_step = 2 if args.kn == 0 else 7
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -92,7 +92,10 @@ typedef struct aap_params {
     int32_t  tile_w;     /* cells per tile along x; 0 = automatic               */
     int32_t  tile_h;     /* cells per tile along y; 0 = automatic               */
     int32_t  threads;    /* threads per block of the step kernel: 0 (automatic),
-                            256 or 512                                          */
+                            256 or 512 (whole-block tile kernel), 1024 (the
+                            pipelined kernel: one block per SM with copy, sort
+                            and update warps; one species, not in ensembles).
+                            Automatic picks 1024 where it applies, else 512  */
     double   capacity;   /* tile-region capacity over the mean occupancy;
                             0 = automatic (4)                                   */
     int32_t  binnum_theta;      /* bins of the orientation histogram over

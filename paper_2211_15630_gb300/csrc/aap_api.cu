@@ -68,6 +68,7 @@ struct aap_handle {
     Ctl *d_ctl = nullptr;
     int *d_x0tab = nullptr, *d_y0tab = nullptr;
     unsigned char *d_scratch = nullptr;
+    int *d_dense = nullptr;             // pipelined step: tiles left to the whole-block routine
     unsigned long long *d_obs = nullptr;
     int *d_seen = nullptr;
     unsigned long long *d_bad = nullptr;     // [2] first invalid position / orientation of aap_set_state
@@ -213,8 +214,10 @@ int check_params(const aap_params *p)
         return fail(AAP_EINVAL, "tile_w and tile_h must be 0 (automatic) or in [6, 64]");
     if ((p->tile_w && p->tile_w < 6) || (p->tile_h && p->tile_h < 6))
         return fail(AAP_EINVAL, "tile_w and tile_h must be 0 (automatic) or in [6, 64]");
-    if (p->threads != 0 && p->threads != 256 && p->threads != 512)
-        return fail(AAP_EINVAL, "threads must be 0, 256 or 512");
+    if (p->threads != 0 && p->threads != 256 && p->threads != 512 && p->threads != 1024)
+        return fail(AAP_EINVAL, "threads must be 0, 256, 512 or 1024");
+    if (p->threads == 1024 && (p->nspecies > 1 || p->kn > 0))
+        return fail(AAP_EINVAL, "threads = 1024 (the pipelined step) needs one species and a metric neighbourhood");
     if (!finite(p->capacity) || p->capacity < 0 || (p->capacity > 0 && p->capacity < 1))
         return fail(AAP_EINVAL, "capacity must be 0 (automatic) or >= 1");
     if (p->weight_len < 0 || p->weight_len > 128) return fail(AAP_EINVAL, "weight_len must be in [0, 128]");
@@ -289,6 +292,7 @@ int set_capacity_mf(aap_handle *h)
     L.scratch_cap = 0;
     L.scratch_per_block = 0;
     L.threads = 256;
+    L.pipe = 0;
     L.model = p.model;
     L.stage_cap = 0;
     L.nce_max = 0;
@@ -300,6 +304,32 @@ int set_capacity_mf(aap_handle *h)
     L.mf_n = p.n;
     L.mf_ncell = (long long)S.ncx * S.ncy;
     AAP_CK(aapk::configure_mf_kernels(p.model, p.kn, L.hist_words, sm_count(), &L.mf_grid));
+    return AAP_OK;
+}
+
+// Shared buffers of the pipelined step: the largest staging capacity (a
+// multiple of 64, at most kPipeMaxStage) whose two raw and two sorted buffers,
+// with own lists sized for 7/8 of it, fit the block's shared memory.
+int set_pipe(aap_handle *h)
+{
+    LaunchCfg &L = h->L;
+    int dev = 0, optin = 0;
+    AAP_CK(cudaGetDevice(&dev));
+    AAP_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    size_t stat = 0;
+    AAP_CK(aapk::pipe_static_smem(L.model, &stat));
+    int cap = aapk::kPipeMaxStage;
+    auto own_of = [](int c) { return aapk::round_up(c * 7 / 8, 64); };
+    while (cap >= 256 && aapk::pipe_smem_bytes(cap, own_of(cap), L.nce_max, L.hist_words) + stat > (size_t)optin)
+        cap -= 64;
+    if (cap < 256) return AAP_OK;
+    L.pipe_cap = cap;
+    L.pipe_cap_own = own_of(cap);
+    L.pipe_grid = std::max(1, std::min(h->hs.ntiles, sm_count()));
+    AAP_CK(aapk::configure_pipe_kernel(L.model, aapk::pipe_smem_bytes(L.pipe_cap, L.pipe_cap_own, L.nce_max,
+                                                                      L.hist_words)));
+    L.pipe = 1;
+    L.threads = 1024;
     return AAP_OK;
 }
 
@@ -326,7 +356,7 @@ int set_capacity(aap_handle *h, double factor)
     if ((long long)own + halo + L.spill_list_cap > 65472)
         return fail(AAP_EINVAL, "tile capacity too large (reduce tile size or capacity)");
     L.scratch_cap = aapk::round_up(own + halo + L.spill_list_cap, 64);
-    L.threads = p.threads ? p.threads : 512;
+    L.threads = p.threads == 1024 ? 512 : (p.threads ? p.threads : 512);
     L.model = p.model;
     L.stage_cap = scap;
     L.nce_max = nce;
@@ -340,6 +370,14 @@ int set_capacity(aap_handle *h, double factor)
     L.scratch_per_block = aapk::stage_bytes(L.scratch_cap) + aapk::spill_list_bytes(L.spill_list_cap);
     L.scratch_per_block = (L.scratch_per_block + 255) / 256 * 256;
     L.nsys = 1;
+    // the pipelined step: one system, one species (ensemble members use the
+    // whole-block kernel, which batches systems)
+    L.pipe = 0;
+    if (!h->member && p.nspecies <= 1 && (p.threads == 0 || p.threads == 1024)) {
+        int rc = set_pipe(h);
+        if (rc) return rc;
+        if (!L.pipe && p.threads == 1024) return fail(AAP_EINVAL, "the pipelined step kernel does not fit this tiling");
+    }
     return AAP_OK;
 }
 
@@ -599,6 +637,8 @@ int alloc_all(aap_handle *h)
         if ((rc = dev_alloc(h, &h->d_sys, sizeof(Sys)))) return rc;
         if ((rc = dev_alloc(h, &h->d_tile_base, 2 * sizeof(int)))) return rc;
         if ((rc = dev_alloc(h, &h->d_ctl, sizeof(Ctl)))) return rc;
+        if ((rc = dev_alloc(h, &h->d_dense, (size_t)std::max(S.ntiles, 1) * sizeof(int)))) return rc;
+        AAP_CK(cudaMemsetAsync(h->d_dense, 0, (size_t)std::max(S.ntiles, 1) * sizeof(int), h->stream));
     }
     if ((rc = dev_alloc(h, &h->d_x0tab, (size_t)(S.ntx + 1) * sizeof(int)))) return rc;
     if ((rc = dev_alloc(h, &h->d_y0tab, (size_t)(S.nty + 1) * sizeof(int)))) return rc;
@@ -631,6 +671,7 @@ int alloc_all(aap_handle *h)
     L.sys = h->d_sys;
     L.tile_base = h->d_tile_base;
     L.ctl = h->d_ctl;
+    L.dense_list = h->d_dense;
     return push_sys(h);
 }
 
@@ -649,6 +690,10 @@ int read_errors(aap_handle *h)
     if (err & aapk::ERR_BOUNDS) {
         h->broken = true;
         return fail(AAP_ESTATE, "a particle record decoded outside its tile (internal fault)");
+    }
+    if (err & aapk::ERR_TIMEOUT) {
+        h->broken = true;
+        return fail(AAP_ETIMEOUT, "a bounded wait of the pipelined step kernel ran out");
     }
     if (err & aapk::ERR_NAN) return fail(AAP_ENAN, "a non-finite orientation was produced");
     return AAP_OK;
@@ -879,6 +924,10 @@ int act_on_error(aap_handle *h, int err, bool *relaid)
         h->broken = true;
         return fail(AAP_EOVERFLOW, "particles were lost: a tile overflowed its spill capacity");
     }
+    if (err & aapk::ERR_TIMEOUT) {
+        h->broken = true;
+        return fail(AAP_ETIMEOUT, "a bounded wait of the pipelined step kernel ran out");
+    }
     if ((err & aapk::ERR_SPILL) && h->p.capacity == 0) {
         // grow by 1.5, or by as much as the staged indices allow; at the limit
         // the overflow stays in the spill list (exact, only slower)
@@ -1027,6 +1076,7 @@ int ens_combine(aap_ens *e)
     L.tile_base = e->d_tile_base;
     L.ctl = e->d_ctl;
     L.threads = e->params[0].threads ? e->params[0].threads : pol.threads;
+    L.pipe = 0;
     L.stage_cap = 64;
     L.nce_max = 9;
     L.hist_words = 0;
@@ -1608,6 +1658,8 @@ int aap_ens_create(const aap_params *params, int32_t count, void *stream, aap_en
         if (params[r].kn > 0) return fail(AAP_EINVAL, "metric-free systems (kn > 0) are not batched; use aap_create");
         if (params[r].model != params[0].model) return fail(AAP_EINVAL, "all replicas must use the same model");
         if (params[r].threads != params[0].threads) return fail(AAP_EINVAL, "all replicas must use the same threads");
+        if (params[r].threads == 1024)
+            return fail(AAP_EINVAL, "ensembles run the whole-block step kernel: threads must be 0, 256 or 512");
     }
     aap_ens *e = new aap_ens();
     e->params.assign(params, params + count);
@@ -1845,7 +1897,7 @@ int aap_get_layout(aap_handle *h, aap_layout *out)
     out->fix_bits_x = S.sx;
     out->fix_bits_y = S.sy;
     out->threads = h->L.threads;
-    out->stage_cap = h->L.stage_cap;
+    out->stage_cap = h->L.pipe ? h->L.pipe_cap : h->L.stage_cap;
     out->tile_slots = S.tile_slots;
     out->device_bytes = (int64_t)h->bytes;
     out->cell_x = h->csx;

@@ -43,7 +43,11 @@ enum : int {
     ERR_BOUNDS = 4,   // a record decoded outside its tile (internal fault)
     ERR_NAN = 8,      // a non-finite orientation was produced
     ERR_STAGE = 16,   // a tile exceeded the scratch staging capacity
+    ERR_TIMEOUT = 32, // a bounded wait of the pipelined step kernel ran out
 };
+
+constexpr int kPipeMaxStage = 4096;     // staged particles per tile in the pipelined step
+constexpr int kPipeMaxSpill = 256;      // spilled records one pipelined tile may take
 
 struct Sys {
     // geometry
@@ -124,7 +128,9 @@ struct Ctl {
     long long step;             // steps taken; parity selects the current buffer
     int tile_next;              // dynamic tile fetch of the step kernel
     int finish_ticket;
-    int pad[4];
+    int dense_count;            // pipelined step: tiles listed for the whole-block routine
+    int dense_next;             // ... and taken
+    int pad[2];
 };
 
 // Segment: one region of one (possibly the same) tile mapped into the

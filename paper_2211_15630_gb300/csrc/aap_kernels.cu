@@ -195,6 +195,8 @@ __global__ void k_finish(Sys *sys, int nsys, const int *__restrict__ tile_base, 
     if (s_last && threadIdx.x == 0) {
         ctl->tile_next = 0;
         ctl->finish_ticket = 0;
+        ctl->dense_count = 0;
+        ctl->dense_next = 0;
         ctl->step = step + 1;
     }
 }
@@ -351,10 +353,14 @@ static cudaError_t launch_step_t(const LaunchCfg &L, cudaStream_t st, cudaEvent_
     const size_t smem = step_smem_bytes(L.stage_cap, L.nce_max, L.hist_words);
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    k_step<NT, MODEL><<<L.grid_step, NT, smem, st>>>(L.sys, L.nsys, L.tile_base, L.ctl, L.stage_cap,
-                                                      L.nce_max, L.scratch, L.scratch_per_block,
-                                                      L.scratch_cap, L.spill_list_cap);
-    e = cudaGetLastError();
+    if (L.pipe) {
+        e = launch_step_pipe(L, st);
+    } else {
+        k_step<NT, MODEL><<<L.grid_step, NT, smem, st>>>(L.sys, L.nsys, L.tile_base, L.ctl, L.stage_cap,
+                                                          L.nce_max, L.scratch, L.scratch_per_block,
+                                                          L.scratch_cap, L.spill_list_cap);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
     k_finish<<<L.grid_finish, 256, 0, st>>>(L.sys, L.nsys, L.tile_base, L.ctl);
@@ -367,6 +373,7 @@ static cudaError_t launch_step_t(const LaunchCfg &L, cudaStream_t st, cudaEvent_
 template <int MODEL>
 static cudaError_t launch_step_m(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev)
 {
+    if (L.pipe) return launch_step_t<512, MODEL>(L, st, ev);     // the pipelined kernel has its own shape
     switch (L.threads) {
     case 256: return launch_step_t<256, MODEL>(L, st, ev);
     case 512: return launch_step_t<512, MODEL>(L, st, ev);

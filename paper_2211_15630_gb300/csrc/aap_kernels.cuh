@@ -24,6 +24,12 @@ struct LaunchCfg {
     int nce_max;                 // cells of the largest tile plus its ring
     int hist_words;              // histogram bins (theta + |Omega|) of the widest system
     int grid_step, grid_finish;
+    // pipelined step (one system, one species): shared buffers of pipe_cap
+    // staged / pipe_cap_own own particles per tile, one block per SM; tiles
+    // that do not fit go to dense_list (device [ntiles], zero between steps)
+    int pipe;
+    int pipe_cap, pipe_cap_own, pipe_grid;
+    int *dense_list;
     // metric-free step (knn > 0): cell count, scan, scatter, k-nearest update
     int knn;
     long long mf_n, mf_ncell;
@@ -35,7 +41,16 @@ size_t step_smem_bytes(int stage_cap, int nce_max, int hist_words);
 // of its blocks fit on one SM.
 cudaError_t configure_step_kernel(int model, int threads, size_t smem_bytes, int *blocks_per_sm);
 
-// One full step: k_step then k_finish.  With ev != nullptr, ev[0..2] are
+// Dynamic shared memory of the pipelined step kernel.
+__host__ __device__ size_t pipe_smem_bytes(int cap, int cap_own, int nce_max, int hist_words);
+// Static shared memory of the pipelined step kernel of a model.
+cudaError_t pipe_static_smem(int model, size_t *bytes);
+// Set the dynamic shared-memory limit of the pipelined step kernel.
+cudaError_t configure_pipe_kernel(int model, size_t smem);
+// The pipelined step kernel alone (launch_step adds k_finish).
+cudaError_t launch_step_pipe(const LaunchCfg &L, cudaStream_t st);
+
+// One full step: k_step (or the pipelined step kernel) then k_finish.  With ev != nullptr, ev[0..2] are
 // recorded before k_step, after k_step and after k_finish.
 cudaError_t launch_step(const LaunchCfg &L, cudaStream_t st, cudaEvent_t *ev = nullptr);
 

@@ -1,0 +1,885 @@
+// aap_pipe.cu -- the pipelined tile step of one system (sm_103a).
+//
+// One time step (Sec. 2 of Kuersten, "Aligning Active Particles Py
+// Package") with the arithmetic of the whole-block tile routine of
+// aap_tile.cuh, but the 32 warps of a persistent block (one per SM) split into
+// three roles that hand tiles to each other through mbarriers instead of
+// block-wide barriers:
+//
+//   copy warp (warp 0)     claims tiles, computes each tile's geometry and its
+//                          25 source segments (own regions, facing halo
+//                          regions with periodic shifts or mirror maps,
+//                          Sec. 2.4; the cell lists of Sec. 3.2) and copies
+//                          them global -> shared with one cp.async.bulk per
+//                          segment into one of two raw record buffers,
+//                          completing on that buffer's mbarrier;
+//   sort warps (NSORT)     map each staged record into the tile's extended
+//                          frame, histogram it by cell, prefix-scan the
+//                          histogram and place the records in cell order
+//                          (x, y and cos, sin as exact integers) into one of
+//                          two output buffers, with the tile's own particles
+//                          listed in cell order;
+//   update warps (rest)    take chunks of 32 own particles from the ready
+//                          output buffer, sum their 3x3 cells (Eq. collision_VM
+//                          / collision_NVM, or the Langevin coupling sum of
+//                          Eq. Langevin_dynamics) in exact integers, draw
+//                          Philox noise, stream, apply the boundary rule and
+//                          scatter the new records into the next step's
+//                          regions.
+//
+// Tile i+1 is copied and sorted while the update warps work on tile i, and an
+// update warp that is done with tile i starts on tile i+1 without waiting for
+// the slowest warp.  Tiles whose staged set does not fit the shared buffers
+// go to a list and are done at the end by the whole block with the tile
+// routine of aap_tile.cuh (shared staging area or global scratch).  Every
+// mbarrier wait is bounded (about two seconds of SM clock); a wait that runs
+// out sets ERR_TIMEOUT in the error word and the block winds down.
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "aap_device.cuh"
+#include "aap_internal.cuh"
+#include "aap_kernels.cuh"
+#include "aap_tile.cuh"
+
+namespace aapk {
+
+namespace {
+
+constexpr int kPipeThreads = 1024;
+constexpr int kPipeWarps = kPipeThreads / 32;
+constexpr int kPipeMaxChunks = kPipeMaxStage / 32 + 1;
+constexpr long long kPipeWaitCycles = 4000000000ll;    // about 2 s at 2 GHz
+
+// Segment maps and counts of one staged tile, written by the copy warp.
+struct RawMeta {
+    int tile;                   // tile index, -1: no more tiles
+    int m, m_seg, n_spill, n_own;
+    int tx, ty, tw, th, twL, twR, thD, thU;
+    int segpre[kSegs + 1];
+    int ax[kSegs], ay[kSegs], cx[kSegs], cy[kSegs], flip[kSegs];
+    long long bx[kSegs], by[kSegs];
+    unsigned char segc[kPipeMaxChunks];     // segment of staged index 32 i
+    unsigned char spill_seg[kPipeMaxSpill]; // segment of staged spill record j
+};
+
+// What the update warps need of a sorted tile.
+struct OutMeta {
+    int tile;                   // -1: no more tiles
+    int n_own, tx, ty, tw, th, W2, twL, twR, thD, thU;
+    int wide;                   // a cell holds enough particles for 512 candidates
+};
+
+struct PipeShared {
+    Sys S;
+    RawMeta raw[2];
+    OutMeta out[2];
+    const int4 *src[kSegs];     // copy warp: segment sources of the tile being set up
+    int chunk[2];               // next chunk of 32 own particles, per output buffer
+    int issued[2], taken[2];    // raw buffer fills issued by the copy warp / sorted
+    int flag;                   // a previous step's wait ran out
+    int dense_tile;
+    int warp_tot[kPipeWarps];
+    long long red[5][kPipeWarps];
+    __align__(8) unsigned long long bar_raw_full[2], bar_raw_empty[2], bar_full[2], bar_empty[2];
+};
+
+// Per-buffer shared arrays, carved from dynamic shared memory.  Buffer b of
+// each kind is reached by pointer arithmetic (no arrays of pointers indexed at
+// run time, which would live in local memory).
+struct PipeBufs {
+    int4 *raw0;                 // [2][cap] staged records as copied; mapped in place by the sort warps
+    float4 *P0;                 // [2][cap] records in cell order: x, y from the tile centre, cos, sin (int32, 2^-22)
+    int4 *own0;                 // [2][cap_own] own particles in cell order: X, Y (tile frame), theta bits, id
+    int *cst0;                  // [2][cst_stride] cell starts in P
+    unsigned short *oq0;        // [2][oq_stride] position in P of own particle o
+    unsigned short *cellw;      // sort scratch: flip << 14 | ey << 7 | ex of staged record k
+    unsigned short *slotw;      // arrival rank in its cell
+    int *hist;                  // [nce]
+    int *rowoff;                // own index = position in P + rowoff[ey]
+    int *mhist;                 // measured theta / |Omega| counts of the block
+    int cap, cap_own, cst_stride, oq_stride;
+    __device__ __forceinline__ int4 *raw(int b) const { return raw0 + b * cap; }
+    __device__ __forceinline__ float4 *P(int b) const { return P0 + b * cap; }
+    __device__ __forceinline__ int4 *own(int b) const { return own0 + b * cap_own; }
+    __device__ __forceinline__ int *cstart(int b) const { return cst0 + b * cst_stride; }
+    __device__ __forceinline__ unsigned short *ownq(int b) const { return oq0 + b * oq_stride; }
+};
+
+__device__ __forceinline__ void carve_pipe(PipeBufs &B, unsigned char *p, int cap, int cap_own, int nce)
+{
+    B.cap = cap;
+    B.cap_own = cap_own;
+    B.cst_stride = round_up(nce + 1, 4);
+    B.oq_stride = round_up(cap_own, 8);
+    B.raw0 = (int4 *)p;
+    p += (size_t)2 * cap * 16;
+    B.P0 = (float4 *)p;
+    p += (size_t)2 * cap * 16;
+    B.own0 = (int4 *)p;
+    p += (size_t)2 * cap_own * 16;
+    B.cst0 = (int *)p;
+    p += (size_t)2 * B.cst_stride * 4;
+    B.oq0 = (unsigned short *)p;
+    p += (size_t)2 * B.oq_stride * 2;
+    B.cellw = (unsigned short *)p;
+    p += (size_t)round_up(cap, 8) * 2;
+    B.slotw = (unsigned short *)p;
+    p += (size_t)round_up(cap, 8) * 2;
+    B.hist = (int *)p;
+    p += (size_t)round_up(nce, 4) * 4;
+    B.rowoff = (int *)p;
+    p += (size_t)(kMaxTile + 4) * 4;
+    B.mhist = (int *)p;
+}
+
+// ------------------------------------------------------------- mbarriers --
+__device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(sa(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(sa(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Wait for the completion of the phase of the given parity, bounded in time.
+// false: the bound ran out (ERR_TIMEOUT is set).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done) : "r"(sa(bar)), "r"(parity) : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kPipeWaitCycles) {
+            atomicOr(err, ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Every lane of the warp polls (one instruction for the warp), so that each
+// lane itself acquires what the phase released; the outcome is made
+// warp-uniform (a lane whose bound ran out makes the warp give up).
+__device__ __forceinline__ bool warp_wait(unsigned long long *bar, unsigned parity, int *err)
+{
+    const bool ok = mbar_wait(bar, parity, err);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Named barrier of the sort warps (id 1).
+__device__ __forceinline__ void sort_sync(int nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// The same barrier, returning whether every participating thread passed ok.
+__device__ __forceinline__ bool sort_sync_and(int nthreads, bool ok)
+{
+    int r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                 "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+                 : "=r"(r) : "r"((int)ok), "r"(nthreads) : "memory");
+    return r != 0;
+}
+
+// One bulk copy global -> shared of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned) that completes on bar's transaction count.
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(sa(dst)), "l"(src), "r"(bytes), "r"(sa(bar)) : "memory");
+}
+
+// -------------------------------------------------------------- copy warp --
+// Geometry, the 25 segments and the spill matches of tile g into M and
+// sh.src (all lanes of the copy warp).  spill_e (global scratch) receives the
+// spill entry of staged spill record j.  Returns false (warp-uniform) when the
+// tile does not fit the pipeline's buffers.
+__device__ __forceinline__ bool copy_setup(PipeShared &sh, int g, int cur, RawMeta &M, int cap, int cap_own,
+                                           int *spill_e)
+{
+    const Sys &S = sh.S;
+    const int lane = threadIdx.x & 31;
+    const TileGeo G = tile_geo(S, g);
+    Seg sg;
+    if (lane < kSegs) sg = make_seg(S, G, lane, cur);
+    const int c = lane < kSegs ? sg.count : 0;
+    const int incl = warp_incl_scan(c);
+    const int m_seg = __shfl_sync(0xffffffffu, incl, kSegs - 1);
+    const int own_seg = __shfl_sync(0xffffffffu, incl, 8);
+    // particles parked in the spill list for one of the tile's segments
+    const int nsp = min(*((volatile int *)&S.spill_cnt[cur]), S.spill_cap);
+    int n_spill = 0, n_own_spill = 0;
+    if (nsp > 0) {
+        const int mt = lane < kSegs ? sg.tile : -1, mr = lane < kSegs ? sg.region : -1;
+        for (int e0 = 0; e0 < nsp; e0 += 32) {
+            const int e = e0 + lane;
+            const int key = e < nsp ? S.spill_key[cur][e] : -1;
+            const int et = key >= 0 ? key / kCntStride : -2, er = key >= 0 ? key % kCntStride : -2;
+            for (int s = 0; s < kSegs; ++s) {
+                const int st = __shfl_sync(0xffffffffu, mt, s), sr = __shfl_sync(0xffffffffu, mr, s);
+                const bool hit = et == st && er == sr;
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                const int j = n_spill + __popc(bal & ((1u << lane) - 1u));
+                if (hit && j < kPipeMaxSpill) {
+                    M.spill_seg[j] = (unsigned char)s;
+                    spill_e[j] = e;
+                }
+                n_spill += __popc(bal);
+                if (s < 9) n_own_spill += __popc(bal);
+            }
+        }
+    }
+    const int m = m_seg + n_spill;
+    const int n_own = own_seg + n_own_spill;
+    if (m > cap || n_own > cap_own || n_spill > kPipeMaxSpill) return false;
+    if (lane < kSegs) {
+        M.segpre[lane] = incl - c;
+        M.ax[lane] = sg.ax;
+        M.ay[lane] = sg.ay;
+        M.cx[lane] = sg.cx;
+        M.cy[lane] = sg.cy;
+        M.bx[lane] = sg.bx;
+        M.by[lane] = sg.by;
+        M.flip[lane] = sg.flip;
+        sh.src[lane] = sg.base;
+    }
+    if (lane == 0) {
+        M.segpre[kSegs] = m_seg;
+        M.tile = g;
+        M.m = m;
+        M.m_seg = m_seg;
+        M.n_spill = n_spill;
+        M.n_own = n_own;
+        M.tx = G.tx; M.ty = G.ty; M.tw = G.tw; M.th = G.th;
+        M.twL = G.twL; M.twR = G.twR; M.thD = G.thD; M.thU = G.thU;
+    }
+    __syncwarp();
+    // segment of every 32nd staged index
+    for (int i = lane; i * 32 < m_seg; i += 32) {
+        const int k = i * 32;
+        int lo = 0, hi = kSegs;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (M.segpre[mid] <= k) lo = mid; else hi = mid;
+        }
+        M.segc[i] = (unsigned char)lo;
+    }
+    __syncwarp();
+    return true;
+}
+
+// ------------------------------------------------------------- sort warps --
+// Map every staged record of raw buffer r into the tile's extended frame (in
+// place) and histogram it by cell.  tid: index among the NS sort threads.
+__device__ __forceinline__ void sort_map(PipeShared &sh, const PipeBufs &B, int r, int tid, int NS)
+{
+    const Sys &S = sh.S;
+    const RawMeta &M = sh.raw[r];
+    const int m = M.m, m_seg = M.m_seg;
+    const int W2 = M.tw + 2, H2 = M.th + 2;
+    int4 *R = B.raw(r);
+    for (int k = tid; k < m; k += NS) {
+        int s;
+        if (k < m_seg) {
+            s = M.segc[k >> 5];
+            while (M.segpre[s + 1] <= k) ++s;
+        } else {
+            s = M.spill_seg[k - m_seg];
+        }
+        const int4 rr = R[k];
+        const int ax = M.ax[s], ay = M.ay[s];
+        const int lx = rr.x >> S.sx, ly = rr.y >> S.sy;
+        int ex = ax * lx + M.cx[s] + 1, ey = ay * ly + M.cy[s] + 1;
+        if ((unsigned)ex >= (unsigned)W2 || (unsigned)ey >= (unsigned)H2) {
+            atomicOr(S.err, ERR_BOUNDS);
+            ex = min(max(ex, 0), W2 - 1);
+            ey = min(max(ey, 0), H2 - 1);
+        }
+        R[k] = make_int4((int)(ax * (long long)rr.x + M.bx[s]), (int)(ay * (long long)rr.y + M.by[s]), rr.z, rr.w);
+        B.cellw[k] = (unsigned short)((M.flip[s] << 14) | (ey << 7) | ex);
+        B.slotw[k] = (unsigned short)atomicAdd(&B.hist[ey * W2 + ex], 1);
+    }
+}
+
+// Scan the histogram into output buffer b's cell starts (clearing the
+// histogram), the own-row offsets and the tile's output meta, then place the
+// records in cell order.  The output buffer must be free.
+template <int MODEL>
+__device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, int r, int b, int tid, int NS,
+                                           int cap_own)
+{
+    const Sys &S = sh.S;
+    const RawMeta &M = sh.raw[r];
+    const int m = M.m, tw = M.tw, th = M.th;
+    const int W2 = tw + 2, nce = W2 * (th + 2);
+    int *cst = B.cstart(b);
+    const int lane = tid & 31, w = tid >> 5, nw = NS >> 5;
+    int maxc = 0;
+    {
+        const int per = (nce + NS - 1) / NS;
+        const int b0 = min(tid * per, nce), e0 = min(b0 + per, nce);
+        int sum = 0;
+        for (int i = b0; i < e0; ++i) {
+            const int h = B.hist[i];
+            sum += h;
+            maxc = max(maxc, h);
+        }
+        const int incl = warp_incl_scan(sum);
+        if (lane == 31) sh.warp_tot[w] = incl;
+        sort_sync(NS);
+        if (w == 0) {
+            const int v = lane < nw ? sh.warp_tot[lane] : 0;
+            const int wi = warp_incl_scan(v);
+            if (lane < nw) sh.warp_tot[lane] = wi - v;
+            if (lane == nw - 1) cst[nce] = wi;
+        }
+        sort_sync(NS);
+        int run = incl - sum + sh.warp_tot[w];
+        for (int i = b0; i < e0; ++i) {
+            cst[i] = run;
+            run += B.hist[i];
+            B.hist[i] = 0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
+    sort_sync(NS);                            // every warp has read its scan offset
+    if (lane == 0) sh.warp_tot[w] = maxc;
+    sort_sync(NS);
+    // own rows: index offsets; the tile's output meta
+    if (w == 0) {
+        int carry = 0;
+        for (int r0 = 0; r0 < th; r0 += 32) {
+            const int rw = r0 + lane;
+            int len = 0, first = 0;
+            if (rw < th) {
+                first = cst[(rw + 1) * W2 + 1];
+                len = cst[(rw + 1) * W2 + tw + 1] - first;
+            }
+            const int incl = warp_incl_scan(len);
+            if (rw < th) B.rowoff[rw + 1] = carry + incl - len - first;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        int mx = lane < nw ? sh.warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+            OutMeta &O = sh.out[b];
+            O.tile = M.tile;
+            O.n_own = min(carry, cap_own);
+            O.tx = M.tx; O.ty = M.ty; O.tw = tw; O.th = th; O.W2 = W2;
+            O.twL = M.twL; O.twR = M.twR; O.thD = M.thD; O.thU = M.thU;
+            O.wide = 9 * mx >= 512;
+            sh.chunk[b] = 0;
+            if (carry != M.n_own) atomicOr(S.err, ERR_BOUNDS);
+        }
+    }
+    sort_sync(NS);
+    // records into cell order (arrival order inside a cell: the sums are
+    // exact integers, so this order does not matter); own particles listed
+    const int xc = tw << (S.sx - 1), yc = th << (S.sy - 1);
+    const int4 *R = B.raw(r);
+    float4 *P = B.P(b);
+    int4 *OWN = B.own(b);
+    unsigned short *OQ = B.ownq(b);
+    for (int k = tid; k < m; k += NS) {
+        const unsigned cf = B.cellw[k];
+        const int ex = cf & 127, ey = (cf >> 7) & 127;
+        const int q = cst[ey * W2 + ex] + B.slotw[k];
+        const int4 rk = R[k];
+        float thv = __int_as_float(rk.z);
+        float sn, cs;
+        if (MODEL == 1 && S.order != 1) {
+            thv *= (float)S.order;
+            sincosf(thv, &sn, &cs);
+        } else {
+            // |theta| <= pi: the hardware sine/cosine is within 2^-21.4 absolute
+            __sincosf(thv, &sn, &cs);
+        }
+        const int flip = cf >> 14;
+        if (flip & 1) {
+            if (MODEL != 1 || (S.order & 1)) cs = -cs; else sn = -sn;
+        }
+        if (flip & 2) sn = -sn;
+        P[q] = make_float4((float)(rk.x - xc) * S.ux, (float)(rk.y - yc) * S.uy,
+                           __int_as_float(__float2int_rn(cs * kFixNbF)), __int_as_float(__float2int_rn(sn * kFixNbF)));
+        if (ex >= 1 && ex <= tw && ey >= 1 && ey <= th) {
+            const int o = q + B.rowoff[ey];
+            if (o < cap_own) {
+                OWN[o] = rk;
+                OQ[o] = (unsigned short)q;
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------- update warps --
+struct Acc {
+    long long c, s, n, c2, s2;
+};
+
+// One particle per lane (own index o, inactive when o >= n_own); every lane
+// of the warp must call (the scatter is warp-aggregated).
+template <int MODEL>
+__device__ __forceinline__ void update_one(const Sys &S, const OutMeta &O, const float4 *__restrict__ P,
+                                           const int *cstart, const int4 *OWN, const unsigned short *OQ, int o,
+                                           long long step, bool measure, int *mhist, Acc &acc)
+{
+    const int nxt = (int)(step & 1) ^ 1;
+    const bool act = o < O.n_own;
+    int4 rec = make_int4(0, 0, 0, 0);
+    int dtile = 0, region = 0;
+    if (act) {
+        const int tw = O.tw, th = O.th, W2 = O.W2;
+        const int4 rk = OWN[o];
+        const int X = rk.x, Y = rk.y;
+        const float thi = __int_as_float(rk.z);
+        const unsigned id = (unsigned)rk.w;
+        const int ec = ((Y >> S.sy) + 1) * W2 + (X >> S.sx) + 1;
+        const float4 pi = P[OQ[o]];
+        float sc, ss;                    // neighbour sums in units of 2^-22
+        int cnt;
+        bool narrow = !O.wide;
+        if (!narrow) {
+            const int ncand = cstart[ec - W2 + 2] - cstart[ec - W2 - 1] + cstart[ec + 2] - cstart[ec - 1] +
+                              cstart[ec + W2 + 2] - cstart[ec + W2 - 1];
+            narrow = ncand < 512;
+        }
+        if (narrow) {
+            int a, b;
+            neighbour_sum<MODEL, int>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
+            sc = (float)a;
+            ss = (float)b;
+        } else {
+            long long a, b;
+            neighbour_sum<MODEL, long long>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
+            sc = (float)a;
+            ss = (float)b;
+        }
+        const int nb = cnt - 1;          // the particle itself was counted
+        if (measure) {
+            int bt = (int)floorf((thi + AAP_PI_F) * ((float)S.bins_theta * (1.0f / AAP_2PI_F)));
+            bt = min(max(bt, 0), S.bins_theta - 1);
+            atomicAdd(&mhist[bt], 1);
+            atomicAdd(&mhist[S.bins_theta + min(nb, S.bins_nbr - 1)], 1);
+        }
+        uint32_t c4[4] = {id, (uint32_t)step, (uint32_t)((unsigned long long)step >> 32), 0u};
+        philox4x32_10(c4, S.seed_lo, S.seed_hi);
+        const float u0 = u01f(c4[0]);
+        float thn, cn, sn;
+        int dX, dY;
+        if (MODEL != 1) {
+            // Eq. (collision_VM) / (collision_NVM) + noise; Eq. (streaming)
+            thn = atan2f(ss, sc) + S.omega_step + S.eta_pi * (2.0f * u0 - 1.0f);
+            __sincosf(thn, &sn, &cn);
+            dX = __float2int_rn(S.kx * cn);
+            dY = __float2int_rn(S.ky * sn);
+        } else {
+            // Eq. (Langevin_dynamics), one Euler-Maruyama step
+            const float u1 = u01f(c4[1]);
+            const float h = S.wlen > 0 ? S.wtab[min(nb, S.wlen - 1)]
+                                       : (S.weight ? 1.0f : 1.0f / (1.0f + (float)nb));
+            // sum_j sin(o (theta_j - theta_i)) from the exact sums (units 2^-22 x 2^-22)
+            const float tsum = ((float)__float_as_int(pi.z) * ss - (float)__float_as_int(pi.w) * sc) *
+                               (1.0f / (kFixNbF * kFixNbF));
+            const float gz = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
+            thn = thi + S.gamma_dt * h * tsum + S.omega_step + S.noise_amp * gz;
+            float co, so;
+            __sincosf(thi, &so, &co);    // streaming direction theta(t), |theta| <= pi
+            dX = __float2int_rn(S.kx * co);
+            dY = __float2int_rn(S.ky * so);
+            cn = 0.f;
+            sn = 0.f;
+        }
+        // boundary rule (Sec. 2.4) in exact fixed point
+        const int TWs = tw << S.sx, THs = th << S.sy;
+        int Xn = X + dX, Yn = Y + dY;
+        int dtx = O.tx, dty = O.ty, twd = tw, thd = th;
+        bool fx = false, fy = false;
+        if (Xn < 0) {
+            if (S.bx && O.tx == 0) { Xn = -Xn; fx = true; }
+            else { dtx = O.tx > 0 ? O.tx - 1 : S.ntx - 1; twd = O.twL; Xn += O.twL << S.sx; }
+        } else if (Xn >= TWs) {
+            if (S.bx && O.tx == S.ntx - 1) {
+                if (Xn == TWs) Xn = TWs - 1; else { Xn = TWs - (Xn - TWs); fx = true; }
+            } else { dtx = O.tx < S.ntx - 1 ? O.tx + 1 : 0; twd = O.twR; Xn -= TWs; }
+        }
+        if (Yn < 0) {
+            if (S.by && O.ty == 0) { Yn = -Yn; fy = true; }
+            else { dty = O.ty > 0 ? O.ty - 1 : S.nty - 1; thd = O.thD; Yn += O.thD << S.sy; }
+        } else if (Yn >= THs) {
+            if (S.by && O.ty == S.nty - 1) {
+                if (Yn == THs) Yn = THs - 1; else { Yn = THs - (Yn - THs); fy = true; }
+            } else { dty = O.ty < S.nty - 1 ? O.ty + 1 : 0; thd = O.thU; Yn -= THs; }
+        }
+        if (fx) { thn = AAP_PI_F - thn; cn = -cn; }
+        if (fy) { thn = -thn; sn = -sn; }
+        if (thn >= AAP_PI_F || thn < -AAP_PI_F)
+            thn -= AAP_2PI_F * floorf((thn + AAP_PI_F) * (1.0f / AAP_2PI_F));
+        if (MODEL == 1) __sincosf(thn, &sn, &cn);
+        if (!isfinite(thn)) atomicOr(S.err, ERR_NAN);
+        dtile = dty * S.ntx + dtx;
+        region = region_of(Xn >> S.sx, Yn >> S.sy, twd, thd);
+        rec = make_int4(Xn, Yn, __float_as_int(thn), (int)id);
+        acc.c += __float2int_rn(cn * kFixStepF);
+        acc.s += __float2int_rn(sn * kFixStepF);
+        acc.c2 += __float2int_rn(fmaf(cn, cn, -sn * sn) * kFixStepF);
+        acc.s2 += __float2int_rn(2.0f * cn * sn * kFixStepF);
+        acc.n += nb;
+        if (S.nbr_out && id < (unsigned long long)S.n) S.nbr_out[id] = nb;
+    }
+    warp_insert(S, nxt, act, dtile, region, rec);
+}
+
+}  // namespace
+
+__host__ __device__ size_t pipe_smem_bytes(int cap, int cap_own, int nce_max, int hist_words)
+{
+    return 4 * (size_t)cap * 16 + 2 * (size_t)cap_own * 16 + 2 * (size_t)round_up(nce_max + 1, 4) * 4 +
+           2 * (size_t)round_up(cap_own, 8) * 2 + 2 * (size_t)round_up(cap, 8) * 2 +
+           (size_t)round_up(nce_max, 4) * 4 + (size_t)(kMaxTile + 4) * 4 + (size_t)round_up(hist_words, 4) * 4;
+}
+
+// The pipelined step of one system with one species (any model): one block
+// of kPipeThreads threads per SM.
+template <int MODEL, int NSORT>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce_max, int hist_words,
+            int *dense_list, unsigned char *scratch, size_t scratch_per_block, int scratch_cap, int spill_list_cap)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ PipeShared sh;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NS = NSORT * 32;                          // sort threads
+    constexpr int NU = kPipeWarps - 1 - NSORT;              // update warps
+    {
+        const int words = (int)(sizeof(Sys) / 4);
+        const int *src = reinterpret_cast<const int *>(sys);
+        int *dst = reinterpret_cast<int *>(&sh.S);
+        for (int i = tid; i < words; i += kPipeThreads) dst[i] = src[i];
+    }
+    PipeBufs B;
+    carve_pipe(B, smem, cap, cap_own, nce_max);
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh.bar_raw_full[b], 1);
+            mbar_init(&sh.bar_raw_empty[b], 1);
+            mbar_init(&sh.bar_full[b], 1);
+            mbar_init(&sh.bar_empty[b], NU);
+            sh.issued[b] = 0;
+            sh.taken[b] = 0;
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < nce_max; i += kPipeThreads) B.hist[i] = 0;
+    for (int i = tid; i < hist_words; i += kPipeThreads) B.mhist[i] = 0;
+    if (tid == 0) sh.flag = *((volatile int *)sys->err) & ERR_TIMEOUT;
+    __syncthreads();
+    // after a wait has run out the handle is unusable: later steps do nothing
+    // (so that a queue of steps cannot each wait out their bounds)
+    if (sh.flag) return;
+    const Sys &S = sh.S;
+    const long long step = ctl->step;
+    const int cur = (int)(step & 1);
+    const int total = S.ntiles;
+    const bool measure = step < S.meas_until;
+    Acc acc = {0, 0, 0, 0, 0};
+    unsigned char *mine = scratch + scratch_per_block * blockIdx.x;
+
+    if (warp == 0) {
+        // ---------------------------------------------------- copy warp --
+        int *spill_e = reinterpret_cast<int *>(mine);
+        unsigned kpar = 0, used = 0;       // per raw buffer: parity of its fills, filled before
+        int r = 0;
+        int g = 0;
+        if (lane == 0) g = atomicAdd(&ctl->tile_next, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        for (;;) {
+            // the following tile, claimed now so that its round trip overlaps this one's setup
+            int gn = 0;
+            if (g < total && lane == 0) gn = atomicAdd(&ctl->tile_next, 1);
+            // the raw buffer must be free (its previous tile sorted)
+            if (((used >> r) & 1u) && !warp_wait(&sh.bar_raw_empty[r], ((kpar >> r) & 1u) ^ 1u, S.err)) break;
+            RawMeta &M = sh.raw[r];
+            if (g >= total) {
+                if (lane == 0) {
+                    M.tile = -1;
+                    mbar_arrive(&sh.bar_raw_full[r]);
+                }
+                break;
+            }
+            if (!copy_setup(sh, g, cur, M, cap, cap_own, spill_e)) {
+                // done by the whole block after the pipeline
+                if (lane == 0) {
+                    const int j = atomicAdd(&ctl->dense_count, 1);
+                    dense_list[j] = g + 1;
+                }
+                g = __shfl_sync(0xffffffffu, gn, 0);
+                continue;
+            }
+            int4 *R = B.raw(r);
+            // spilled records by plain loads, after the segments
+            for (int j = lane; j < M.n_spill; j += 32) R[M.m_seg + j] = S.spill_rec[cur][spill_e[j]];
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                sh.issued[r] += 1;
+                mbar_arrive_tx(&sh.bar_raw_full[r], (unsigned)M.m_seg * 16u);
+            }
+            __syncwarp();
+            if (lane < kSegs) {
+                const int c = M.segpre[lane + 1] - M.segpre[lane];
+                if (c > 0) bulk_copy(R + M.segpre[lane], sh.src[lane], (unsigned)c * 16u, &sh.bar_raw_full[r]);
+            }
+            __syncwarp();
+            kpar ^= 1u << r;
+            used |= 1u << r;
+            r ^= 1;
+            g = __shfl_sync(0xffffffffu, gn, 0);
+        }
+    } else if (warp <= NSORT) {
+        // --------------------------------------------------- sort warps --
+        const int st = tid - 32;
+        unsigned rpar = 0, opar = 0, oused = 0;
+        int r = 0, b = 0;
+        for (;;) {
+            bool ok = mbar_wait(&sh.bar_raw_full[r], (rpar >> r) & 1u, S.err);
+            if (!sort_sync_and(NS, ok)) break;
+            rpar ^= 1u << r;
+            const bool end = sh.raw[r].tile < 0;
+            if (!end) sort_map(sh, B, r, st, NS);
+            // the output buffer must be free (its previous tile updated)
+            ok = !((oused >> b) & 1u) || mbar_wait(&sh.bar_empty[b], ((opar >> b) & 1u) ^ 1u, S.err);
+            if (!sort_sync_and(NS, ok)) break;
+            if (end) {
+                if (st == 0) {
+                    sh.out[b].tile = -1;
+                    mbar_arrive(&sh.bar_full[b]);
+                }
+                break;
+            }
+            sort_order<MODEL>(sh, B, r, b, st, NS, cap_own);
+            sort_sync(NS);
+            if (st == 0) {
+                sh.taken[r] += 1;
+                mbar_arrive(&sh.bar_raw_empty[r]);
+                mbar_arrive(&sh.bar_full[b]);
+            }
+            opar ^= 1u << b;
+            oused |= 1u << b;
+            r ^= 1;
+            b ^= 1;
+        }
+    } else {
+        // ------------------------------------------------- update warps --
+        unsigned fpar = 0;
+        int b = 0;
+        for (;;) {
+            if (!warp_wait(&sh.bar_full[b], (fpar >> b) & 1u, S.err)) break;
+            fpar ^= 1u << b;
+            const OutMeta &O = sh.out[b];
+            if (O.tile < 0) break;
+            const float4 *P = B.P(b);
+            const int *cst = B.cstart(b);
+            const int4 *OWN = B.own(b);
+            const unsigned short *OQ = B.ownq(b);
+            for (;;) {
+                int c = 0;
+                if (lane == 0) c = atomicAdd(&sh.chunk[b], 1);
+                c = __shfl_sync(0xffffffffu, c, 0);
+                const int o0 = c * 32;
+                if (o0 >= O.n_own) break;
+                update_one<MODEL>(S, O, P, cst, OWN, OQ, o0 + lane, step, measure, B.mhist, acc);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.bar_empty[b]);
+            b ^= 1;
+        }
+    }
+    __syncthreads();
+    // copies still in flight (only after a wait ran out): let them land
+    if (tid == 0) {
+        for (int r = 0; r < 2; ++r)
+            if (sh.issued[r] > sh.taken[r]) mbar_wait(&sh.bar_raw_full[r], (unsigned)(sh.issued[r] - 1) & 1u, S.err);
+    }
+    // --- the block's sums -> the step's accumulators ----------------------
+    {
+        const long long a[5] = {acc.c, acc.s, acc.n, acc.c2, acc.s2};
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const long long v = warp_sum_ll(a[k]);
+            if (lane == 0) sh.red[k][warp] = v;
+        }
+    }
+    __syncthreads();
+    if (tid < 5) {
+        long long v = 0;
+        for (int w = 0; w < kPipeWarps; ++w) v += sh.red[tid][w];
+        unsigned long long *slot = S.acc + ((size_t)cur * kAccSlots + (blockIdx.x & (kAccSlots - 1))) * kAccWords;
+        atomicAdd(slot + tid, (unsigned long long)v);
+    }
+    if (measure) {
+        for (int i = tid; i < S.bins_theta + S.bins_nbr; i += kPipeThreads)
+            if (B.mhist[i]) atomicAdd(S.hist + i, (unsigned long long)B.mhist[i]);
+    }
+    __syncthreads();
+
+    // --- tiles too large for the pipeline's buffers: the whole block, with
+    //     the shared staging area or the block's global scratch ------------
+    __shared__ TileCtx T;
+    const size_t tbytes = table_bytes(nce_max, hist_words);
+    const size_t dyn = pipe_smem_bytes(cap, cap_own, nce_max, hist_words);
+    // stage_bytes(a) <= 41 a + 18: the staging area and the tables fit in dyn
+    const int as_cap = (int)(((dyn - tbytes - 256) / 41) & ~63);
+    Stage As;
+    carve_stage(As, smem, as_cap);
+    Tables tb;
+    carve_tables(tb, smem + stage_bytes(as_cap), nce_max);
+    Stage Ag;
+    carve_stage(Ag, mine, scratch_cap);
+    int *spill_e = (int *)(mine + stage_bytes(scratch_cap));
+    unsigned char *spill_s = (unsigned char *)(spill_e + spill_list_cap);
+    bool first = true;
+    for (;;) {
+        if (tid == 0) {
+            int got = -1;
+            int d = *((volatile int *)&ctl->dense_next);
+            while (d < *((volatile int *)&ctl->dense_count)) {
+                const int prev = atomicCAS(&ctl->dense_next, d, d + 1);
+                if (prev == d) {
+                    // the entry is written right after its index was taken
+                    const long long t0 = clock64();
+                    int v;
+                    while ((v = *((volatile int *)&dense_list[d])) == 0) {
+                        if (clock64() - t0 > kPipeWaitCycles) {
+                            atomicOr(S.err, ERR_TIMEOUT);
+                            break;
+                        }
+                    }
+                    dense_list[d] = 0;
+                    got = v - 1;
+                    break;
+                }
+                d = prev;
+            }
+            sh.dense_tile = got;
+        }
+        __syncthreads();
+        const int g = sh.dense_tile;
+        if (g < 0) break;
+        if (first) {
+            const int words = (int)(sizeof(Sys) / 4);
+            const int *src = reinterpret_cast<const int *>(&sh.S);
+            int *dst = reinterpret_cast<int *>(&T.S);
+            for (int i = tid; i < words; i += kPipeThreads) dst[i] = src[i];
+            first = false;
+        }
+        if (tid == 0) {
+            T.sysi = 0;
+            T.tile = g;
+            T.pf_tile = -1;
+            T.total = total;
+            T.nsys = 1;
+            T.tile_base = nullptr;
+            T.next = total;
+        }
+        __syncthreads();
+        tile_setup<kPipeThreads>(T, tb, cur, nce_max, spill_e, spill_s, spill_list_cap);
+        if (T.m <= as_cap) {
+            tile_body<kPipeThreads, MODEL>(T, As, tb, step, spill_e, spill_s, total);
+        } else if (T.m <= scratch_cap) {
+            Stage Ah = Ag;
+            if ((size_t)T.m * sizeof(float4) <= stage_bytes(as_cap)) Ah.P = reinterpret_cast<float4 *>(smem);
+            tile_body<kPipeThreads, MODEL>(T, Ah, tb, step, spill_e, spill_s, total);
+        } else if (tid == 0) {
+            atomicOr(S.err, ERR_STAGE | ERR_LOST);
+        }
+        __syncthreads();
+    }
+}
+
+#ifndef AAP_PIPE_SORT_WARPS
+#define AAP_PIPE_SORT_WARPS 4
+#endif
+
+template <int MODEL>
+static cudaError_t static_pipe_t(size_t *bytes)
+{
+    cudaFuncAttributes a;
+    const cudaError_t e = cudaFuncGetAttributes(&a, k_step_pipe<MODEL, AAP_PIPE_SORT_WARPS>);
+    if (e == cudaSuccess) *bytes = a.sharedSizeBytes;
+    return e;
+}
+
+cudaError_t pipe_static_smem(int model, size_t *bytes)
+{
+    switch (model) {
+    case 0: return static_pipe_t<0>(bytes);
+    case 1: return static_pipe_t<1>(bytes);
+    case 2: return static_pipe_t<2>(bytes);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int MODEL>
+static cudaError_t config_pipe_t(size_t smem)
+{
+    // The limit belongs to the kernel, not to a handle: keep the largest size
+    // any handle of this process asked for, so that a handle with smaller
+    // buffers never breaks the launches of one with larger buffers.
+    static std::atomic<int> limit{0};
+    int want = (int)smem, prev = limit.load();
+    while (want > prev && !limit.compare_exchange_weak(prev, want)) {
+    }
+    return cudaFuncSetAttribute(k_step_pipe<MODEL, AAP_PIPE_SORT_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                std::max(want, limit.load()));
+}
+
+cudaError_t configure_pipe_kernel(int model, size_t smem)
+{
+    switch (model) {
+    case 0: return config_pipe_t<0>(smem);
+    case 1: return config_pipe_t<1>(smem);
+    case 2: return config_pipe_t<2>(smem);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int MODEL>
+static cudaError_t launch_pipe_t(const LaunchCfg &L, cudaStream_t st)
+{
+    const size_t smem = pipe_smem_bytes(L.pipe_cap, L.pipe_cap_own, L.nce_max, L.hist_words);
+    k_step_pipe<MODEL, AAP_PIPE_SORT_WARPS><<<L.pipe_grid, kPipeThreads, smem, st>>>(
+        L.sys, L.ctl, L.pipe_cap, L.pipe_cap_own, L.nce_max, L.hist_words, L.dense_list, L.scratch,
+        L.scratch_per_block, L.scratch_cap, L.spill_list_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_pipe(const LaunchCfg &L, cudaStream_t st)
+{
+    switch (L.model) {
+    case 0: return launch_pipe_t<0>(L, st);
+    case 1: return launch_pipe_t<1>(L, st);
+    case 2: return launch_pipe_t<2>(L, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace aapk

@@ -178,12 +178,18 @@ def test_deterministic_and_resume_bitwise(lib):
         A.aap_destroy(h2)
 
 
-def test_handles_of_different_staging_sizes_coexist(lib):
+@pytest.mark.parametrize("threads", [512, 0])
+def test_handles_of_different_staging_sizes_coexist(lib, threads):
     """A dense system (large shared-memory staging) keeps stepping after a
     sparse one (small staging) was created, and its trajectory is the one it
-    has alone: the kernel's shared-memory limit is a per-process maximum."""
-    dense = params(n=40000, lx=100.0, ly=100.0, eta=0.3, seed=41)       # rho = 4
-    sparse = params(n=2000, lx=60.0, ly=60.0, eta=0.3, seed=42)         # rho = 0.56
+    has alone: the kernel's shared-memory limit is a per-process maximum.
+    threads = 512: the whole-block kernel, whose staging follows the density;
+    0: the pipelined kernel, whose buffers follow the tile shape (the sparse
+    system's tiles are smaller here, so its launch asks for a different
+    amount of shared memory)."""
+    dense = params(n=40000, lx=100.0, ly=100.0, eta=0.3, seed=41, threads=threads)       # rho = 4
+    sparse = params(n=2000, lx=60.0, ly=60.0, eta=0.3, seed=42, threads=threads,         # rho = 0.56
+                    tile_w=0 if threads else 12, tile_h=0 if threads else 12)
     ref = A.aap_create(dense)
     try:
         A.aap_step(ref, 10)
@@ -193,7 +199,11 @@ def test_handles_of_different_staging_sizes_coexist(lib):
     h1 = A.aap_create(dense)
     h2 = A.aap_create(sparse)
     try:
-        assert A.aap_get_layout(h1).stage_cap > A.aap_get_layout(h2).stage_cap
+        l1, l2 = A.aap_get_layout(h1), A.aap_get_layout(h2)
+        if threads:
+            assert l1.stage_cap > l2.stage_cap
+        else:
+            assert l1.threads == l2.threads == 1024
         A.aap_step(h2, 5)
         A.aap_step(h1, 10)
         for u, v in zip(A.aap_get_state(h1, dense.n), want):
