@@ -1218,6 +1218,11 @@ namespace aapk {
 cudaError_t read_phase_times(unsigned long long *out16);
 }
 #endif
+#ifdef AAP_PIPE_TIMING
+namespace aapk {
+cudaError_t read_pipe_times(unsigned long long *out16);
+}
+#endif
 
 namespace {
 constexpr char kSaveMagic[8] = {'A', 'A', 'P', 'S', 'A', 'V', 'E', '1'};
@@ -1904,6 +1909,15 @@ int aap_get_layout(aap_handle *h, aap_layout *out)
     out->cell_y = h->csy;
     return AAP_OK;
 }
+
+#ifdef AAP_PIPE_TIMING
+// Instrumented builds only: cycles per role of the pipelined step kernel.
+int aap_debug_pipe_times(unsigned long long *out16)
+{
+    AAP_CK(aapk::read_pipe_times(out16));
+    return AAP_OK;
+}
+#endif
 
 #ifdef AAP_PHASE_TIMING
 // Instrumented builds only: cycles per step-kernel phase summed over blocks.

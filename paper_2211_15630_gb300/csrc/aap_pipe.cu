@@ -54,14 +54,39 @@ constexpr int kPipeWarps = kPipeThreads / 32;
 constexpr int kPipeMaxChunks = kPipeMaxStage / 32 + 1;
 constexpr long long kPipeWaitCycles = 4000000000ll;    // about 2 s at 2 GHz
 
+}  // namespace
+
+// Optional per-role timing (tracing aid, compiled out unless AAP_PIPE_TIMING
+// is defined): SM cycles each role spends waiting and working, summed over
+// warps and blocks.  Slots: 0 copy total, 1 copy waiting, 2 copy setup,
+// 3 sort waiting for records, 4 sort waiting for a free buffer, 5 sort map,
+// 6 sort order, 7 update waiting, 8 update working, 9 whole-block tiles,
+// 10 tiles through the pipeline, 11 whole-block tiles, 12 kernel per block.
+#ifdef AAP_PIPE_TIMING
+__device__ unsigned long long g_pipe_t[16];
+#define PT_NOW() clock64()
+#define PT_ADD(i, v) atomicAdd(&g_pipe_t[i], (unsigned long long)(v))
+cudaError_t read_pipe_times(unsigned long long *out16)
+{
+    return cudaMemcpyFromSymbol(out16, g_pipe_t, sizeof(unsigned long long) * 16);
+}
+#else
+#define PT_NOW() 0ll
+#define PT_ADD(i, v) do { } while (0)
+#endif
+
+namespace {
+
 // Segment maps and counts of one staged tile, written by the copy warp.
 struct RawMeta {
     int tile;                   // tile index, -1: no more tiles
     int m, m_seg, n_spill, n_own;
     int tx, ty, tw, th, twL, twR, thD, thU;
     int segpre[kSegs + 1];
-    int ax[kSegs], ay[kSegs], cx[kSegs], cy[kSegs], flip[kSegs];
-    long long bx[kSegs], by[kSegs];
+    // map of segment s into the extended frame: x = offset of X (mod 2^32),
+    // y = offset of Y, z = 2 (cx + 1) + (mirrored in x), w = 2 (cy + 1) +
+    // (mirrored in y); a mirrored axis negates the coordinate first
+    int4 map[kSegs];
     unsigned char segc[kPipeMaxChunks];     // segment of staged index 32 i
     unsigned char spill_seg[kPipeMaxSpill]; // segment of staged spill record j
 };
@@ -162,9 +187,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     const long long t0 = clock64();
     for (;;) {
         unsigned done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        // the hint lets the hardware suspend the warp (up to 0.1 ms) instead of
+        // spinning on issue slots the working warps need
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}\n"
-                     : "=r"(done) : "r"(sa(bar)), "r"(parity) : "memory");
+                     : "=r"(done) : "r"(sa(bar)), "r"(parity), "r"(100000u) : "memory");
         if (done) return true;
         if (clock64() - t0 > kPipeWaitCycles) {
             atomicOr(err, ERR_TIMEOUT);
@@ -212,7 +239,7 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned b
 // spill entry of staged spill record j.  Returns false (warp-uniform) when the
 // tile does not fit the pipeline's buffers.
 __device__ __forceinline__ bool copy_setup(PipeShared &sh, int g, int cur, RawMeta &M, int cap, int cap_own,
-                                           int *spill_e)
+                                           int nsp, int *spill_e)
 {
     const Sys &S = sh.S;
     const int lane = threadIdx.x & 31;
@@ -223,8 +250,7 @@ __device__ __forceinline__ bool copy_setup(PipeShared &sh, int g, int cur, RawMe
     const int incl = warp_incl_scan(c);
     const int m_seg = __shfl_sync(0xffffffffu, incl, kSegs - 1);
     const int own_seg = __shfl_sync(0xffffffffu, incl, 8);
-    // particles parked in the spill list for one of the tile's segments
-    const int nsp = min(*((volatile int *)&S.spill_cnt[cur]), S.spill_cap);
+    // particles parked in the spill list (nsp of them) for one of the tile's segments
     int n_spill = 0, n_own_spill = 0;
     if (nsp > 0) {
         const int mt = lane < kSegs ? sg.tile : -1, mr = lane < kSegs ? sg.region : -1;
@@ -251,13 +277,9 @@ __device__ __forceinline__ bool copy_setup(PipeShared &sh, int g, int cur, RawMe
     if (m > cap || n_own > cap_own || n_spill > kPipeMaxSpill) return false;
     if (lane < kSegs) {
         M.segpre[lane] = incl - c;
-        M.ax[lane] = sg.ax;
-        M.ay[lane] = sg.ay;
-        M.cx[lane] = sg.cx;
-        M.cy[lane] = sg.cy;
-        M.bx[lane] = sg.bx;
-        M.by[lane] = sg.by;
-        M.flip[lane] = sg.flip;
+        // the mapped coordinate fits int32, so its offset is kept mod 2^32
+        M.map[lane] = make_int4((int)(unsigned)(unsigned long long)sg.bx, (int)(unsigned)(unsigned long long)sg.by,
+                                2 * (sg.cx + 1) + (sg.ax < 0), 2 * (sg.cy + 1) + (sg.ay < 0));
         sh.src[lane] = sg.base;
     }
     if (lane == 0) {
@@ -304,16 +326,20 @@ __device__ __forceinline__ void sort_map(PipeShared &sh, const PipeBufs &B, int 
             s = M.spill_seg[k - m_seg];
         }
         const int4 rr = R[k];
-        const int ax = M.ax[s], ay = M.ay[s];
+        const int4 g = M.map[s];
+        const int mx = -(g.z & 1), my = -(g.w & 1);       // all ones where the axis is mirrored
         const int lx = rr.x >> S.sx, ly = rr.y >> S.sy;
-        int ex = ax * lx + M.cx[s] + 1, ey = ay * ly + M.cy[s] + 1;
+        int ex = ((lx ^ mx) - mx) + (g.z >> 1), ey = ((ly ^ my) - my) + (g.w >> 1);
         if ((unsigned)ex >= (unsigned)W2 || (unsigned)ey >= (unsigned)H2) {
             atomicOr(S.err, ERR_BOUNDS);
             ex = min(max(ex, 0), W2 - 1);
             ey = min(max(ey, 0), H2 - 1);
         }
-        R[k] = make_int4((int)(ax * (long long)rr.x + M.bx[s]), (int)(ay * (long long)rr.y + M.by[s]), rr.z, rr.w);
-        B.cellw[k] = (unsigned short)((M.flip[s] << 14) | (ey << 7) | ex);
+        // X_ext = a X + b in 32-bit wrapping arithmetic (the result fits int32)
+        const unsigned Xe = ((unsigned)rr.x ^ (unsigned)mx) - (unsigned)mx + (unsigned)g.x;
+        const unsigned Ye = ((unsigned)rr.y ^ (unsigned)my) - (unsigned)my + (unsigned)g.y;
+        R[k] = make_int4((int)Xe, (int)Ye, rr.z, rr.w);
+        B.cellw[k] = (unsigned short)((((g.z & 1) | ((g.w & 1) << 1)) << 14) | (ey << 7) | ex);
         B.slotw[k] = (unsigned short)atomicAdd(&B.hist[ey * W2 + ex], 1);
     }
 }
@@ -567,6 +593,8 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ PipeShared sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long tk0 = PT_NOW();
+    (void)tk0;
     constexpr int NS = NSORT * 32;                          // sort threads
     constexpr int NU = kPipeWarps - 1 - NSORT;              // update warps
     {
@@ -606,17 +634,22 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
     if (warp == 0) {
         // ---------------------------------------------------- copy warp --
         int *spill_e = reinterpret_cast<int *>(mine);
+        // the spill list of the current buffer is final during this step
+        const int nsp = min(*((volatile int *)&S.spill_cnt[cur]), S.spill_cap);
         unsigned kpar = 0, used = 0;       // per raw buffer: parity of its fills, filled before
         int r = 0;
         int g = 0;
         if (lane == 0) g = atomicAdd(&ctl->tile_next, 1);
         g = __shfl_sync(0xffffffffu, g, 0);
+        const long long tc0 = PT_NOW();
         for (;;) {
             // the following tile, claimed now so that its round trip overlaps this one's setup
             int gn = 0;
             if (g < total && lane == 0) gn = atomicAdd(&ctl->tile_next, 1);
             // the raw buffer must be free (its previous tile sorted)
+            const long long tw0 = PT_NOW();
             if (((used >> r) & 1u) && !warp_wait(&sh.bar_raw_empty[r], ((kpar >> r) & 1u) ^ 1u, S.err)) break;
+            if (lane == 0) PT_ADD(1, PT_NOW() - tw0);
             RawMeta &M = sh.raw[r];
             if (g >= total) {
                 if (lane == 0) {
@@ -625,7 +658,10 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                 }
                 break;
             }
-            if (!copy_setup(sh, g, cur, M, cap, cap_own, spill_e)) {
+            const long long ts0 = PT_NOW();
+            const bool fits = copy_setup(sh, g, cur, M, cap, cap_own, nsp, spill_e);
+            if (lane == 0) PT_ADD(2, PT_NOW() - ts0);
+            if (!fits) {
                 // done by the whole block after the pipeline
                 if (lane == 0) {
                     const int j = atomicAdd(&ctl->dense_count, 1);
@@ -654,20 +690,27 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             r ^= 1;
             g = __shfl_sync(0xffffffffu, gn, 0);
         }
+        if (lane == 0) PT_ADD(0, PT_NOW() - tc0);
     } else if (warp <= NSORT) {
         // --------------------------------------------------- sort warps --
         const int st = tid - 32;
         unsigned rpar = 0, opar = 0, oused = 0;
         int r = 0, b = 0;
         for (;;) {
+            long long t0 = PT_NOW();
             bool ok = mbar_wait(&sh.bar_raw_full[r], (rpar >> r) & 1u, S.err);
             if (!sort_sync_and(NS, ok)) break;
+            if (st == 0) PT_ADD(3, PT_NOW() - t0);
+            t0 = PT_NOW();
             rpar ^= 1u << r;
             const bool end = sh.raw[r].tile < 0;
             if (!end) sort_map(sh, B, r, st, NS);
             // the output buffer must be free (its previous tile updated)
+            if (st == 0) PT_ADD(5, PT_NOW() - t0);
+            t0 = PT_NOW();
             ok = !((oused >> b) & 1u) || mbar_wait(&sh.bar_empty[b], ((opar >> b) & 1u) ^ 1u, S.err);
             if (!sort_sync_and(NS, ok)) break;
+            if (st == 0) PT_ADD(4, PT_NOW() - t0);
             if (end) {
                 if (st == 0) {
                     sh.out[b].tile = -1;
@@ -675,9 +718,12 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                 }
                 break;
             }
+            t0 = PT_NOW();
             sort_order<MODEL>(sh, B, r, b, st, NS, cap_own);
             sort_sync(NS);
             if (st == 0) {
+                PT_ADD(6, PT_NOW() - t0);
+                PT_ADD(10, 1);
                 sh.taken[r] += 1;
                 mbar_arrive(&sh.bar_raw_empty[r]);
                 mbar_arrive(&sh.bar_full[b]);
@@ -692,7 +738,10 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
         unsigned fpar = 0;
         int b = 0;
         for (;;) {
+            const long long t0 = PT_NOW();
             if (!warp_wait(&sh.bar_full[b], (fpar >> b) & 1u, S.err)) break;
+            const long long t1 = PT_NOW();
+            if (lane == 0) PT_ADD(7, t1 - t0);
             fpar ^= 1u << b;
             const OutMeta &O = sh.out[b];
             if (O.tile < 0) break;
@@ -709,7 +758,10 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                 update_one<MODEL>(S, O, P, cst, OWN, OQ, o0 + lane, step, measure, B.mhist, acc);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.bar_empty[b]);
+            if (lane == 0) {
+                mbar_arrive(&sh.bar_empty[b]);
+                PT_ADD(8, PT_NOW() - t1);
+            }
             b ^= 1;
         }
     }
@@ -757,6 +809,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
     int *spill_e = (int *)(mine + stage_bytes(scratch_cap));
     unsigned char *spill_s = (unsigned char *)(spill_e + spill_list_cap);
     bool first = true;
+    const long long td0 = PT_NOW();
     for (;;) {
         if (tid == 0) {
             int got = -1;
@@ -811,12 +864,17 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
         } else if (tid == 0) {
             atomicOr(S.err, ERR_STAGE | ERR_LOST);
         }
+        if (tid == 0) PT_ADD(11, 1);
         __syncthreads();
+    }
+    if (tid == 0) {
+        PT_ADD(9, PT_NOW() - td0);
+        PT_ADD(12, PT_NOW() - tk0);
     }
 }
 
 #ifndef AAP_PIPE_SORT_WARPS
-#define AAP_PIPE_SORT_WARPS 4
+#define AAP_PIPE_SORT_WARPS 8
 #endif
 
 template <int MODEL>
