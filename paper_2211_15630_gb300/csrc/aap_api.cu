@@ -320,13 +320,18 @@ int set_pipe(aap_handle *h)
     AAP_CK(aapk::pipe_static_smem(L.model, &stat));
     int cap = aapk::kPipeMaxStage;
     auto own_of = [](int c) { return aapk::round_up(c * 7 / 8, 64); };
-    while (cap >= 256 && aapk::pipe_smem_bytes(cap, own_of(cap), L.nce_max, L.hist_words) + stat > (size_t)optin)
+    L.pipe_nceh = (2 * h->hs.twmax + 4) * (h->hs.thmax + 2);
+    while (cap >= 256 && aapk::pipe_smem_bytes(cap, own_of(cap), L.pipe_nceh, L.hist_words) + stat > (size_t)optin)
         cap -= 64;
     if (cap < 256) return AAP_OK;
+    // the whole-block routine for oversized tiles reuses the same shared memory
+    if (aapk::step_smem_bytes(256, L.nce_max, L.hist_words) >
+        aapk::pipe_smem_bytes(cap, own_of(cap), L.pipe_nceh, L.hist_words))
+        return AAP_OK;
     L.pipe_cap = cap;
     L.pipe_cap_own = own_of(cap);
     L.pipe_grid = std::max(1, std::min(h->hs.ntiles, sm_count()));
-    AAP_CK(aapk::configure_pipe_kernel(L.model, aapk::pipe_smem_bytes(L.pipe_cap, L.pipe_cap_own, L.nce_max,
+    AAP_CK(aapk::configure_pipe_kernel(L.model, aapk::pipe_smem_bytes(L.pipe_cap, L.pipe_cap_own, L.pipe_nceh,
                                                                       L.hist_words)));
     L.pipe = 1;
     L.threads = 1024;

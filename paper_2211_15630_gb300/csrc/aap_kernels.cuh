@@ -29,6 +29,7 @@ struct LaunchCfg {
     // that do not fit go to dense_list (device [ntiles], zero between steps)
     int pipe;
     int pipe_cap, pipe_cap_own, pipe_grid;
+    int pipe_nceh;               // half cells (split along x) of the largest extended tile, (2 tw + 4)(th + 2)
     int *dense_list;
     // metric-free step (knn > 0): cell count, scan, scatter, k-nearest update
     int knn;
@@ -42,7 +43,7 @@ size_t step_smem_bytes(int stage_cap, int nce_max, int hist_words);
 cudaError_t configure_step_kernel(int model, int threads, size_t smem_bytes, int *blocks_per_sm);
 
 // Dynamic shared memory of the pipelined step kernel.
-__host__ __device__ size_t pipe_smem_bytes(int cap, int cap_own, int nce_max, int hist_words);
+__host__ __device__ size_t pipe_smem_bytes(int cap, int cap_own, int nceh, int hist_words);
 // Static shared memory of the pipelined step kernel of a model.
 cudaError_t pipe_static_smem(int model, size_t *bytes);
 // Set the dynamic shared-memory limit of the pipelined step kernel.

@@ -14,15 +14,19 @@
 //                          segment into one of two raw record buffers,
 //                          completing on that buffer's mbarrier;
 //   sort warps (NSORT)     map each staged record into the tile's extended
-//                          frame, histogram it by cell, prefix-scan the
-//                          histogram and place the records in cell order
-//                          (x, y and cos, sin as exact integers) into one of
-//                          two output buffers, with the tile's own particles
-//                          listed in cell order;
+//                          frame, histogram it by half cell (a cell split in
+//                          two along x), prefix-scan the histogram and place
+//                          the records in half-cell order (x, y and cos, sin
+//                          as exact integers) into one of two output buffers,
+//                          with the tile's own particles listed in that order;
 //   update warps (rest)    take chunks of 32 own particles from the ready
-//                          output buffer, sum their 3x3 cells (Eq. collision_VM
-//                          / collision_NVM, or the Langevin coupling sum of
-//                          Eq. Langevin_dynamics) in exact integers, draw
+//                          output buffer, sum over three rows of five half
+//                          cells (every point within R of a half cell lies in
+//                          that block, which covers 15/18 of the 3x3 cells;
+//                          Eq. collision_VM / collision_NVM, or the Langevin
+//                          coupling sum of Eq. Langevin_dynamics) in exact
+//                          integers, so the result is the 3x3 kernel's bit for
+//                          bit, draw
 //                          Philox noise, stream, apply the boundary rule and
 //                          scatter the new records into the next step's
 //                          regions.
@@ -51,7 +55,7 @@ namespace {
 
 constexpr int kPipeThreads = 1024;
 constexpr int kPipeWarps = kPipeThreads / 32;
-constexpr int kPipeMaxChunks = kPipeMaxStage / 32 + 1;
+constexpr int kPipeMaxChunks = 2 * kPipeMaxStage / 32 + 1;   // a wide tile spans both raw buffers
 constexpr long long kPipeWaitCycles = 4000000000ll;    // about 2 s at 2 GHz
 
 }  // namespace
@@ -60,8 +64,10 @@ constexpr long long kPipeWaitCycles = 4000000000ll;    // about 2 s at 2 GHz
 // is defined): SM cycles each role spends waiting and working, summed over
 // warps and blocks.  Slots: 0 copy total, 1 copy waiting, 2 copy setup,
 // 3 sort waiting for records, 4 sort waiting for a free buffer, 5 sort map,
-// 6 sort order, 7 update waiting, 8 update working, 9 whole-block tiles,
-// 10 tiles through the pipeline, 11 whole-block tiles, 12 kernel per block.
+// 6 sort order, 7 update waiting, 8 update working, 9 copy issuing the bulk copies,
+// 10 tiles through the pipeline, 11 whole-block tiles, 12 kernel per block,
+// 13 copy waiting for its next tile index, 14 copy planning, 15 copy spill
+// records and proxy fence.
 #ifdef AAP_PIPE_TIMING
 __device__ unsigned long long g_pipe_t[16];
 #define PT_NOW() clock64()
@@ -79,13 +85,15 @@ namespace {
 
 // Segment maps and counts of one staged tile, written by the copy warp.
 struct RawMeta {
-    int tile;                   // tile index, -1: no more tiles
+    int tile;                   // tile index, -1: no more tiles, -2: skip (the buffer holds part of a wide tile)
     int m, m_seg, n_spill, n_own;
+    int wide;                   // 1: the tile spans both raw buffers (staged from buffer 0's start)
     int tx, ty, tw, th, twL, twR, thD, thU;
     int segpre[kSegs + 1];
     // map of segment s into the extended frame: x = offset of X (mod 2^32),
-    // y = offset of Y, z = 2 (cx + 1) + (mirrored in x), w = 2 (cy + 1) +
-    // (mirrored in y); a mirrored axis negates the coordinate first
+    // y = offset of Y, z = 2 e + (mirrored in x) with e the extended
+    // half-cell column of source half-cell column 0, w = 2 (cy + 1) +
+    // (mirrored in y); a mirrored axis negates the local index first
     int4 map[kSegs];
     unsigned char segc[kPipeMaxChunks];     // segment of staged index 32 i
     unsigned char spill_seg[kPipeMaxSpill]; // segment of staged spill record j
@@ -93,16 +101,15 @@ struct RawMeta {
 
 // What the update warps need of a sorted tile.
 struct OutMeta {
-    int tile;                   // -1: no more tiles
-    int n_own, tx, ty, tw, th, W2, twL, twR, thD, thU;
-    int wide;                   // a cell holds enough particles for 512 candidates
+    int tile;                   // -1: no more tiles, -2: skip (the buffer holds part of a wide tile)
+    int n_own, tx, ty, tw, th, W2, twL, twR, thD, thU;   // W2: half cells per extended row, 2 tw + 4
+    int wide;                   // a half cell holds enough particles for 512 candidates
 };
 
 struct PipeShared {
     Sys S;
     RawMeta raw[2];
     OutMeta out[2];
-    const int4 *src[kSegs];     // copy warp: segment sources of the tile being set up
     int chunk[2];               // next chunk of 32 own particles, per output buffer
     int issued[2], taken[2];    // raw buffer fills issued by the copy warp / sorted
     int flag;                   // a previous step's wait ran out
@@ -119,18 +126,18 @@ struct PipeBufs {
     int4 *raw0;                 // [2][cap] staged records as copied; mapped in place by the sort warps
     float4 *P0;                 // [2][cap] records in cell order: x, y from the tile centre, cos, sin (int32, 2^-22)
     int4 *own0;                 // [2][cap_own] own particles in cell order: X, Y (tile frame), theta bits, id
-    int *cst0;                  // [2][cst_stride] cell starts in P
+    unsigned short *cst0;       // [2][cst_stride] half-cell starts in P
     unsigned short *oq0;        // [2][oq_stride] position in P of own particle o
-    unsigned short *cellw;      // sort scratch: flip << 14 | ey << 7 | ex of staged record k
-    unsigned short *slotw;      // arrival rank in its cell
-    int *hist;                  // [nce]
+    unsigned short *cellw;      // sort scratch: ey << 8 | ex (extended half cell) of staged record k
+    unsigned short *slotw;      // flip << 14 | arrival rank in its half cell
+    int *hist;                  // [nce] (half cells)
     int *rowoff;                // own index = position in P + rowoff[ey]
     int *mhist;                 // measured theta / |Omega| counts of the block
     int cap, cap_own, cst_stride, oq_stride;
     __device__ __forceinline__ int4 *raw(int b) const { return raw0 + b * cap; }
     __device__ __forceinline__ float4 *P(int b) const { return P0 + b * cap; }
     __device__ __forceinline__ int4 *own(int b) const { return own0 + b * cap_own; }
-    __device__ __forceinline__ int *cstart(int b) const { return cst0 + b * cst_stride; }
+    __device__ __forceinline__ unsigned short *cstart(int b) const { return cst0 + b * cst_stride; }
     __device__ __forceinline__ unsigned short *ownq(int b) const { return oq0 + b * oq_stride; }
 };
 
@@ -138,7 +145,7 @@ __device__ __forceinline__ void carve_pipe(PipeBufs &B, unsigned char *p, int ca
 {
     B.cap = cap;
     B.cap_own = cap_own;
-    B.cst_stride = round_up(nce + 1, 4);
+    B.cst_stride = round_up(nce + 1, 8);
     B.oq_stride = round_up(cap_own, 8);
     B.raw0 = (int4 *)p;
     p += (size_t)2 * cap * 16;
@@ -146,14 +153,14 @@ __device__ __forceinline__ void carve_pipe(PipeBufs &B, unsigned char *p, int ca
     p += (size_t)2 * cap * 16;
     B.own0 = (int4 *)p;
     p += (size_t)2 * cap_own * 16;
-    B.cst0 = (int *)p;
-    p += (size_t)2 * B.cst_stride * 4;
+    B.cst0 = (unsigned short *)p;
+    p += (size_t)2 * B.cst_stride * 2;
     B.oq0 = (unsigned short *)p;
     p += (size_t)2 * B.oq_stride * 2;
-    B.cellw = (unsigned short *)p;
-    p += (size_t)round_up(cap, 8) * 2;
+    B.cellw = (unsigned short *)p;              // sized for a wide tile (two buffers)
+    p += (size_t)round_up(2 * cap, 8) * 2;
     B.slotw = (unsigned short *)p;
-    p += (size_t)round_up(cap, 8) * 2;
+    p += (size_t)round_up(2 * cap, 8) * 2;
     B.hist = (int *)p;
     p += (size_t)round_up(nce, 4) * 4;
     B.rowoff = (int *)p;
@@ -234,26 +241,38 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned b
 }
 
 // -------------------------------------------------------------- copy warp --
-// Geometry, the 25 segments and the spill matches of tile g into M and
-// sh.src (all lanes of the copy warp).  spill_e (global scratch) receives the
-// spill entry of staged spill record j.  Returns false (warp-uniform) when the
-// tile does not fit the pipeline's buffers.
-__device__ __forceinline__ bool copy_setup(PipeShared &sh, int g, int cur, RawMeta &M, int cap, int cap_own,
-                                           int nsp, int *spill_e)
-{
-    const Sys &S = sh.S;
-    const int lane = threadIdx.x & 31;
-    const TileGeo G = tile_geo(S, g);
+// What the copy warp learns of a tile before it needs a raw buffer: the
+// geometry and, in lane s < 25, source segment s with its record count and
+// the inclusive prefix of the counts.
+struct CopyPlan {
+    TileGeo G;
     Seg sg;
-    if (lane < kSegs) sg = make_seg(S, G, lane, cur);
-    const int c = lane < kSegs ? sg.count : 0;
-    const int incl = warp_incl_scan(c);
-    const int m_seg = __shfl_sync(0xffffffffu, incl, kSegs - 1);
-    const int own_seg = __shfl_sync(0xffffffffu, incl, 8);
-    // particles parked in the spill list (nsp of them) for one of the tile's segments
-    int n_spill = 0, n_own_spill = 0;
+    int c, incl, m_seg, own_seg;
+};
+
+// Geometry and the 25 segments of tile g (all lanes of the copy warp; global
+// loads of the region counts, no shared-memory writes).
+__device__ __forceinline__ void copy_plan(const Sys &S, int g, int cur, CopyPlan &pl)
+{
+    const int lane = threadIdx.x & 31;
+    pl.G = tile_geo(S, g);
+    if (lane < kSegs) pl.sg = make_seg(S, pl.G, lane, cur);
+    pl.c = lane < kSegs ? pl.sg.count : 0;
+    pl.incl = warp_incl_scan(pl.c);
+    pl.m_seg = __shfl_sync(0xffffffffu, pl.incl, kSegs - 1);
+    pl.own_seg = __shfl_sync(0xffffffffu, pl.incl, 8);
+}
+
+// The planned tile's spill matches (nsp spilled records): spill_e / spill_s
+// (the copy warp's global scratch) receive the spill entry and the segment of
+// staged spill record j; n_spill and the own count follow.
+__device__ __forceinline__ void copy_spills(const Sys &S, const CopyPlan &pl, int cur, int nsp, int *spill_e,
+                                            unsigned char *spill_s, int &n_spill, int &n_own)
+{
+    const int lane = threadIdx.x & 31;
+    int ns = 0, nos = 0;
     if (nsp > 0) {
-        const int mt = lane < kSegs ? sg.tile : -1, mr = lane < kSegs ? sg.region : -1;
+        const int mt = lane < kSegs ? pl.sg.tile : -1, mr = lane < kSegs ? pl.sg.region : -1;
         for (int e0 = 0; e0 < nsp; e0 += 32) {
             const int e = e0 + lane;
             const int key = e < nsp ? S.spill_key[cur][e] : -1;
@@ -262,49 +281,61 @@ __device__ __forceinline__ bool copy_setup(PipeShared &sh, int g, int cur, RawMe
                 const int st = __shfl_sync(0xffffffffu, mt, s), sr = __shfl_sync(0xffffffffu, mr, s);
                 const bool hit = et == st && er == sr;
                 const unsigned bal = __ballot_sync(0xffffffffu, hit);
-                const int j = n_spill + __popc(bal & ((1u << lane) - 1u));
+                const int j = ns + __popc(bal & ((1u << lane) - 1u));
                 if (hit && j < kPipeMaxSpill) {
-                    M.spill_seg[j] = (unsigned char)s;
+                    spill_s[j] = (unsigned char)s;
                     spill_e[j] = e;
                 }
-                n_spill += __popc(bal);
-                if (s < 9) n_own_spill += __popc(bal);
+                ns += __popc(bal);
+                if (s < 9) nos += __popc(bal);
             }
         }
     }
-    const int m = m_seg + n_spill;
-    const int n_own = own_seg + n_own_spill;
-    if (m > cap || n_own > cap_own || n_spill > kPipeMaxSpill) return false;
+    __syncwarp();
+    n_spill = ns;
+    n_own = pl.own_seg + nos;
+}
+
+// The planned tile's meta into raw buffer meta M (the raw buffer, or both for
+// a wide tile, must be free).
+__device__ __forceinline__ void copy_commit(const CopyPlan &pl, int g, RawMeta &M, int n_spill, int n_own, int wide,
+                                            const unsigned char *spill_s)
+{
+    const int lane = threadIdx.x & 31;
+    const Seg &sg = pl.sg;
+    const int m_seg = pl.m_seg;
+    const int start = pl.incl - pl.c;                   // segment start (lanes < 25)
     if (lane < kSegs) {
-        M.segpre[lane] = incl - c;
-        // the mapped coordinate fits int32, so its offset is kept mod 2^32
+        M.segpre[lane] = start;
+        // the mapped coordinate fits int32, so its offset is kept mod 2^32;
+        // extended half-cell column of local half cell h: a h + 2 cx + (mirrored) + 2
+        const int mxr = sg.ax < 0;
         M.map[lane] = make_int4((int)(unsigned)(unsigned long long)sg.bx, (int)(unsigned)(unsigned long long)sg.by,
-                                2 * (sg.cx + 1) + (sg.ax < 0), 2 * (sg.cy + 1) + (sg.ay < 0));
-        sh.src[lane] = sg.base;
+                                2 * (2 * sg.cx + mxr + 2) + mxr, 2 * (sg.cy + 1) + (sg.ay < 0));
     }
+    for (int j = lane; j < n_spill; j += 32) M.spill_seg[j] = spill_s[j];
     if (lane == 0) {
         M.segpre[kSegs] = m_seg;
         M.tile = g;
-        M.m = m;
+        M.m = m_seg + n_spill;
         M.m_seg = m_seg;
         M.n_spill = n_spill;
         M.n_own = n_own;
-        M.tx = G.tx; M.ty = G.ty; M.tw = G.tw; M.th = G.th;
-        M.twL = G.twL; M.twR = G.twR; M.thD = G.thD; M.thU = G.thU;
+        M.wide = wide;
+        M.tx = pl.G.tx; M.ty = pl.G.ty; M.tw = pl.G.tw; M.th = pl.G.th;
+        M.twL = pl.G.twL; M.twR = pl.G.twR; M.thD = pl.G.thD; M.thU = pl.G.thU;
+    }
+    // segment of every 32nd staged index: the last segment starting at or
+    // before it (segment starts taken from the lanes, no shared-memory reads)
+    const int sp = lane < kSegs ? start : 0x7fffffff;
+    for (int i0 = 0; i0 * 32 < m_seg; i0 += 32) {
+        const int k = (i0 + lane) * 32;
+        int n = 0;
+#pragma unroll
+        for (int s = 0; s < kSegs; ++s) n += __shfl_sync(0xffffffffu, sp, s) <= k;
+        if (k < m_seg) M.segc[i0 + lane] = (unsigned char)(n - 1);
     }
     __syncwarp();
-    // segment of every 32nd staged index
-    for (int i = lane; i * 32 < m_seg; i += 32) {
-        const int k = i * 32;
-        int lo = 0, hi = kSegs;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (M.segpre[mid] <= k) lo = mid; else hi = mid;
-        }
-        M.segc[i] = (unsigned char)lo;
-    }
-    __syncwarp();
-    return true;
 }
 
 // ------------------------------------------------------------- sort warps --
@@ -315,7 +346,7 @@ __device__ __forceinline__ void sort_map(PipeShared &sh, const PipeBufs &B, int 
     const Sys &S = sh.S;
     const RawMeta &M = sh.raw[r];
     const int m = M.m, m_seg = M.m_seg;
-    const int W2 = M.tw + 2, H2 = M.th + 2;
+    const int W2 = 2 * M.tw + 4, H2 = M.th + 2;       // half cells per extended row, rows
     int4 *R = B.raw(r);
     for (int k = tid; k < m; k += NS) {
         int s;
@@ -328,7 +359,7 @@ __device__ __forceinline__ void sort_map(PipeShared &sh, const PipeBufs &B, int 
         const int4 rr = R[k];
         const int4 g = M.map[s];
         const int mx = -(g.z & 1), my = -(g.w & 1);       // all ones where the axis is mirrored
-        const int lx = rr.x >> S.sx, ly = rr.y >> S.sy;
+        const int lx = rr.x >> (S.sx - 1), ly = rr.y >> S.sy;
         int ex = ((lx ^ mx) - mx) + (g.z >> 1), ey = ((ly ^ my) - my) + (g.w >> 1);
         if ((unsigned)ex >= (unsigned)W2 || (unsigned)ey >= (unsigned)H2) {
             atomicOr(S.err, ERR_BOUNDS);
@@ -339,8 +370,8 @@ __device__ __forceinline__ void sort_map(PipeShared &sh, const PipeBufs &B, int 
         const unsigned Xe = ((unsigned)rr.x ^ (unsigned)mx) - (unsigned)mx + (unsigned)g.x;
         const unsigned Ye = ((unsigned)rr.y ^ (unsigned)my) - (unsigned)my + (unsigned)g.y;
         R[k] = make_int4((int)Xe, (int)Ye, rr.z, rr.w);
-        B.cellw[k] = (unsigned short)((((g.z & 1) | ((g.w & 1) << 1)) << 14) | (ey << 7) | ex);
-        B.slotw[k] = (unsigned short)atomicAdd(&B.hist[ey * W2 + ex], 1);
+        B.cellw[k] = (unsigned short)((ey << 8) | ex);
+        B.slotw[k] = (unsigned short)((((g.z & 1) | ((g.w & 1) << 1)) << 14) | atomicAdd(&B.hist[ey * W2 + ex], 1));
     }
 }
 
@@ -354,8 +385,8 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
     const Sys &S = sh.S;
     const RawMeta &M = sh.raw[r];
     const int m = M.m, tw = M.tw, th = M.th;
-    const int W2 = tw + 2, nce = W2 * (th + 2);
-    int *cst = B.cstart(b);
+    const int W2 = 2 * tw + 4, nce = W2 * (th + 2);     // half cells of the extended tile
+    unsigned short *cst = B.cstart(b);
     const int lane = tid & 31, w = tid >> 5, nw = NS >> 5;
     int maxc = 0;
     {
@@ -374,12 +405,12 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
             const int v = lane < nw ? sh.warp_tot[lane] : 0;
             const int wi = warp_incl_scan(v);
             if (lane < nw) sh.warp_tot[lane] = wi - v;
-            if (lane == nw - 1) cst[nce] = wi;
+            if (lane == nw - 1) cst[nce] = (unsigned short)wi;
         }
         sort_sync(NS);
         int run = incl - sum + sh.warp_tot[w];
         for (int i = b0; i < e0; ++i) {
-            cst[i] = run;
+            cst[i] = (unsigned short)run;
             run += B.hist[i];
             B.hist[i] = 0;
         }
@@ -395,9 +426,9 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
         for (int r0 = 0; r0 < th; r0 += 32) {
             const int rw = r0 + lane;
             int len = 0, first = 0;
-            if (rw < th) {
-                first = cst[(rw + 1) * W2 + 1];
-                len = cst[(rw + 1) * W2 + tw + 1] - first;
+            if (rw < th) {               // own half cells 2 .. 2 tw + 1 of row rw + 1
+                first = cst[(rw + 1) * W2 + 2];
+                len = cst[(rw + 1) * W2 + 2 * tw + 2] - first;
             }
             const int incl = warp_incl_scan(len);
             if (rw < th) B.rowoff[rw + 1] = carry + incl - len - first;
@@ -412,7 +443,7 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
             O.n_own = min(carry, cap_own);
             O.tx = M.tx; O.ty = M.ty; O.tw = tw; O.th = th; O.W2 = W2;
             O.twL = M.twL; O.twR = M.twR; O.thD = M.thD; O.thU = M.thU;
-            O.wide = 9 * mx >= 512;
+            O.wide = 15 * mx >= 512;
             sh.chunk[b] = 0;
             if (carry != M.n_own) atomicOr(S.err, ERR_BOUNDS);
         }
@@ -426,9 +457,9 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
     int4 *OWN = B.own(b);
     unsigned short *OQ = B.ownq(b);
     for (int k = tid; k < m; k += NS) {
-        const unsigned cf = B.cellw[k];
-        const int ex = cf & 127, ey = (cf >> 7) & 127;
-        const int q = cst[ey * W2 + ex] + B.slotw[k];
+        const unsigned cf = B.cellw[k], sl = B.slotw[k];
+        const int ex = cf & 255, ey = cf >> 8;
+        const int q = cst[ey * W2 + ex] + (sl & 0x3fff);
         const int4 rk = R[k];
         float thv = __int_as_float(rk.z);
         float sn, cs;
@@ -439,14 +470,14 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
             // |theta| <= pi: the hardware sine/cosine is within 2^-21.4 absolute
             __sincosf(thv, &sn, &cs);
         }
-        const int flip = cf >> 14;
+        const int flip = sl >> 14;
         if (flip & 1) {
             if (MODEL != 1 || (S.order & 1)) cs = -cs; else sn = -sn;
         }
         if (flip & 2) sn = -sn;
         P[q] = make_float4((float)(rk.x - xc) * S.ux, (float)(rk.y - yc) * S.uy,
                            __int_as_float(__float2int_rn(cs * kFixNbF)), __int_as_float(__float2int_rn(sn * kFixNbF)));
-        if (ex >= 1 && ex <= tw && ey >= 1 && ey <= th) {
+        if (ex >= 2 && ex < 2 * tw + 2 && ey >= 1 && ey <= th) {
             const int o = q + B.rowoff[ey];
             if (o < cap_own) {
                 OWN[o] = rk;
@@ -457,6 +488,43 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
 }
 
 // ----------------------------------------------------------- update warps --
+// The neighbour sum of one particle over three rows of five half cells,
+// each row contiguous in the half-cell order.  The particle itself is
+// included (it adds e^{i theta_i} to the VM/NVM sum and sin 0 to the
+// Langevin sum; cnt counts it).  The staged (cos, sin) are integers in units
+// of 2^-22, so the sums are exact and order-free; ACC is int below 512
+// candidates and long long beyond.
+template <int MODEL, typename ACC>
+__device__ __forceinline__ void neighbour_sum_h(const float4 *__restrict__ P, const unsigned short *cstart, int ec,
+                                                int W2, float4 pi, float r2, ACC &sc, ACC &ss, int &cnt)
+{
+    sc = 0;
+    ss = 0;
+    cnt = 0;
+    const float pcf = (float)__float_as_int(pi.z), psf = (float)__float_as_int(pi.w);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int c0 = ec + dy * W2 - 2;
+        const int a = cstart[c0], b = cstart[c0 + 5];
+#pragma unroll 4
+        for (int j = a; j < b; ++j) {
+            const float4 pj = P[j];
+            const float dx = pj.x - pi.x, dyy = pj.y - pi.y;
+            const float d2 = fmaf(dx, dx, dyy * dyy);
+            if (d2 <= r2) {
+                int cj = __float_as_int(pj.z), sj = __float_as_int(pj.w);
+                if (MODEL == 2 && fmaf(pcf, (float)cj, psf * (float)sj) < 0.f) {
+                    cj = -cj;                         // Eq. (collision_NVM): the reversed direction
+                    sj = -sj;
+                }
+                sc += cj;
+                ss += sj;
+                ++cnt;
+            }
+        }
+    }
+}
+
 struct Acc {
     long long c, s, n, c2, s2;
 };
@@ -465,8 +533,8 @@ struct Acc {
 // of the warp must call (the scatter is warp-aggregated).
 template <int MODEL>
 __device__ __forceinline__ void update_one(const Sys &S, const OutMeta &O, const float4 *__restrict__ P,
-                                           const int *cstart, const int4 *OWN, const unsigned short *OQ, int o,
-                                           long long step, bool measure, int *mhist, Acc &acc)
+                                           const unsigned short *cstart, const int4 *OWN, const unsigned short *OQ,
+                                           int o, long long step, bool measure, int *mhist, Acc &acc)
 {
     const int nxt = (int)(step & 1) ^ 1;
     const bool act = o < O.n_own;
@@ -478,24 +546,24 @@ __device__ __forceinline__ void update_one(const Sys &S, const OutMeta &O, const
         const int X = rk.x, Y = rk.y;
         const float thi = __int_as_float(rk.z);
         const unsigned id = (unsigned)rk.w;
-        const int ec = ((Y >> S.sy) + 1) * W2 + (X >> S.sx) + 1;
+        const int ec = ((Y >> S.sy) + 1) * W2 + (X >> (S.sx - 1)) + 2;      // extended half cell
         const float4 pi = P[OQ[o]];
         float sc, ss;                    // neighbour sums in units of 2^-22
         int cnt;
         bool narrow = !O.wide;
         if (!narrow) {
-            const int ncand = cstart[ec - W2 + 2] - cstart[ec - W2 - 1] + cstart[ec + 2] - cstart[ec - 1] +
-                              cstart[ec + W2 + 2] - cstart[ec + W2 - 1];
+            const int ncand = cstart[ec - W2 + 3] - cstart[ec - W2 - 2] + cstart[ec + 3] - cstart[ec - 2] +
+                              cstart[ec + W2 + 3] - cstart[ec + W2 - 2];
             narrow = ncand < 512;
         }
         if (narrow) {
             int a, b;
-            neighbour_sum<MODEL, int>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
+            neighbour_sum_h<MODEL, int>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
             sc = (float)a;
             ss = (float)b;
         } else {
             long long a, b;
-            neighbour_sum<MODEL, long long>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
+            neighbour_sum_h<MODEL, long long>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
             sc = (float)a;
             ss = (float)b;
         }
@@ -576,18 +644,19 @@ __device__ __forceinline__ void update_one(const Sys &S, const OutMeta &O, const
 
 }  // namespace
 
-__host__ __device__ size_t pipe_smem_bytes(int cap, int cap_own, int nce_max, int hist_words)
+// nceh: half cells of the largest extended tile, (2 tw + 4)(th + 2).
+__host__ __device__ size_t pipe_smem_bytes(int cap, int cap_own, int nceh, int hist_words)
 {
-    return 4 * (size_t)cap * 16 + 2 * (size_t)cap_own * 16 + 2 * (size_t)round_up(nce_max + 1, 4) * 4 +
-           2 * (size_t)round_up(cap_own, 8) * 2 + 2 * (size_t)round_up(cap, 8) * 2 +
-           (size_t)round_up(nce_max, 4) * 4 + (size_t)(kMaxTile + 4) * 4 + (size_t)round_up(hist_words, 4) * 4;
+    return 4 * (size_t)cap * 16 + 2 * (size_t)cap_own * 16 + 2 * (size_t)round_up(nceh + 1, 8) * 2 +
+           2 * (size_t)round_up(cap_own, 8) * 2 + 2 * (size_t)round_up(2 * cap, 8) * 2 +
+           (size_t)round_up(nceh, 4) * 4 + (size_t)(kMaxTile + 4) * 4 + (size_t)round_up(hist_words, 4) * 4;
 }
 
 // The pipelined step of one system with one species (any model): one block
 // of kPipeThreads threads per SM.
 template <int MODEL, int NSORT>
 __global__ void __launch_bounds__(kPipeThreads, 1)
-k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce_max, int hist_words,
+k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nceh_max, int nce_max, int hist_words,
             int *dense_list, unsigned char *scratch, size_t scratch_per_block, int scratch_cap, int spill_list_cap)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -604,7 +673,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
         for (int i = tid; i < words; i += kPipeThreads) dst[i] = src[i];
     }
     PipeBufs B;
-    carve_pipe(B, smem, cap, cap_own, nce_max);
+    carve_pipe(B, smem, cap, cap_own, nceh_max);
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh.bar_raw_full[b], 1);
@@ -616,7 +685,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = tid; i < nce_max; i += kPipeThreads) B.hist[i] = 0;
+    for (int i = tid; i < nceh_max; i += kPipeThreads) B.hist[i] = 0;
     for (int i = tid; i < hist_words; i += kPipeThreads) B.mhist[i] = 0;
     if (tid == 0) sh.flag = *((volatile int *)sys->err) & ERR_TIMEOUT;
     __syncthreads();
@@ -633,7 +702,15 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
 
     if (warp == 0) {
         // ---------------------------------------------------- copy warp --
+        // Each tile is planned (geometry, segments, counts: global loads)
+        // while the sort warps still hold the raw buffer it will go to; only
+        // writing its meta and issuing its copies wait for that buffer.  A
+        // tile with up to twice the staging capacity goes as one wide tile
+        // over both raw buffers (from buffer 0's start; the other buffer gets
+        // a skip token), so that it stays in the pipeline; larger ones go to
+        // the list for the whole-block routine.
         int *spill_e = reinterpret_cast<int *>(mine);
+        unsigned char *spill_s = reinterpret_cast<unsigned char *>(spill_e + kPipeMaxSpill);
         // the spill list of the current buffer is final during this step
         const int nsp = min(*((volatile int *)&S.spill_cnt[cur]), S.spill_cap);
         unsigned kpar = 0, used = 0;       // per raw buffer: parity of its fills, filled before
@@ -641,14 +718,52 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
         int g = 0;
         if (lane == 0) g = atomicAdd(&ctl->tile_next, 1);
         g = __shfl_sync(0xffffffffu, g, 0);
+        CopyPlan pl;
         const long long tc0 = PT_NOW();
+        if (g < total) copy_plan(S, g, cur, pl);
+        bool ok = true;
         for (;;) {
-            // the following tile, claimed now so that its round trip overlaps this one's setup
+            // the following tile, claimed now so that its round trip overlaps this one's copies
             int gn = 0;
             if (g < total && lane == 0) gn = atomicAdd(&ctl->tile_next, 1);
-            // the raw buffer must be free (its previous tile sorted)
+            int n_spill = 0, n_own = 0, mode = 0;               // 0: whole-block list, 1: normal, 2: wide
+            if (g < total) {
+                copy_spills(S, pl, cur, nsp, spill_e, spill_s, n_spill, n_own);
+                const int m = pl.m_seg + n_spill;
+                if (n_spill <= kPipeMaxSpill) {
+                    if (m <= cap && n_own <= cap_own) mode = 1;
+                    else if (m <= 2 * cap && n_own <= 2 * cap_own) mode = 2;
+                }
+                if (mode == 0) {
+                    // done by the whole block after the pipeline
+                    if (lane == 0) {
+                        const int j = atomicAdd(&ctl->dense_count, 1);
+                        dense_list[j] = g + 1;
+                    }
+                    g = __shfl_sync(0xffffffffu, gn, 0);
+                    if (g < total) copy_plan(S, g, cur, pl);
+                    continue;
+                }
+                if (mode == 2 && r == 1) {
+                    // a wide tile starts at buffer 0: buffer 1 passes a skip token first
+                    if (((used >> 1) & 1u) && !warp_wait(&sh.bar_raw_empty[1], ((kpar >> 1) & 1u) ^ 1u, S.err)) {
+                        ok = false;
+                        break;
+                    }
+                    if (lane == 0) {
+                        sh.raw[1].tile = -2;
+                        mbar_arrive(&sh.bar_raw_full[1]);
+                    }
+                    kpar ^= 2u;
+                    used |= 2u;
+                    r = 0;
+                }
+            }
+            // the raw buffer (both for a wide tile) must be free (its previous tile sorted)
             const long long tw0 = PT_NOW();
             if (((used >> r) & 1u) && !warp_wait(&sh.bar_raw_empty[r], ((kpar >> r) & 1u) ^ 1u, S.err)) break;
+            if (mode == 2 && ((used >> 1) & 1u) && !warp_wait(&sh.bar_raw_empty[1], ((kpar >> 1) & 1u) ^ 1u, S.err))
+                break;
             if (lane == 0) PT_ADD(1, PT_NOW() - tw0);
             RawMeta &M = sh.raw[r];
             if (g >= total) {
@@ -659,37 +774,51 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                 break;
             }
             const long long ts0 = PT_NOW();
-            const bool fits = copy_setup(sh, g, cur, M, cap, cap_own, nsp, spill_e);
+            copy_commit(pl, g, M, n_spill, n_own, mode == 2, spill_s);
             if (lane == 0) PT_ADD(2, PT_NOW() - ts0);
-            if (!fits) {
-                // done by the whole block after the pipeline
-                if (lane == 0) {
-                    const int j = atomicAdd(&ctl->dense_count, 1);
-                    dense_list[j] = g + 1;
-                }
-                g = __shfl_sync(0xffffffffu, gn, 0);
-                continue;
-            }
+            const long long ti0 = PT_NOW();
             int4 *R = B.raw(r);
             // spilled records by plain loads, after the segments
-            for (int j = lane; j < M.n_spill; j += 32) R[M.m_seg + j] = S.spill_rec[cur][spill_e[j]];
+            for (int j = lane; j < n_spill; j += 32) R[pl.m_seg + j] = S.spill_rec[cur][spill_e[j]];
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
+            const long long ti1 = PT_NOW();
             if (lane == 0) {
                 sh.issued[r] += 1;
-                mbar_arrive_tx(&sh.bar_raw_full[r], (unsigned)M.m_seg * 16u);
+                mbar_arrive_tx(&sh.bar_raw_full[r], (unsigned)pl.m_seg * 16u);
             }
             __syncwarp();
-            if (lane < kSegs) {
-                const int c = M.segpre[lane + 1] - M.segpre[lane];
-                if (c > 0) bulk_copy(R + M.segpre[lane], sh.src[lane], (unsigned)c * 16u, &sh.bar_raw_full[r]);
-            }
+            if (lane < kSegs && pl.c > 0)
+                bulk_copy(R + (pl.incl - pl.c), pl.sg.base, (unsigned)pl.c * 16u, &sh.bar_raw_full[r]);
             __syncwarp();
+            if (lane == 0) {
+                PT_ADD(15, ti1 - ti0);
+                PT_ADD(9, PT_NOW() - ti1);
+            }
             kpar ^= 1u << r;
             used |= 1u << r;
-            r ^= 1;
+            if (mode == 2) {
+                // the wide tile's second buffer: a skip token (no copies into it)
+                if (lane == 0) {
+                    sh.raw[1].tile = -2;
+                    mbar_arrive(&sh.bar_raw_full[1]);
+                }
+                kpar ^= 2u;
+                used |= 2u;
+                r = 0;
+            } else {
+                r ^= 1;
+            }
+            const long long tq0 = PT_NOW();
             g = __shfl_sync(0xffffffffu, gn, 0);
+            const long long tq1 = PT_NOW();
+            if (g < total) copy_plan(S, g, cur, pl);
+            if (lane == 0) {
+                PT_ADD(13, tq1 - tq0);
+                PT_ADD(14, PT_NOW() - tq1);
+            }
         }
+        (void)ok;
         if (lane == 0) PT_ADD(0, PT_NOW() - tc0);
     } else if (warp <= NSORT) {
         // --------------------------------------------------- sort warps --
@@ -701,14 +830,35 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             bool ok = mbar_wait(&sh.bar_raw_full[r], (rpar >> r) & 1u, S.err);
             if (!sort_sync_and(NS, ok)) break;
             if (st == 0) PT_ADD(3, PT_NOW() - t0);
-            t0 = PT_NOW();
             rpar ^= 1u << r;
-            const bool end = sh.raw[r].tile < 0;
+            const int tile = sh.raw[r].tile;
+            if (tile == -2) {
+                // skip token: the buffer held (or will hold) part of a wide tile
+                if (st == 0) mbar_arrive(&sh.bar_raw_empty[r]);
+                r ^= 1;
+                continue;
+            }
+            const bool end = tile < 0;
+            const bool wide = !end && sh.raw[r].wide;
+            if (wide && b == 1) {
+                // a wide tile fills output buffers 0 and 1: buffer 1 passes a skip token first
+                ok = !((oused >> 1) & 1u) || mbar_wait(&sh.bar_empty[1], ((opar >> 1) & 1u) ^ 1u, S.err);
+                if (!sort_sync_and(NS, ok)) break;
+                if (st == 0) {
+                    sh.out[1].tile = -2;
+                    mbar_arrive(&sh.bar_full[1]);
+                }
+                opar ^= 2u;
+                oused |= 2u;
+                b = 0;
+            }
+            t0 = PT_NOW();
             if (!end) sort_map(sh, B, r, st, NS);
-            // the output buffer must be free (its previous tile updated)
             if (st == 0) PT_ADD(5, PT_NOW() - t0);
+            // the output buffer (both for a wide tile) must be free (its previous tile updated)
             t0 = PT_NOW();
             ok = !((oused >> b) & 1u) || mbar_wait(&sh.bar_empty[b], ((opar >> b) & 1u) ^ 1u, S.err);
+            if (wide) ok = ok && (!((oused >> 1) & 1u) || mbar_wait(&sh.bar_empty[1], ((opar >> 1) & 1u) ^ 1u, S.err));
             if (!sort_sync_and(NS, ok)) break;
             if (st == 0) PT_ADD(4, PT_NOW() - t0);
             if (end) {
@@ -719,7 +869,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                 break;
             }
             t0 = PT_NOW();
-            sort_order<MODEL>(sh, B, r, b, st, NS, cap_own);
+            sort_order<MODEL>(sh, B, r, b, st, NS, wide ? 2 * cap_own : cap_own);
             sort_sync(NS);
             if (st == 0) {
                 PT_ADD(6, PT_NOW() - t0);
@@ -727,11 +877,21 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                 sh.taken[r] += 1;
                 mbar_arrive(&sh.bar_raw_empty[r]);
                 mbar_arrive(&sh.bar_full[b]);
+                if (wide) {
+                    sh.out[1].tile = -2;
+                    mbar_arrive(&sh.bar_full[1]);
+                }
             }
             opar ^= 1u << b;
             oused |= 1u << b;
+            if (wide) {
+                opar ^= 2u;
+                oused |= 2u;
+                b = 0;
+            } else {
+                b ^= 1;
+            }
             r ^= 1;
-            b ^= 1;
         }
     } else {
         // ------------------------------------------------- update warps --
@@ -744,9 +904,16 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             if (lane == 0) PT_ADD(7, t1 - t0);
             fpar ^= 1u << b;
             const OutMeta &O = sh.out[b];
+            if (O.tile == -2) {
+                // skip token: this buffer holds part of the wide tile just updated
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.bar_empty[b]);
+                b ^= 1;
+                continue;
+            }
             if (O.tile < 0) break;
             const float4 *P = B.P(b);
-            const int *cst = B.cstart(b);
+            const unsigned short *cst = B.cstart(b);
             const int4 *OWN = B.own(b);
             const unsigned short *OQ = B.ownq(b);
             for (;;) {
@@ -797,7 +964,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
     //     the shared staging area or the block's global scratch ------------
     __shared__ TileCtx T;
     const size_t tbytes = table_bytes(nce_max, hist_words);
-    const size_t dyn = pipe_smem_bytes(cap, cap_own, nce_max, hist_words);
+    const size_t dyn = pipe_smem_bytes(cap, cap_own, nceh_max, hist_words);
     // stage_bytes(a) <= 41 a + 18: the staging area and the tables fit in dyn
     const int as_cap = (int)(((dyn - tbytes - 256) / 41) & ~63);
     Stage As;
@@ -867,15 +1034,14 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
         if (tid == 0) PT_ADD(11, 1);
         __syncthreads();
     }
-    if (tid == 0) {
-        PT_ADD(9, PT_NOW() - td0);
-        PT_ADD(12, PT_NOW() - tk0);
-    }
+    if (tid == 0) PT_ADD(12, PT_NOW() - tk0);
+    (void)td0;
 }
 
 #ifndef AAP_PIPE_SORT_WARPS
 #define AAP_PIPE_SORT_WARPS 8
 #endif
+
 
 template <int MODEL>
 static cudaError_t static_pipe_t(size_t *bytes)
@@ -923,9 +1089,9 @@ cudaError_t configure_pipe_kernel(int model, size_t smem)
 template <int MODEL>
 static cudaError_t launch_pipe_t(const LaunchCfg &L, cudaStream_t st)
 {
-    const size_t smem = pipe_smem_bytes(L.pipe_cap, L.pipe_cap_own, L.nce_max, L.hist_words);
+    const size_t smem = pipe_smem_bytes(L.pipe_cap, L.pipe_cap_own, L.pipe_nceh, L.hist_words);
     k_step_pipe<MODEL, AAP_PIPE_SORT_WARPS><<<L.pipe_grid, kPipeThreads, smem, st>>>(
-        L.sys, L.ctl, L.pipe_cap, L.pipe_cap_own, L.nce_max, L.hist_words, L.dense_list, L.scratch,
+        L.sys, L.ctl, L.pipe_cap, L.pipe_cap_own, L.pipe_nceh, L.nce_max, L.hist_words, L.dense_list, L.scratch,
         L.scratch_per_block, L.scratch_cap, L.spill_list_cap);
     return cudaGetLastError();
 }

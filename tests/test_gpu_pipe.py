@@ -82,20 +82,21 @@ def test_pipelined_equals_block_kernel(lib, case):
         A.aap_destroy(h2)
 
 
-@pytest.mark.parametrize("n,w", [(5000, 4.0), (12000, 3.0)])
+@pytest.mark.parametrize("n,w", [(3200, 7.0), (5000, 4.0), (12000, 3.0)])
 def test_pipelined_dense_tiles(lib, oracle, n, w):
-    """A cluster denser than a tile's shared buffers hold: those tiles go to
-    the whole-block routine at the end of the pipelined kernel (its shared
-    staging area for the first case, global scratch for the second); the
-    result equals the block kernel's bit for bit and the oracle's within
-    tolerance."""
+    """A cluster denser than a tile's shared buffers hold: up to twice their
+    capacity a tile goes through the pipeline as one wide tile over both
+    buffers (first case), beyond that to the whole-block routine at the end of
+    the pipelined kernel (its shared staging area, or global scratch for the
+    last case); the result equals the block kernel's bit for bit and the
+    oracle's within tolerance."""
     L = 64.0
     x, y, th = inputs.clustered_state(n, L, L, 7, 30.5, 33.2, w)
     p = params(n=n, lx=L, ly=L, eta=0.2, v=0.3, seed=43)
     h1, h2 = _pair(p, (x, y, th.astype(np.float32)))
     try:
         lay = A.aap_get_layout(h1)
-        assert lay.threads == 1024 and n > 2 * lay.stage_cap
+        assert lay.threads == 1024 and n > lay.stage_cap
         compare_one_step(oracle, p, h1)
         A.aap_step_neighbours(h2, n)
         _same(h1, h2, n)
