@@ -554,6 +554,7 @@ int dev_free(aap_handle *h, void *p, size_t bytes)
 }
 
 size_t region_bytes(const Sys &S) { return (size_t)S.ntiles * S.tile_slots * sizeof(int4); }
+size_t spill_bits_bytes(const Sys &S) { return (size_t)(S.ntiles / 32 + 1) * sizeof(unsigned); }
 
 // Buffers whose size depends on the capacity factor.
 int alloc_regions(aap_handle *h)
@@ -604,6 +605,8 @@ int clear_buffers(aap_handle *h)
     for (int b = 0; b < 2; ++b)
         AAP_CK(cudaMemsetAsync(S.cnt[b], 0, (size_t)S.ntiles * aapk::kCntStride * sizeof(int), h->stream));
     AAP_CK(cudaMemsetAsync(S.spill_cnt, 0, 2 * sizeof(int), h->stream));
+    for (int b = 0; b < 2; ++b)
+        AAP_CK(cudaMemsetAsync(S.spill_bits[b], 0, spill_bits_bytes(S), h->stream));
     AAP_CK(cudaMemsetAsync(S.acc, 0, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long), h->stream));
     AAP_CK(cudaMemsetAsync(S.err, 0, sizeof(int), h->stream));
     return AAP_OK;
@@ -617,6 +620,8 @@ int alloc_all(aap_handle *h)
         if ((rc = dev_alloc(h, &S.cnt[b], (size_t)S.ntiles * aapk::kCntStride * sizeof(int)))) return rc;
     if ((rc = alloc_regions(h))) return rc;
     if ((rc = dev_alloc(h, &S.spill_cnt, 2 * sizeof(int)))) return rc;
+    for (int b = 0; b < 2; ++b)
+        if ((rc = dev_alloc(h, &S.spill_bits[b], spill_bits_bytes(S)))) return rc;
     if ((rc = dev_alloc(h, &S.acc, 2 * aapk::kAccSlots * aapk::kAccWords * sizeof(unsigned long long)))) return rc;
     if ((rc = dev_alloc(h, &S.last, 4 * sizeof(double)))) return rc;
     if ((rc = dev_alloc(h, &S.stats, 16 * sizeof(double)))) return rc;
@@ -765,7 +770,7 @@ int run_steps(aap_handle *h, long long nsteps);
 int act_on_error(aap_handle *h, int err, bool *relaid);
 
 // Steps between capacity checks inside one long call.
-constexpr long long kAdaptSteps = 128;
+constexpr long long kAdaptSteps = 32;
 
 // nsteps steps, with the device error word copied to the host after every
 // kAdaptSteps steps (counted across calls).  When a copy is taken the host

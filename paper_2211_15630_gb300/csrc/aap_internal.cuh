@@ -48,6 +48,7 @@ enum : int {
 
 constexpr int kPipeMaxStage = 4096;     // staged particles per tile in the pipelined step
 constexpr int kPipeMaxSpill = 256;      // spilled records one pipelined tile may take
+constexpr int kPipeSpillScan = 256;     // longest spill list the pipelined copy warp scans itself
 
 struct Sys {
     // geometry
@@ -78,6 +79,7 @@ struct Sys {
     int4 *spill_rec[2];
     int *spill_key[2];          // tile * kCntStride + region
     int *spill_cnt;             // [2]
+    unsigned *spill_bits[2];    // [ntiles / 32 + 1]: bit t set when a record bound for tile t spilled
     unsigned long long *acc;    // [2][kAccSlots][kAccWords]
     // measurement outputs
     double *trace;              // p(t) for t = trace_base .. trace_base + trace_cap - 1

@@ -132,7 +132,9 @@ __global__ void k_finish(Sys *sys, int nsys, const int *__restrict__ tile_base, 
          i += (long long)gridDim.x * blockDim.x) {
         const int g = (int)(i / kCntStride);
         const int si = nsys > 1 ? sys_of_tile(tile_base, nsys, g) : 0;
-        sys[si].cnt[cur][(long long)(g - tile_base[si]) * kCntStride + (int)(i % kCntStride)] = 0;
+        const int t = g - tile_base[si], w = (int)(i % kCntStride);
+        sys[si].cnt[cur][(long long)t * kCntStride + w] = 0;
+        if (w == 0 && (t & 31) == 0) sys[si].spill_bits[cur][t >> 5] = 0u;    // the tiles' spill marks
     }
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);

@@ -265,13 +265,22 @@ __device__ __forceinline__ void copy_plan(const Sys &S, int g, int cur, CopyPlan
 
 // The planned tile's spill matches (nsp spilled records): spill_e / spill_s
 // (the copy warp's global scratch) receive the spill entry and the segment of
-// staged spill record j; n_spill and the own count follow.
-__device__ __forceinline__ void copy_spills(const Sys &S, const CopyPlan &pl, int cur, int nsp, int *spill_e,
+// staged spill record j; n_spill and the own count follow.  Only a tile whose
+// source tiles received spilled records (their bits in spill_bits) looks at
+// the list, and only a short list is scanned here: false (warp-uniform) when
+// the tile must go to the whole-block routine, which scans with all threads.
+__device__ __forceinline__ bool copy_spills(const Sys &S, const CopyPlan &pl, int cur, int nsp, int *spill_e,
                                             unsigned char *spill_s, int &n_spill, int &n_own)
 {
     const int lane = threadIdx.x & 31;
     int ns = 0, nos = 0;
+    bool near = false;
     if (nsp > 0) {
+        const bool b = lane < kSegs && ((S.spill_bits[cur][pl.sg.tile >> 5] >> (pl.sg.tile & 31)) & 1u);
+        near = __any_sync(0xffffffffu, b);
+    }
+    if (near && nsp > kPipeSpillScan) return false;
+    if (near) {
         const int mt = lane < kSegs ? pl.sg.tile : -1, mr = lane < kSegs ? pl.sg.region : -1;
         for (int e0 = 0; e0 < nsp; e0 += 32) {
             const int e = e0 + lane;
@@ -294,6 +303,7 @@ __device__ __forceinline__ void copy_spills(const Sys &S, const CopyPlan &pl, in
     __syncwarp();
     n_spill = ns;
     n_own = pl.own_seg + nos;
+    return true;
 }
 
 // The planned tile's meta into raw buffer meta M (the raw buffer, or both for
@@ -728,9 +738,9 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             if (g < total && lane == 0) gn = atomicAdd(&ctl->tile_next, 1);
             int n_spill = 0, n_own = 0, mode = 0;               // 0: whole-block list, 1: normal, 2: wide
             if (g < total) {
-                copy_spills(S, pl, cur, nsp, spill_e, spill_s, n_spill, n_own);
+                const bool scanned = copy_spills(S, pl, cur, nsp, spill_e, spill_s, n_spill, n_own);
                 const int m = pl.m_seg + n_spill;
-                if (n_spill <= kPipeMaxSpill) {
+                if (scanned && n_spill <= kPipeMaxSpill) {
                     if (m <= cap && n_own <= cap_own) mode = 1;
                     else if (m <= 2 * cap && n_own <= 2 * cap_own) mode = 2;
                 }

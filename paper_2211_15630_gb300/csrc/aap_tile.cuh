@@ -74,6 +74,7 @@ __device__ __forceinline__ void warp_insert(const Sys &S, int b, bool act, int d
             if (e < S.spill_cap) {
                 S.spill_rec[b][e] = rec;
                 S.spill_key[b][e] = key;
+                atomicOr(&S.spill_bits[b][dtile >> 5], 1u << (dtile & 31));
                 atomicOr(S.err, ERR_SPILL);
             } else {
                 atomicOr(S.err, ERR_LOST);
