@@ -53,4 +53,34 @@ __device__ __forceinline__ int warp_incl_scan(int v)
     return v;
 }
 
+// arg(x + i y) in [-pi, pi] (the angle of the VM sum, Eq. collision_VM), with
+// arg(0) = 0.  The octant symmetries of the arctangent reduce the argument to
+// t = min(|x|, |y|) / max(|x|, |y|) in [0, 1]; atan(t) there is an odd
+// polynomial t P(t^2) of degree 15 whose coefficients were fitted in the
+// minimax sense on [0, 1] (Lawson's iteratively reweighted least squares):
+// 3.7e-8 rad in exact arithmetic, 1.4e-7 rad evaluated in FP32 with FMAs, plus
+// the error of the fast quotient (2 ulp of t, times atan' <= 1).  No branches.
+constexpr float kAtan0 = 9.999993443e-01f, kAtan1 = -3.332985938e-01f, kAtan2 = 1.994656622e-01f,
+                kAtan3 = -1.390862912e-01f, kAtan4 = 9.642197192e-02f, kAtan5 = -5.591231957e-02f,
+                kAtan6 = 2.186295204e-02f, kAtan7 = -4.054565448e-03f;
+
+__device__ __forceinline__ float arg2(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float hi = fmaxf(ax, ay), lo = fminf(ax, ay);
+    const float t = hi > 0.f ? __fdividef(lo, hi) : 0.f;      // |sums| < 2^126: the fast quotient is valid
+    const float t2 = t * t;
+    float r = fmaf(kAtan7, t2, kAtan6);
+    r = fmaf(r, t2, kAtan5);
+    r = fmaf(r, t2, kAtan4);
+    r = fmaf(r, t2, kAtan3);
+    r = fmaf(r, t2, kAtan2);
+    r = fmaf(r, t2, kAtan1);
+    r = fmaf(r, t2, kAtan0);
+    r *= t;
+    if (ay > ax) r = 1.57079632679490f - r;
+    if (x < 0.f) r = AAP_PI_F - r;
+    return copysignf(r, y);
+}
+
 }  // namespace aapk

@@ -591,7 +591,7 @@ __device__ __forceinline__ void update_one(const Sys &S, const OutMeta &O, const
         int dX, dY;
         if (MODEL != 1) {
             // Eq. (collision_VM) / (collision_NVM) + noise; Eq. (streaming)
-            thn = atan2f(ss, sc) + S.omega_step + S.eta_pi * (2.0f * u0 - 1.0f);
+            thn = arg2(ss, sc) + S.omega_step + S.eta_pi * (2.0f * u0 - 1.0f);
             __sincosf(thn, &sn, &cn);
             dX = __float2int_rn(S.kx * cn);
             dY = __float2int_rn(S.ky * sn);

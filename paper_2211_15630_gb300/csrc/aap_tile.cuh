@@ -514,7 +514,7 @@ __device__ __forceinline__ void tile_body(TileCtx &T, const Stage &A, const Tabl
             int dX, dY;
             if (MODEL != 1) {
                 // Eq. (collision_VM) / (collision_NVM) + noise; Eq. (streaming)
-                thn = atan2f(ss, sc) + S.sp_omega_step[sp] + S.sp_eta_pi[sp] * (2.0f * u0 - 1.0f);
+                thn = arg2(ss, sc) + S.sp_omega_step[sp] + S.sp_eta_pi[sp] * (2.0f * u0 - 1.0f);
                 __sincosf(thn, &sn, &cn);
                 dX = __float2int_rn(S.sp_kx[sp] * cn);
                 dY = __float2int_rn(S.sp_ky[sp] * sn);
