@@ -318,16 +318,18 @@ def _bench_metric_free(A, W, torch, stream, steps, kn=6):
             "search_update_kernels_ms": kms[0] / max(kl[0], 1), "finish_ms": kms[1] / max(kl[1], 1)}
 
 
-def _bench_ensemble(A, W, torch, stream, steps):
+def _bench_ensemble(A, W, torch, stream, steps, long_steps=5000, trial_steps=50):
     """256 Vicsek replicas (N log-uniform 2^10..2^18, rho in {0.5,1,2,4}, eta in
     [0.1,0.7]): one batched, graph-replayed launch per step vs the same replicas
-    run one after another as standalone systems with the same tile shapes."""
+    run one after another as standalone systems with the same tile shapes
+    (`steps` steps each), then the configured run: `long_steps` measured steps
+    of the whole ensemble and the time-averaged p of every replica."""
     import numpy as np
 
     ps = W.ensemble_replicas(count=256, seed=7)
     ntot = sum(p.n for p in ps)
     e = A.aap_ens_create(ps, stream.cuda_stream)
-    pol, trial = A.aap_ens_autotune(e, 10)
+    pol, trial = A.aap_ens_autotune(e, trial_steps)
     A.aap_ens_step(e, 3)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -357,40 +359,71 @@ def _bench_ensemble(A, W, torch, stream, steps):
             b = A.aap_ens_get_state(e, r, q.n)
             exact = exact and all(np.array_equal(u, v) for u, v in zip(a, b))
         A.aap_destroy(h)
+    # the configured run: long_steps measured steps (Sec. 3.4 window), <p> per replica
+    torch.cuda.synchronize()
+    e0.record(stream)
+    A.aap_ens_measure(e, long_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_long = e0.elapsed_time(e1)
+    pm = A.aap_ens_phi_mean(e)
+    etas = np.array([p.eta for p in ps])
     A.aap_ens_destroy(e)
     return {"workload": "256 Vicsek replicas, N log-uniform [2^10,2^18], rho {0.5,1,2,4}, eta U[0.1,0.7]",
             "replicas": len(ps), "total_particles": ntot, "steps": steps,
             "updates_per_s": ntot * steps / (ms_ens / 1e3),
             "sequential_updates_per_s": ntot * steps / (ms_seq / 1e3),
             "speedup_vs_sequential": ms_seq / ms_ens, "policy": int(pol),
+            "policy_trial_steps": trial_steps,
             "policy_ms_per_step": [round(float(v), 4) for v in trial],
-            "phi_error": 0.0 if exact else None, "replicas_bitwise_equal_checked": [0, 255]}
+            "phi_error": 0.0 if exact else None, "replicas_bitwise_equal_checked": [0, 255],
+            "measured_steps": long_steps, "measured_updates_per_s": ntot * long_steps / (ms_long / 1e3),
+            "measured_ms_per_step": ms_long / long_steps,
+            "phi_mean_eta_below_0.3": [round(float(v), 4) for v in np.percentile(pm[etas < 0.3], [0, 50, 100])],
+            "phi_mean_eta_above_0.5": [round(float(v), 4) for v in np.percentile(pm[etas > 0.5], [0, 50, 100])]}
 
 
-def _bench_surrogate(A, W, torch, stream, train_traj=32, iters=300, horizon=100, lr=2e-3,
-                     pushforward=0.0, nfr=40, conserve=0):
-    """Train the field surrogate on Vicsek N = 524,288, L = 512 trajectories
-    (eta in [0.3, 0.5]) coarse-grained to 128 x 128 x 3 every 10 steps, then
-    advance held-out states by `horizon` particle steps with the surrogate
-    and with the particle method; report speedup and errors in p and S(k)."""
+def _surrogate_data(A, W, torch, stream, train_traj=200, steps=2000, every=10):
+    """Training fields of the learned surrogate at its stated size: Vicsek
+    N = 524,288, L = 512 trajectories (eta uniform in [0.3, 0.5], seeds
+    10000 + r) from the Philox initial state, advanced together as one
+    batched ensemble and coarse-grained to 128 x 128 x 3 every `every` steps
+    (steps / every + 1 frames each, kept on the device: 7.9 GB at 200 x 2000)."""
     import numpy as np
 
-    nb, every = 128, 10
+    nb = 128
     g = np.random.default_rng(3)
     etas = g.uniform(0.3, 0.5, train_traj)
     ps = [W.surrogate_training(eta=float(etas[r]), seed=10000 + r) for r in range(train_traj)]
     e = A.aap_ens_create(ps, stream.cuda_stream)
-    A.aap_ens_step(e, 100)
+    nfr = steps // every + 1
     frames = torch.zeros(train_traj, nfr, 3, nb, nb, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(nfr):
         for r in range(train_traj):
             A.aap_ens_coarse_grain(e, r, nb, nb, frames[r, k].data_ptr())
-        A.aap_ens_step(e, every)
+        if k + 1 < nfr:
+            A.aap_ens_step(e, every)
     stream.synchronize()
     A.aap_ens_destroy(e)
     t_data = time.perf_counter() - t0
+    return {"frames": frames, "etas": etas, "train_traj": train_traj, "steps": steps, "every": every,
+            "nfr": nfr, "data_s": t_data,
+            "particle_updates_per_s": train_traj * 524288 * steps / t_data}
+
+
+def _bench_surrogate(A, W, torch, stream, data, iters=3000, horizon=100, lr=2e-3, pushforward=0.0, conserve=0):
+    """Train the field surrogate on `data` (_surrogate_data), then advance
+    held-out states by `horizon` particle steps with the surrogate and with
+    the particle method; report speedup and the errors in p and S(k), beside
+    those of keeping the fields unchanged."""
+    import numpy as np
+
+    nb, every = 128, data["every"]
+    g = np.random.default_rng(3)
+    frames, etas, train_traj, nfr = data["frames"], data["etas"], data["train_traj"], data["nfr"]
+    t_data = data["data_s"]
     B = 32
     s = A.aap_sur_create(A.aap_sur_params_default(nbx=nb, nby=nb, max_batch=B, lr=lr, seed=11, conserve=conserve),
                          stream.cuda_stream)
@@ -429,39 +462,46 @@ def _bench_surrogate(A, W, torch, stream, train_traj=32, iters=300, horizon=100,
     # the first call captures the predict graph for these buffers; later calls replay it
     A.aap_sur_predict(s, f0.data_ptr(), ed.data_ptr(), 1, apps, fp.data_ptr())
     torch.cuda.synchronize()
+    starts = (300, 1500)                              # both inside the time range of the training frames
     for j, eta in enumerate(held_out):
         p = W.surrogate_training(eta=float(eta), seed=20000 + j)
         h = A.aap_create(p, stream.cuda_stream)
-        A.aap_step(h, 300)                        # inside the time range of the training frames
-        A.aap_coarse_grain(h, nb, nb, f0.data_ptr())
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        A.aap_step(h, horizon)
-        A.aap_coarse_grain(h, nb, nb, ft.data_ptr())
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        t_part += ev0.elapsed_time(ev1)
-        ed.fill_(float(eta))
-        ev0.record(stream)
-        A.aap_sur_predict(s, f0.data_ptr(), ed.data_ptr(), 1, apps, fp.data_ptr())
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        t_sur += ev0.elapsed_time(ev1)
+        done = 0
+        for t_start in starts:
+            A.aap_step(h, t_start - done)
+            A.aap_coarse_grain(h, nb, nb, f0.data_ptr())
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            A.aap_step(h, horizon)
+            A.aap_coarse_grain(h, nb, nb, ft.data_ptr())
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            done = t_start + horizon
+            t_part += ev0.elapsed_time(ev1)
+            ed.fill_(float(eta))
+            ev0.record(stream)
+            A.aap_sur_predict(s, f0.data_ptr(), ed.data_ptr(), 1, apps, fp.data_ptr())
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t_sur += ev0.elapsed_time(ev1)
+            a_t, a_p, a_0 = (v.cpu().numpy()[0].astype(np.float64) for v in (ft, fp, f0))
+            phi = lambda f: np.hypot(f[1].sum(), f[2].sum()) / f[0].sum()
+            errs.append(abs(phi(a_p) - phi(a_t)))
+            keep_errs.append(abs(phi(a_0) - phi(a_t)))
+            s_t, s_p, s_0 = (_structure_factor(f[0] * area) for f in (a_t, a_p, a_0))
+            sk_errs.append(float(np.linalg.norm(s_p - s_t) / np.linalg.norm(s_t)))
+            sk_keep.append(float(np.linalg.norm(s_0 - s_t) / np.linalg.norm(s_t)))
         A.aap_destroy(h)
-        a_t, a_p, a_0 = (v.cpu().numpy()[0].astype(np.float64) for v in (ft, fp, f0))
-        phi = lambda f: np.hypot(f[1].sum(), f[2].sum()) / f[0].sum()
-        errs.append(abs(phi(a_p) - phi(a_t)))
-        keep_errs.append(abs(phi(a_0) - phi(a_t)))
-        s_t, s_p, s_0 = (_structure_factor(f[0] * area) for f in (a_t, a_p, a_0))
-        sk_errs.append(float(np.linalg.norm(s_p - s_t) / np.linalg.norm(s_t)))
-        sk_keep.append(float(np.linalg.norm(s_0 - s_t) / np.linalg.norm(s_t)))
     A.aap_sur_destroy(s)
+    nev = len(errs)
     return {"workload": "Vicsek N=524288 L=512 eta[0.3,0.5] -> 128x128x3 fields, 4-layer 3x3 conv 32 ch",
-            "train_trajectories": train_traj, "frames_per_trajectory": nfr, "iterations": iters,
+            "train_trajectories": train_traj, "steps_per_trajectory": data["steps"],
+            "frames_per_trajectory": nfr, "iterations": iters,
+            "data_particle_updates_per_s": data["particle_updates_per_s"],
             "batch": B, "lr": lr, "pushforward": pushforward, "conserve": conserve, "final_loss": loss, "data_s": t_data, "train_s": t_train,
             "horizon_steps": horizon, "speedup_vs_particles": t_part / t_sur,
-            "particle_ms": t_part / len(held_out), "surrogate_ms": t_sur / len(held_out),
-            "held_out_states": len(held_out),
+            "particle_ms": t_part / nev, "surrogate_ms": t_sur / nev,
+            "held_out_states": nev, "held_out_seeds": len(held_out), "start_steps": list(starts),
             "phi_abs_error": float(np.mean(errs)), "phi_abs_error_keep_fields": float(np.mean(keep_errs)),
             "sk_rel_l2_error": float(np.mean(sk_errs)), "sk_rel_l2_error_keep_fields": float(np.mean(sk_keep))}
 
@@ -619,14 +659,16 @@ def main():
             msx = timed(he, max(args.steps // 4, 50))
             extras[f"vicsek_eta_{eta}_updates_per_s"] = args.n * max(args.steps // 4, 50) / (msx / 1e3)
             A.aap_destroy(he)
-        extras["brownian"] = _bench_brownian(A, W, torch, stream, 500)
+        extras["brownian"] = _bench_brownian(A, W, torch, stream, 10000)
         extras["metric_free"] = _bench_metric_free(A, W, torch, stream, 100)
         extras["ensemble"] = _bench_ensemble(A, W, torch, stream, 200)
         extras["coarse_grain"] = _bench_coarse(A, W, torch, stream, _peaks()[0])
         with torch.cuda.stream(stream):     # torch copies and library calls share one stream
             # conserving (grid means of density and polarisation kept) and free
-            extras["surrogate"] = _bench_surrogate(A, W, torch, stream, conserve=3)
-            extras["surrogate_unconstrained"] = _bench_surrogate(A, W, torch, stream, conserve=0)
+            data = _surrogate_data(A, W, torch, stream)
+            extras["surrogate"] = _bench_surrogate(A, W, torch, stream, data, conserve=3)
+            extras["surrogate_unconstrained"] = _bench_surrogate(A, W, torch, stream, data, conserve=0)
+            del data
 
     if rank != 0:
         if dist:

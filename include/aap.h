@@ -94,8 +94,9 @@ typedef struct aap_params {
     int32_t  threads;    /* threads per block of the step kernel: 0 (automatic),
                             256 or 512 (whole-block tile kernel), 1024 (the
                             pipelined kernel: one block per SM with copy, sort
-                            and update warps; one species, not in ensembles).
-                            Automatic picks 1024 where it applies, else 512  */
+                            and update warps; one species per system).
+                            Automatic picks 1024 where it applies, else 512;
+                            an ensemble follows its first replica's value   */
     double   capacity;   /* tile-region capacity over the mean occupancy;
                             0 = automatic (4)                                   */
     int32_t  binnum_theta;      /* bins of the orientation histogram over
@@ -366,7 +367,8 @@ int aap_ens_coarse_grain(aap_ens *e, int32_t r, int32_t nbx, int32_t nby, float 
 int aap_ens_get_layout(aap_ens *e, int32_t r, aap_layout *out);
 
 /* Autotuner of block and tile shapes: time trial_steps steps of the whole
- * ensemble under each candidate policy (threads per block x nominal tile),
+ * ensemble under each candidate policy (nominal tile; threads per block for
+ * the whole-block kernel),
  * keep the fastest and re-create every replica in its initial state with it.
  * Only allowed before the first step.  *policy_out (may be NULL) receives the
  * chosen policy index; *ms_out (may be NULL, 8 doubles) the trial times in

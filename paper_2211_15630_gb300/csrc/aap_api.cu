@@ -310,9 +310,8 @@ int set_capacity_mf(aap_handle *h)
 // Shared buffers of the pipelined step: the largest staging capacity (a
 // multiple of 64, at most kPipeMaxStage) whose two raw and two sorted buffers,
 // with own lists sized for 7/8 of it, fit the block's shared memory.
-int set_pipe(aap_handle *h)
+int set_pipe_launch(LaunchCfg &L, int twmax, int thmax, int total_tiles)
 {
-    LaunchCfg &L = h->L;
     int dev = 0, optin = 0;
     AAP_CK(cudaGetDevice(&dev));
     AAP_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -320,7 +319,7 @@ int set_pipe(aap_handle *h)
     AAP_CK(aapk::pipe_static_smem(L.model, &stat));
     int cap = aapk::kPipeMaxStage;
     auto own_of = [](int c) { return aapk::round_up(c * 7 / 8, 64); };
-    L.pipe_nceh = (2 * h->hs.twmax + 4) * (h->hs.thmax + 2);
+    L.pipe_nceh = (2 * twmax + 4) * (thmax + 2);
     while (cap >= 256 && aapk::pipe_smem_bytes(cap, own_of(cap), L.pipe_nceh, L.hist_words) + stat > (size_t)optin)
         cap -= 64;
     if (cap < 256) return AAP_OK;
@@ -330,13 +329,15 @@ int set_pipe(aap_handle *h)
         return AAP_OK;
     L.pipe_cap = cap;
     L.pipe_cap_own = own_of(cap);
-    L.pipe_grid = std::max(1, std::min(h->hs.ntiles, sm_count()));
+    L.pipe_grid = std::max(1, std::min(total_tiles, sm_count()));
     AAP_CK(aapk::configure_pipe_kernel(L.model, aapk::pipe_smem_bytes(L.pipe_cap, L.pipe_cap_own, L.pipe_nceh,
                                                                       L.hist_words)));
     L.pipe = 1;
     L.threads = 1024;
     return AAP_OK;
 }
+
+int set_pipe(aap_handle *h) { return set_pipe_launch(h->L, h->hs.twmax, h->hs.thmax, h->hs.ntiles); }
 
 int set_capacity(aap_handle *h, double factor)
 {
@@ -1038,6 +1039,8 @@ struct aap_ens {
     Ctl *d_ctl = nullptr;
     unsigned char *d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    int *d_dense = nullptr;             // pipelined step: tiles left to the whole-block routine
+    size_t dense_tiles = 0;
     LaunchCfg L{};
     long long step = 0;
     cudaStream_t cap = nullptr;
@@ -1067,10 +1070,13 @@ void ens_free(aap_ens *e)
     if (e->d_tile_base) cudaFree(e->d_tile_base);
     if (e->d_ctl) cudaFree(e->d_ctl);
     if (e->d_scratch) cudaFree(e->d_scratch);
+    if (e->d_dense) cudaFree(e->d_dense);
     e->d_sys = nullptr;
     e->d_tile_base = nullptr;
     e->d_ctl = nullptr;
     e->d_scratch = nullptr;
+    e->d_dense = nullptr;
+    e->dense_tiles = 0;
     e->scratch_bytes = 0;
 }
 
@@ -1085,7 +1091,7 @@ int ens_combine(aap_ens *e)
     L.model = e->params[0].model;
     L.tile_base = e->d_tile_base;
     L.ctl = e->d_ctl;
-    L.threads = e->params[0].threads ? e->params[0].threads : pol.threads;
+    L.threads = (e->params[0].threads && e->params[0].threads != 1024) ? e->params[0].threads : pol.threads;
     L.pipe = 0;
     L.stage_cap = 64;
     L.nce_max = 9;
@@ -1145,6 +1151,33 @@ int ens_combine(aap_ens *e)
         e->scratch_bytes = need;
     }
     L.scratch = e->d_scratch;
+    // the pipelined kernel (threads 0 or 1024): one block per SM over all
+    // replicas' tiles, tiles that do not fit listed for the whole-block routine
+    bool one_species = true;
+    for (const aap_params &q : e->params) one_species = one_species && q.nspecies <= 1;
+    if (one_species && (e->params[0].threads == 0 || e->params[0].threads == 1024)) {
+        int twmax = 1, thmax = 1;
+        for (const aap_handle *h : e->m) {
+            twmax = std::max(twmax, h->hs.twmax);
+            thmax = std::max(thmax, h->hs.thmax);
+        }
+        if ((size_t)total > e->dense_tiles) {
+            if (e->d_dense) cudaFree(e->d_dense);
+            e->d_dense = nullptr;
+            e->dense_tiles = 0;
+            if (cudaMalloc(&e->d_dense, (size_t)total * sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(AAP_ENOMEM, "ensemble tile list allocation failed");
+            }
+            e->dense_tiles = (size_t)total;
+        }
+        AAP_CK(cudaMemset(e->d_dense, 0, (size_t)total * sizeof(int)));
+        L.dense_list = e->d_dense;
+        int rc = set_pipe_launch(L, twmax, thmax, (int)total);
+        if (rc) return rc;
+        if (!L.pipe && e->params[0].threads == 1024)
+            return fail(AAP_EINVAL, "the pipelined step kernel does not fit this ensemble's tiling");
+    }
     if (e->exec) cudaGraphExecDestroy(e->exec);
     e->exec = nullptr;
     return AAP_OK;
@@ -1673,8 +1706,8 @@ int aap_ens_create(const aap_params *params, int32_t count, void *stream, aap_en
         if (params[r].kn > 0) return fail(AAP_EINVAL, "metric-free systems (kn > 0) are not batched; use aap_create");
         if (params[r].model != params[0].model) return fail(AAP_EINVAL, "all replicas must use the same model");
         if (params[r].threads != params[0].threads) return fail(AAP_EINVAL, "all replicas must use the same threads");
-        if (params[r].threads == 1024)
-            return fail(AAP_EINVAL, "ensembles run the whole-block step kernel: threads must be 0, 256 or 512");
+        if (params[r].nspecies > 1 && params[r].threads == 1024)
+            return fail(AAP_EINVAL, "an ensemble of multi-species replicas needs threads = 0, 256 or 512");
     }
     aap_ens *e = new aap_ens();
     e->params.assign(params, params + count);
@@ -1811,7 +1844,7 @@ int aap_ens_get_layout(aap_ens *e, int32_t r, aap_layout *out)
     int rc = aap_get_layout(e->m[r], out);
     if (rc == AAP_OK) {
         out->threads = e->L.threads;
-        out->stage_cap = e->L.stage_cap;
+        out->stage_cap = e->L.pipe ? e->L.pipe_cap : e->L.stage_cap;
         out->tile_w = e->m[r]->nom_tw;
         out->tile_h = e->m[r]->nom_th;
     }

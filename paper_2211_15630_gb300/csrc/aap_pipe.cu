@@ -88,6 +88,10 @@ struct RawMeta {
     int tile;                   // tile index, -1: no more tiles, -2: skip (the buffer holds part of a wide tile)
     int m, m_seg, n_spill, n_own;
     int wide;                   // 1: the tile spans both raw buffers (staged from buffer 0's start)
+    int si;                     // system of the tile (ensembles: its replica)
+    int sx, sy, order;          // of that system: fixed-point bits per cell side, interaction order
+    float ux, uy;               // length of one fixed-point unit
+    int *err;                   // its error word
     int tx, ty, tw, th, twL, twR, thD, thU;
     int segpre[kSegs + 1];
     // map of segment s into the extended frame: x = offset of X (mod 2^32),
@@ -107,7 +111,9 @@ struct OutMeta {
 };
 
 struct PipeShared {
-    Sys S;
+    Sys os[2];                  // system of the tile in each output buffer (read by the update warps)
+    int osys[2];                // its index, -1: none yet
+    Sys cs;                     // the copy warp's current system
     RawMeta raw[2];
     OutMeta out[2];
     int chunk[2];               // next chunk of 32 own particles, per output buffer
@@ -132,8 +138,9 @@ struct PipeBufs {
     unsigned short *slotw;      // flip << 14 | arrival rank in its half cell
     int *hist;                  // [nce] (half cells)
     int *rowoff;                // own index = position in P + rowoff[ey]
-    int *mhist;                 // measured theta / |Omega| counts of the block
-    int cap, cap_own, cst_stride, oq_stride;
+    int *mhist0;                // [2][mh_stride] measured theta / |Omega| counts of each output buffer's tile
+    int cap, cap_own, cst_stride, oq_stride, mh_stride;
+    __device__ __forceinline__ int *mhist(int b) const { return mhist0 + b * mh_stride; }
     __device__ __forceinline__ int4 *raw(int b) const { return raw0 + b * cap; }
     __device__ __forceinline__ float4 *P(int b) const { return P0 + b * cap; }
     __device__ __forceinline__ int4 *own(int b) const { return own0 + b * cap_own; }
@@ -141,9 +148,10 @@ struct PipeBufs {
     __device__ __forceinline__ unsigned short *ownq(int b) const { return oq0 + b * oq_stride; }
 };
 
-__device__ __forceinline__ void carve_pipe(PipeBufs &B, unsigned char *p, int cap, int cap_own, int nce)
+__device__ __forceinline__ void carve_pipe(PipeBufs &B, unsigned char *p, int cap, int cap_own, int nce, int hist_words)
 {
     B.cap = cap;
+    B.mh_stride = round_up(hist_words, 4);
     B.cap_own = cap_own;
     B.cst_stride = round_up(nce + 1, 8);
     B.oq_stride = round_up(cap_own, 8);
@@ -165,7 +173,7 @@ __device__ __forceinline__ void carve_pipe(PipeBufs &B, unsigned char *p, int ca
     p += (size_t)round_up(nce, 4) * 4;
     B.rowoff = (int *)p;
     p += (size_t)(kMaxTile + 4) * 4;
-    B.mhist = (int *)p;
+    B.mhist0 = (int *)p;
 }
 
 // ------------------------------------------------------------- mbarriers --
@@ -308,8 +316,8 @@ __device__ __forceinline__ bool copy_spills(const Sys &S, const CopyPlan &pl, in
 
 // The planned tile's meta into raw buffer meta M (the raw buffer, or both for
 // a wide tile, must be free).
-__device__ __forceinline__ void copy_commit(const CopyPlan &pl, int g, RawMeta &M, int n_spill, int n_own, int wide,
-                                            const unsigned char *spill_s)
+__device__ __forceinline__ void copy_commit(const CopyPlan &pl, const Sys &S, int si, int g, RawMeta &M, int n_spill,
+                                            int n_own, int wide, const unsigned char *spill_s)
 {
     const int lane = threadIdx.x & 31;
     const Seg &sg = pl.sg;
@@ -332,6 +340,13 @@ __device__ __forceinline__ void copy_commit(const CopyPlan &pl, int g, RawMeta &
         M.n_spill = n_spill;
         M.n_own = n_own;
         M.wide = wide;
+        M.si = si;
+        M.sx = S.sx;
+        M.sy = S.sy;
+        M.order = S.order;
+        M.ux = S.ux;
+        M.uy = S.uy;
+        M.err = S.err;
         M.tx = pl.G.tx; M.ty = pl.G.ty; M.tw = pl.G.tw; M.th = pl.G.th;
         M.twL = pl.G.twL; M.twR = pl.G.twR; M.thD = pl.G.thD; M.thU = pl.G.thU;
     }
@@ -353,7 +368,6 @@ __device__ __forceinline__ void copy_commit(const CopyPlan &pl, int g, RawMeta &
 // place) and histogram it by cell.  tid: index among the NS sort threads.
 __device__ __forceinline__ void sort_map(PipeShared &sh, const PipeBufs &B, int r, int tid, int NS)
 {
-    const Sys &S = sh.S;
     const RawMeta &M = sh.raw[r];
     const int m = M.m, m_seg = M.m_seg;
     const int W2 = 2 * M.tw + 4, H2 = M.th + 2;       // half cells per extended row, rows
@@ -369,10 +383,10 @@ __device__ __forceinline__ void sort_map(PipeShared &sh, const PipeBufs &B, int 
         const int4 rr = R[k];
         const int4 g = M.map[s];
         const int mx = -(g.z & 1), my = -(g.w & 1);       // all ones where the axis is mirrored
-        const int lx = rr.x >> (S.sx - 1), ly = rr.y >> S.sy;
+        const int lx = rr.x >> (M.sx - 1), ly = rr.y >> M.sy;
         int ex = ((lx ^ mx) - mx) + (g.z >> 1), ey = ((ly ^ my) - my) + (g.w >> 1);
         if ((unsigned)ex >= (unsigned)W2 || (unsigned)ey >= (unsigned)H2) {
-            atomicOr(S.err, ERR_BOUNDS);
+            atomicOr(M.err, ERR_BOUNDS);
             ex = min(max(ex, 0), W2 - 1);
             ey = min(max(ey, 0), H2 - 1);
         }
@@ -392,7 +406,6 @@ template <int MODEL>
 __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, int r, int b, int tid, int NS,
                                            int cap_own)
 {
-    const Sys &S = sh.S;
     const RawMeta &M = sh.raw[r];
     const int m = M.m, tw = M.tw, th = M.th;
     const int W2 = 2 * tw + 4, nce = W2 * (th + 2);     // half cells of the extended tile
@@ -455,13 +468,13 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
             O.twL = M.twL; O.twR = M.twR; O.thD = M.thD; O.thU = M.thU;
             O.wide = 15 * mx >= 512;
             sh.chunk[b] = 0;
-            if (carry != M.n_own) atomicOr(S.err, ERR_BOUNDS);
+            if (carry != M.n_own) atomicOr(M.err, ERR_BOUNDS);
         }
     }
     sort_sync(NS);
     // records into cell order (arrival order inside a cell: the sums are
     // exact integers, so this order does not matter); own particles listed
-    const int xc = tw << (S.sx - 1), yc = th << (S.sy - 1);
+    const int xc = tw << (M.sx - 1), yc = th << (M.sy - 1);
     const int4 *R = B.raw(r);
     float4 *P = B.P(b);
     int4 *OWN = B.own(b);
@@ -473,8 +486,8 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
         const int4 rk = R[k];
         float thv = __int_as_float(rk.z);
         float sn, cs;
-        if (MODEL == 1 && S.order != 1) {
-            thv *= (float)S.order;
+        if (MODEL == 1 && M.order != 1) {
+            thv *= (float)M.order;
             sincosf(thv, &sn, &cs);
         } else {
             // |theta| <= pi: the hardware sine/cosine is within 2^-21.4 absolute
@@ -482,10 +495,10 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
         }
         const int flip = sl >> 14;
         if (flip & 1) {
-            if (MODEL != 1 || (S.order & 1)) cs = -cs; else sn = -sn;
+            if (MODEL != 1 || (M.order & 1)) cs = -cs; else sn = -sn;
         }
         if (flip & 2) sn = -sn;
-        P[q] = make_float4((float)(rk.x - xc) * S.ux, (float)(rk.y - yc) * S.uy,
+        P[q] = make_float4((float)(rk.x - xc) * M.ux, (float)(rk.y - yc) * M.uy,
                            __int_as_float(__float2int_rn(cs * kFixNbF)), __int_as_float(__float2int_rn(sn * kFixNbF)));
         if (ex >= 2 && ex < 2 * tw + 2 && ey >= 1 && ey <= th) {
             const int o = q + B.rowoff[ey];
@@ -659,15 +672,50 @@ __host__ __device__ size_t pipe_smem_bytes(int cap, int cap_own, int nceh, int h
 {
     return 4 * (size_t)cap * 16 + 2 * (size_t)cap_own * 16 + 2 * (size_t)round_up(nceh + 1, 8) * 2 +
            2 * (size_t)round_up(cap_own, 8) * 2 + 2 * (size_t)round_up(2 * cap, 8) * 2 +
-           (size_t)round_up(nceh, 4) * 4 + (size_t)(kMaxTile + 4) * 4 + (size_t)round_up(hist_words, 4) * 4;
+           (size_t)round_up(nceh, 4) * 4 + (size_t)(kMaxTile + 4) * 4 + 2 * (size_t)round_up(hist_words, 4) * 4;
 }
 
 // The pipelined step of one system with one species (any model): one block
 // of kPipeThreads threads per SM.
+// Flush output buffer b's measured histograms into the system of the tile it
+// held, and clear them.  tid, nt: the calling threads.
+__device__ __forceinline__ void flush_hist(PipeShared &sh, const PipeBufs &B, int b, long long step, int tid, int nt)
+{
+    if (sh.osys[b] < 0) return;
+    const Sys &S = sh.os[b];
+    if (step < S.meas_until) {
+        int *mh = B.mhist(b);
+        for (int i = tid; i < S.bins_theta + S.bins_nbr; i += nt)
+            if (mh[i]) {
+                atomicAdd(S.hist + i, (unsigned long long)mh[i]);
+                mh[i] = 0;
+            }
+    }
+}
+
+// A warp's integer sums of one system (exact, so order-free) into that
+// system's step accumulators.
+__device__ __forceinline__ void flush_acc(const Acc &acc, unsigned long long *sys_acc, int cur)
+{
+    const long long a[5] = {acc.c, acc.s, acc.n, acc.c2, acc.s2};
+    const int lane = threadIdx.x & 31;
+    unsigned long long *slot =
+        sys_acc + ((size_t)cur * kAccSlots + ((blockIdx.x * 32 + (threadIdx.x >> 5)) & (kAccSlots - 1))) * kAccWords;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const long long v = warp_sum_ll(a[k]);
+        if (lane == 0 && v) atomicAdd(slot + k, (unsigned long long)v);
+    }
+}
+
+// The pipelined step of one or more systems with one species each (any
+// model; the systems of one launch share it): one block of kPipeThreads
+// threads per SM.  tile_base[nsys + 1] is the prefix of the systems' tiles.
 template <int MODEL, int NSORT>
 __global__ void __launch_bounds__(kPipeThreads, 1)
-k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nceh_max, int nce_max, int hist_words,
-            int *dense_list, unsigned char *scratch, size_t scratch_per_block, int scratch_cap, int spill_list_cap)
+k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_base, Ctl *ctl, int cap, int cap_own,
+            int nceh_max, int nce_max, int hist_words, int *dense_list, unsigned char *scratch,
+            size_t scratch_per_block, int scratch_cap, int spill_list_cap)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ PipeShared sh;
@@ -676,14 +724,8 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
     (void)tk0;
     constexpr int NS = NSORT * 32;                          // sort threads
     constexpr int NU = kPipeWarps - 1 - NSORT;              // update warps
-    {
-        const int words = (int)(sizeof(Sys) / 4);
-        const int *src = reinterpret_cast<const int *>(sys);
-        int *dst = reinterpret_cast<int *>(&sh.S);
-        for (int i = tid; i < words; i += kPipeThreads) dst[i] = src[i];
-    }
     PipeBufs B;
-    carve_pipe(B, smem, cap, cap_own, nceh_max);
+    carve_pipe(B, smem, cap, cap_own, nceh_max, hist_words);
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh.bar_raw_full[b], 1);
@@ -692,45 +734,61 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             mbar_init(&sh.bar_empty[b], NU);
             sh.issued[b] = 0;
             sh.taken[b] = 0;
+            sh.osys[b] = -1;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int i = tid; i < nceh_max; i += kPipeThreads) B.hist[i] = 0;
-    for (int i = tid; i < hist_words; i += kPipeThreads) B.mhist[i] = 0;
-    if (tid == 0) sh.flag = *((volatile int *)sys->err) & ERR_TIMEOUT;
+    for (int i = tid; i < 2 * B.mh_stride; i += kPipeThreads) B.mhist0[i] = 0;
+    // pipeline waits that run out are reported in the first system's error word
+    int *const err0 = sys[0].err;
+    if (tid == 0) sh.flag = *((volatile int *)err0) & ERR_TIMEOUT;
     __syncthreads();
     // after a wait has run out the handle is unusable: later steps do nothing
     // (so that a queue of steps cannot each wait out their bounds)
     if (sh.flag) return;
-    const Sys &S = sh.S;
     const long long step = ctl->step;
     const int cur = (int)(step & 1);
-    const int total = S.ntiles;
-    const bool measure = step < S.meas_until;
-    Acc acc = {0, 0, 0, 0, 0};
+    const int total = tile_base[nsys];
     unsigned char *mine = scratch + scratch_per_block * blockIdx.x;
 
     if (warp == 0) {
         // ---------------------------------------------------- copy warp --
-        // Each tile is planned (geometry, segments, counts: global loads)
-        // while the sort warps still hold the raw buffer it will go to; only
-        // writing its meta and issuing its copies wait for that buffer.  A
-        // tile with up to twice the staging capacity goes as one wide tile
+        // Each tile is planned (its system, geometry, segments, counts: global
+        // loads) while the sort warps still hold the raw buffer it will go to;
+        // only writing its meta and issuing its copies wait for that buffer.
+        // A tile with up to twice the staging capacity goes as one wide tile
         // over both raw buffers (from buffer 0's start; the other buffer gets
         // a skip token), so that it stays in the pipeline; larger ones go to
         // the list for the whole-block routine.
         int *spill_e = reinterpret_cast<int *>(mine);
         unsigned char *spill_s = reinterpret_cast<unsigned char *>(spill_e + kPipeMaxSpill);
-        // the spill list of the current buffer is final during this step
-        const int nsp = min(*((volatile int *)&S.spill_cnt[cur]), S.spill_cap);
         unsigned kpar = 0, used = 0;       // per raw buffer: parity of its fills, filled before
         int r = 0;
         int g = 0;
         if (lane == 0) g = atomicAdd(&ctl->tile_next, 1);
         g = __shfl_sync(0xffffffffu, g, 0);
+        // the planned tile: its system, local index and the system's spill
+        // list length (final during this step), re-read when the system changes
+        int si = -1, lt = 0, nsp = 0;
         CopyPlan pl;
+        const Sys &Sc = sh.cs;
+        auto plan = [&](int gg) {
+            const int s2 = nsys > 1 ? sys_of_tile(tile_base, nsys, gg) : 0;
+            if (s2 != si) {
+                si = s2;
+                const int words = (int)(sizeof(Sys) / 4);
+                const int *src = reinterpret_cast<const int *>(sys + si);
+                int *dst = reinterpret_cast<int *>(&sh.cs);
+                for (int i = lane; i < words; i += 32) dst[i] = src[i];
+                __syncwarp();
+                nsp = min(*((volatile int *)&Sc.spill_cnt[cur]), Sc.spill_cap);
+            }
+            lt = gg - (nsys > 1 ? tile_base[si] : 0);
+            copy_plan(Sc, lt, cur, pl);
+        };
         const long long tc0 = PT_NOW();
-        if (g < total) copy_plan(S, g, cur, pl);
+        if (g < total) plan(g);
         bool ok = true;
         for (;;) {
             // the following tile, claimed now so that its round trip overlaps this one's copies
@@ -738,7 +796,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             if (g < total && lane == 0) gn = atomicAdd(&ctl->tile_next, 1);
             int n_spill = 0, n_own = 0, mode = 0;               // 0: whole-block list, 1: normal, 2: wide
             if (g < total) {
-                const bool scanned = copy_spills(S, pl, cur, nsp, spill_e, spill_s, n_spill, n_own);
+                const bool scanned = copy_spills(Sc, pl, cur, nsp, spill_e, spill_s, n_spill, n_own);
                 const int m = pl.m_seg + n_spill;
                 if (scanned && n_spill <= kPipeMaxSpill) {
                     if (m <= cap && n_own <= cap_own) mode = 1;
@@ -751,12 +809,12 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                         dense_list[j] = g + 1;
                     }
                     g = __shfl_sync(0xffffffffu, gn, 0);
-                    if (g < total) copy_plan(S, g, cur, pl);
+                    if (g < total) plan(g);
                     continue;
                 }
                 if (mode == 2 && r == 1) {
                     // a wide tile starts at buffer 0: buffer 1 passes a skip token first
-                    if (((used >> 1) & 1u) && !warp_wait(&sh.bar_raw_empty[1], ((kpar >> 1) & 1u) ^ 1u, S.err)) {
+                    if (((used >> 1) & 1u) && !warp_wait(&sh.bar_raw_empty[1], ((kpar >> 1) & 1u) ^ 1u, err0)) {
                         ok = false;
                         break;
                     }
@@ -771,8 +829,8 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             }
             // the raw buffer (both for a wide tile) must be free (its previous tile sorted)
             const long long tw0 = PT_NOW();
-            if (((used >> r) & 1u) && !warp_wait(&sh.bar_raw_empty[r], ((kpar >> r) & 1u) ^ 1u, S.err)) break;
-            if (mode == 2 && ((used >> 1) & 1u) && !warp_wait(&sh.bar_raw_empty[1], ((kpar >> 1) & 1u) ^ 1u, S.err))
+            if (((used >> r) & 1u) && !warp_wait(&sh.bar_raw_empty[r], ((kpar >> r) & 1u) ^ 1u, err0)) break;
+            if (mode == 2 && ((used >> 1) & 1u) && !warp_wait(&sh.bar_raw_empty[1], ((kpar >> 1) & 1u) ^ 1u, err0))
                 break;
             if (lane == 0) PT_ADD(1, PT_NOW() - tw0);
             RawMeta &M = sh.raw[r];
@@ -783,13 +841,14 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                 }
                 break;
             }
+            const Sys &Sg = Sc;
             const long long ts0 = PT_NOW();
-            copy_commit(pl, g, M, n_spill, n_own, mode == 2, spill_s);
+            copy_commit(pl, Sg, si, lt, M, n_spill, n_own, mode == 2, spill_s);
             if (lane == 0) PT_ADD(2, PT_NOW() - ts0);
             const long long ti0 = PT_NOW();
             int4 *R = B.raw(r);
             // spilled records by plain loads, after the segments
-            for (int j = lane; j < n_spill; j += 32) R[pl.m_seg + j] = S.spill_rec[cur][spill_e[j]];
+            for (int j = lane; j < n_spill; j += 32) R[pl.m_seg + j] = Sg.spill_rec[cur][spill_e[j]];
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             const long long ti1 = PT_NOW();
@@ -822,7 +881,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             const long long tq0 = PT_NOW();
             g = __shfl_sync(0xffffffffu, gn, 0);
             const long long tq1 = PT_NOW();
-            if (g < total) copy_plan(S, g, cur, pl);
+            if (g < total) plan(g);
             if (lane == 0) {
                 PT_ADD(13, tq1 - tq0);
                 PT_ADD(14, PT_NOW() - tq1);
@@ -837,7 +896,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
         int r = 0, b = 0;
         for (;;) {
             long long t0 = PT_NOW();
-            bool ok = mbar_wait(&sh.bar_raw_full[r], (rpar >> r) & 1u, S.err);
+            bool ok = mbar_wait(&sh.bar_raw_full[r], (rpar >> r) & 1u, err0);
             if (!sort_sync_and(NS, ok)) break;
             if (st == 0) PT_ADD(3, PT_NOW() - t0);
             rpar ^= 1u << r;
@@ -852,7 +911,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             const bool wide = !end && sh.raw[r].wide;
             if (wide && b == 1) {
                 // a wide tile fills output buffers 0 and 1: buffer 1 passes a skip token first
-                ok = !((oused >> 1) & 1u) || mbar_wait(&sh.bar_empty[1], ((opar >> 1) & 1u) ^ 1u, S.err);
+                ok = !((oused >> 1) & 1u) || mbar_wait(&sh.bar_empty[1], ((opar >> 1) & 1u) ^ 1u, err0);
                 if (!sort_sync_and(NS, ok)) break;
                 if (st == 0) {
                     sh.out[1].tile = -2;
@@ -867,8 +926,8 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             if (st == 0) PT_ADD(5, PT_NOW() - t0);
             // the output buffer (both for a wide tile) must be free (its previous tile updated)
             t0 = PT_NOW();
-            ok = !((oused >> b) & 1u) || mbar_wait(&sh.bar_empty[b], ((opar >> b) & 1u) ^ 1u, S.err);
-            if (wide) ok = ok && (!((oused >> 1) & 1u) || mbar_wait(&sh.bar_empty[1], ((opar >> 1) & 1u) ^ 1u, S.err));
+            ok = !((oused >> b) & 1u) || mbar_wait(&sh.bar_empty[b], ((opar >> b) & 1u) ^ 1u, err0);
+            if (wide) ok = ok && (!((oused >> 1) & 1u) || mbar_wait(&sh.bar_empty[1], ((opar >> 1) & 1u) ^ 1u, err0));
             if (!sort_sync_and(NS, ok)) break;
             if (st == 0) PT_ADD(4, PT_NOW() - t0);
             if (end) {
@@ -879,6 +938,21 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                 break;
             }
             t0 = PT_NOW();
+            // the buffer's histograms go to the system of its previous tile (when
+            // measuring); the buffer takes this tile's system
+            const int si = sh.raw[r].si;
+            const int oi = sh.osys[b];
+            if (oi >= 0 && step < sh.os[b].meas_until) {
+                flush_hist(sh, B, b, step, st, NS);
+                sort_sync(NS);
+            }
+            if (oi != si) {
+                const int words = (int)(sizeof(Sys) / 4);
+                const int *src = reinterpret_cast<const int *>(sys + si);
+                int *dst = reinterpret_cast<int *>(&sh.os[b]);
+                for (int i = st; i < words; i += NS) dst[i] = src[i];
+                if (st == 0) sh.osys[b] = si;
+            }
             sort_order<MODEL>(sh, B, r, b, st, NS, wide ? 2 * cap_own : cap_own);
             sort_sync(NS);
             if (st == 0) {
@@ -905,11 +979,16 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
         }
     } else {
         // ------------------------------------------------- update warps --
+        // Each warp sums its particles' contributions in registers and hands
+        // them to the system's accumulators when it moves to another system
+        // (a single system: once, at the end).
         unsigned fpar = 0;
         int b = 0;
+        Acc acc = {0, 0, 0, 0, 0};
+        unsigned long long *acc_sys = nullptr;
         for (;;) {
             const long long t0 = PT_NOW();
-            if (!warp_wait(&sh.bar_full[b], (fpar >> b) & 1u, S.err)) break;
+            if (!warp_wait(&sh.bar_full[b], (fpar >> b) & 1u, err0)) break;
             const long long t1 = PT_NOW();
             if (lane == 0) PT_ADD(7, t1 - t0);
             fpar ^= 1u << b;
@@ -922,6 +1001,13 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                 continue;
             }
             if (O.tile < 0) break;
+            const Sys &S = sh.os[b];
+            const bool measure = step < S.meas_until;
+            if (S.acc != acc_sys) {
+                if (acc_sys) flush_acc(acc, acc_sys, cur);
+                acc = {0, 0, 0, 0, 0};
+                acc_sys = S.acc;
+            }
             const float4 *P = B.P(b);
             const unsigned short *cst = B.cstart(b);
             const int4 *OWN = B.own(b);
@@ -932,7 +1018,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                 c = __shfl_sync(0xffffffffu, c, 0);
                 const int o0 = c * 32;
                 if (o0 >= O.n_own) break;
-                update_one<MODEL>(S, O, P, cst, OWN, OQ, o0 + lane, step, measure, B.mhist, acc);
+                update_one<MODEL>(S, O, P, cst, OWN, OQ, o0 + lane, step, measure, B.mhist(b), acc);
             }
             __syncwarp();
             if (lane == 0) {
@@ -941,33 +1027,17 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             }
             b ^= 1;
         }
+        if (acc_sys) flush_acc(acc, acc_sys, cur);
     }
     __syncthreads();
     // copies still in flight (only after a wait ran out): let them land
     if (tid == 0) {
         for (int r = 0; r < 2; ++r)
-            if (sh.issued[r] > sh.taken[r]) mbar_wait(&sh.bar_raw_full[r], (unsigned)(sh.issued[r] - 1) & 1u, S.err);
+            if (sh.issued[r] > sh.taken[r]) mbar_wait(&sh.bar_raw_full[r], (unsigned)(sh.issued[r] - 1) & 1u, err0);
     }
-    // --- the block's sums -> the step's accumulators ----------------------
-    {
-        const long long a[5] = {acc.c, acc.s, acc.n, acc.c2, acc.s2};
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const long long v = warp_sum_ll(a[k]);
-            if (lane == 0) sh.red[k][warp] = v;
-        }
-    }
-    __syncthreads();
-    if (tid < 5) {
-        long long v = 0;
-        for (int w = 0; w < kPipeWarps; ++w) v += sh.red[tid][w];
-        unsigned long long *slot = S.acc + ((size_t)cur * kAccSlots + (blockIdx.x & (kAccSlots - 1))) * kAccWords;
-        atomicAdd(slot + tid, (unsigned long long)v);
-    }
-    if (measure) {
-        for (int i = tid; i < S.bins_theta + S.bins_nbr; i += kPipeThreads)
-            if (B.mhist[i]) atomicAdd(S.hist + i, (unsigned long long)B.mhist[i]);
-    }
+    // --- the last tiles' histograms -> their systems -----------------------
+    flush_hist(sh, B, 0, step, tid, kPipeThreads);
+    flush_hist(sh, B, 1, step, tid, kPipeThreads);
     __syncthreads();
 
     // --- tiles too large for the pipeline's buffers: the whole block, with
@@ -999,7 +1069,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
                     int v;
                     while ((v = *((volatile int *)&dense_list[d])) == 0) {
                         if (clock64() - t0 > kPipeWaitCycles) {
-                            atomicOr(S.err, ERR_TIMEOUT);
+                            atomicOr(err0, ERR_TIMEOUT);
                             break;
                         }
                     }
@@ -1014,20 +1084,23 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
         __syncthreads();
         const int g = sh.dense_tile;
         if (g < 0) break;
-        if (first) {
+        const int si = nsys > 1 ? sys_of_tile(tile_base, nsys, g) : 0;
+        if (first || si != T.sysi) {
+            __syncthreads();                // every thread is done with the previous system
             const int words = (int)(sizeof(Sys) / 4);
-            const int *src = reinterpret_cast<const int *>(&sh.S);
+            const int *src = reinterpret_cast<const int *>(sys + si);
             int *dst = reinterpret_cast<int *>(&T.S);
             for (int i = tid; i < words; i += kPipeThreads) dst[i] = src[i];
             first = false;
         }
+        __syncthreads();
         if (tid == 0) {
-            T.sysi = 0;
-            T.tile = g;
+            T.sysi = si;
+            T.tile = g - tile_base[si];
             T.pf_tile = -1;
             T.total = total;
-            T.nsys = 1;
-            T.tile_base = nullptr;
+            T.nsys = nsys;
+            T.tile_base = tile_base;
             T.next = total;
         }
         __syncthreads();
@@ -1039,7 +1112,7 @@ k_step_pipe(const Sys *__restrict__ sys, Ctl *ctl, int cap, int cap_own, int nce
             if ((size_t)T.m * sizeof(float4) <= stage_bytes(as_cap)) Ah.P = reinterpret_cast<float4 *>(smem);
             tile_body<kPipeThreads, MODEL>(T, Ah, tb, step, spill_e, spill_s, total);
         } else if (tid == 0) {
-            atomicOr(S.err, ERR_STAGE | ERR_LOST);
+            atomicOr(T.S.err, ERR_STAGE | ERR_LOST);
         }
         if (tid == 0) PT_ADD(11, 1);
         __syncthreads();
@@ -1101,8 +1174,8 @@ static cudaError_t launch_pipe_t(const LaunchCfg &L, cudaStream_t st)
 {
     const size_t smem = pipe_smem_bytes(L.pipe_cap, L.pipe_cap_own, L.pipe_nceh, L.hist_words);
     k_step_pipe<MODEL, AAP_PIPE_SORT_WARPS><<<L.pipe_grid, kPipeThreads, smem, st>>>(
-        L.sys, L.ctl, L.pipe_cap, L.pipe_cap_own, L.pipe_nceh, L.nce_max, L.hist_words, L.dense_list, L.scratch,
-        L.scratch_per_block, L.scratch_cap, L.spill_list_cap);
+        L.sys, L.nsys, L.tile_base, L.ctl, L.pipe_cap, L.pipe_cap_own, L.pipe_nceh, L.nce_max, L.hist_words,
+        L.dense_list, L.scratch, L.scratch_per_block, L.scratch_cap, L.spill_list_cap);
     return cudaGetLastError();
 }
 

@@ -166,3 +166,31 @@ def test_pipelined_full_size_sample(lib, oracle):
         compare_one_step(oracle, p, h, idx=idx)
     finally:
         A.aap_destroy(h)
+
+
+def test_pipelined_ensemble_equals_block_kernel(lib):
+    """An ensemble of replicas of different sizes, densities and noise runs
+    through the pipelined kernel (one launch over all replicas' tiles, each
+    output buffer carrying its tile's system) and through the whole-block
+    kernel: every replica's state, measured moments and time-averaged p agree
+    bit for bit."""
+    from paper_2211_15630_gb300 import workloads as W
+
+    ps = W.ensemble_replicas(count=12, seed=9, nmin_log2=8.0, nmax_log2=15.0)
+    qs = W.ensemble_replicas(count=12, seed=9, nmin_log2=8.0, nmax_log2=15.0, threads=512)
+    e1, e2 = A.aap_ens_create(ps), A.aap_ens_create(qs)
+    try:
+        assert A.aap_ens_get_layout(e1, 0).threads == 1024 and A.aap_ens_get_layout(e2, 0).threads == 512
+        for e in (e1, e2):
+            A.aap_ens_step(e, 7)
+            A.aap_ens_measure(e, 40)
+        assert np.array_equal(A.aap_ens_phi_mean(e1), A.aap_ens_phi_mean(e2))
+        for r, p in enumerate(ps):
+            a, b = A.aap_ens_results(e1, r), A.aap_ens_results(e2, r)
+            for f in ("p", "q", "nbar"):
+                assert np.array_equal(np.asarray(getattr(a, f)), np.asarray(getattr(b, f))), (r, f)
+            for u, v in zip(A.aap_ens_get_state(e1, r, p.n), A.aap_ens_get_state(e2, r, p.n)):
+                assert np.array_equal(u, v), r
+    finally:
+        A.aap_ens_destroy(e1)
+        A.aap_ens_destroy(e2)
