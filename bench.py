@@ -15,6 +15,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -551,6 +552,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--clock-window", type=float, default=1.0,
+                    help="seconds of steps under the clock sampler, the timed ones included")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--tile", type=str, default="0x0")
     ap.add_argument("--kn", type=int, default=0,
@@ -602,8 +605,10 @@ def main():
 
     p, h = make(args.eta, 1 + rank)
     lay = A.aap_get_layout(h)
+    tw0 = time.perf_counter()
     A.aap_step(h, args.warmup)
     A.aap_sync(h)
+    est_s = max((time.perf_counter() - tw0) / max(args.warmup, 1), 1e-5)
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)
     except (AttributeError, RuntimeError):
@@ -613,6 +618,20 @@ def main():
         clocks = ClockSampler(local)
         clocks.start()
         time.sleep(0.3)
+    # clock window: the same steps run for at least a second under the
+    # sampler, then the state and step counter are put back (the noise is
+    # counter based, so the timed steps are exactly those a run without the
+    # window would take); the window's samples include the timed region's
+    t_window = time.perf_counter()
+    soak = int(math.ceil(args.clock_window / est_s)) - args.steps
+    if soak > 0:
+        snap = A.aap_get_state(h, args.n)
+        step0 = A.aap_observe(h).step
+        A.aap_step(h, soak)
+        A.aap_sync(h)
+        A.aap_set_state(h, *snap, step=step0)
+        del snap
+        torch.cuda.synchronize()
     A.aap_set_timing(h, True)
     t_begin = time.perf_counter()
     ms = timed(h, args.steps)
@@ -678,7 +697,10 @@ def main():
     kstep_ms = kms[0] / max(klaunch[0], 1)
     achieved = ALG_BYTES * args.n / (kstep_ms / 1e3) / 1e9
     traffic = _traffic(args.n) if args.kn == 0 else None
-    csum = clocks.summary(t_begin, t_end)
+    csum = clocks.summary(t_window, t_end)
+    csum["window_s"] = round(t_end - t_window, 3)
+    csum["window_steps"] = max(soak, 0) + args.steps
+    csum["samples_timed_region"] = clocks.summary(t_begin, t_end)["samples"]
     default_size = args.n == N_FULL and args.L == L_FULL
     workload = ("vicsek_N2^24_L2896_rho2" if default_size else f"vicsek_N{args.n}_L{args.L:g}")
     if args.kn:

@@ -829,9 +829,14 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
             }
             // the raw buffer (both for a wide tile) must be free (its previous tile sorted)
             const long long tw0 = PT_NOW();
-            if (((used >> r) & 1u) && !warp_wait(&sh.bar_raw_empty[r], ((kpar >> r) & 1u) ^ 1u, err0)) break;
-            if (mode == 2 && ((used >> 1) & 1u) && !warp_wait(&sh.bar_raw_empty[1], ((kpar >> 1) & 1u) ^ 1u, err0))
+            if (((used >> r) & 1u) && !warp_wait(&sh.bar_raw_empty[r], ((kpar >> r) & 1u) ^ 1u, err0)) {
+                ok = false;
                 break;
+            }
+            if (mode == 2 && ((used >> 1) & 1u) && !warp_wait(&sh.bar_raw_empty[1], ((kpar >> 1) & 1u) ^ 1u, err0)) {
+                ok = false;
+                break;
+            }
             if (lane == 0) PT_ADD(1, PT_NOW() - tw0);
             RawMeta &M = sh.raw[r];
             if (g >= total) {
@@ -887,7 +892,15 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
                 PT_ADD(14, PT_NOW() - tq1);
             }
         }
-        (void)ok;
+        if (!ok) {
+            // given up: before the block may exit, the bulk copies of the last
+            // fill of each raw buffer must have landed.  Those fills were
+            // issued at least one wait bound ago and nothing has filled the
+            // buffers since, so the phase of each last fill is the barrier's
+            // latest and the bounded wait returns at once.
+            for (int b = 0; b < 2; ++b)
+                if ((used >> b) & 1u) warp_wait(&sh.bar_raw_full[b], ((kpar >> b) & 1u) ^ 1u, err0);
+        }
         if (lane == 0) PT_ADD(0, PT_NOW() - tc0);
     } else if (warp <= NSORT) {
         // --------------------------------------------------- sort warps --
