@@ -255,6 +255,18 @@ int aap_get_results(aap_handle *h, aap_results *out);
  * respect to which call sees the failure. */
 int aap_test_fail_alloc_after(int32_t n);
 
+/* Fault injection for tests of the pipelined step kernel's bounded waits
+ * (its hand-offs between the copy, sort and update warps are mbarrier waits
+ * that give up after a bound; the kernel then sets AAP_ETIMEOUT in the
+ * handle's error word, every later step of that handle returns at once, and
+ * the handle reports AAP_ETIMEOUT at its next synchronising call).
+ * wait_cycles: the bound in SM clock cycles for kernels launched from now on
+ * (<= 0: the default, about 2 s).  stall: 1 makes the copy warp of every
+ * block withhold the first tile it claims (no copies, no arrival), so that
+ * the waits behind it run out; 0 switches it off.  Process-wide; call only
+ * while no step kernel is running.  The GPU context stays usable. */
+int aap_test_pipe_wait(int64_t wait_cycles, int32_t stall);
+
 /* Forget the accumulated measurements (moments and histograms). */
 int aap_clear_results(aap_handle *h);
 

@@ -28,7 +28,7 @@ EXPORTS = (
     "aap_step", "aap_phi_trace", "aap_observe", "aap_get_state", "aap_set_state",
     "aap_step_neighbours", "aap_sync", "aap_get_layout", "aap_set_timing", "aap_get_timing",
     "aap_measure", "aap_get_results", "aap_clear_results", "aap_coarse_grain", "aap_get_histograms",
-    "aap_save", "aap_load", "aap_test_fail_alloc_after",
+    "aap_save", "aap_load", "aap_test_fail_alloc_after", "aap_test_pipe_wait",
     "aap_ens_create", "aap_ens_step", "aap_ens_measure", "aap_ens_phi_mean", "aap_ens_results",
     "aap_ens_get_state", "aap_ens_get_layout", "aap_ens_autotune", "aap_ens_info", "aap_ens_destroy",
     "aap_ens_coarse_grain",
@@ -124,6 +124,7 @@ def load(path: str = LIB_PATH):
         "aap_get_histograms": (C.c_int, [vp, vp, i32, vp, i32]),
         "aap_save": (C.c_int, [vp, C.c_char_p]),
         "aap_test_fail_alloc_after": (C.c_int, [i32]),
+        "aap_test_pipe_wait": (C.c_int, [i64, i32]),
         "aap_load": (C.c_int, [C.c_char_p, vp, P(vp)]),
         "aap_coarse_grain": (C.c_int, [vp, i32, i32, vp]),
         "aap_ens_create": (C.c_int, [vp, i32, vp, P(vp)]),
@@ -233,6 +234,13 @@ def aap_load(path: str, stream: int | None = None) -> C.c_void_p:
 def aap_test_fail_alloc_after(n: int) -> None:
     """Fault injection: the allocation after n more successful ones fails (n < 0: off)."""
     _check(load().aap_test_fail_alloc_after(int(n)))
+
+
+def aap_test_pipe_wait(wait_cycles: int, stall: int) -> None:
+    """Fault injection for the pipelined kernel's bounded waits: the wait
+    bound in SM cycles (<= 0: default) and whether every block's copy warp
+    withholds its first tile (process-wide; call while no step runs)."""
+    _check(load().aap_test_pipe_wait(int(wait_cycles), int(stall)))
 
 
 def aap_destroy(h) -> None:

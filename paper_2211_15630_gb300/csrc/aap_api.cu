@@ -1302,6 +1302,13 @@ int aap_test_fail_alloc_after(int32_t n)
     return AAP_OK;
 }
 
+int aap_test_pipe_wait(int64_t wait_cycles, int32_t stall)
+{
+    if (stall != 0 && stall != 1) return fail(AAP_EINVAL, "stall must be 0 or 1");
+    AAP_CK(aapk::set_pipe_test(wait_cycles, stall));
+    return AAP_OK;
+}
+
 int32_t aap_abi_version(void) { return 2; }
 
 void aap_params_default(aap_params *p)

@@ -48,6 +48,8 @@ __host__ __device__ size_t pipe_smem_bytes(int cap, int cap_own, int nceh, int h
 cudaError_t pipe_static_smem(int model, size_t *bytes);
 // Set the dynamic shared-memory limit of the pipelined step kernel.
 cudaError_t configure_pipe_kernel(int model, size_t smem);
+// test hook: the wait bound of the pipelined kernel (<= 0: default) and the stall injection
+cudaError_t set_pipe_test(long long wait_cycles, int stall);
 // The pipelined step kernel alone (launch_step adds k_finish).
 cudaError_t launch_step_pipe(const LaunchCfg &L, cudaStream_t st);
 

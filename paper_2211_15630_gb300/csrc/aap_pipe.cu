@@ -58,6 +58,11 @@ constexpr int kPipeWarps = kPipeThreads / 32;
 constexpr int kPipeMaxChunks = 2 * kPipeMaxStage / 32 + 1;   // a wide tile spans both raw buffers
 constexpr long long kPipeWaitCycles = 4000000000ll;    // about 2 s at 2 GHz
 
+// test hooks (aap_test_pipe_wait): the wait bound (<= 0: kPipeWaitCycles) and
+// whether every block's copy warp withholds the first tile it claims
+__constant__ long long c_pipe_wait_cycles;
+__constant__ int c_pipe_stall;
+
 }  // namespace
 
 // Optional per-role timing (tracing aid, compiled out unless AAP_PIPE_TIMING
@@ -200,6 +205,7 @@ __device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err)
 {
     const long long t0 = clock64();
+    const long long bound = c_pipe_wait_cycles > 0 ? c_pipe_wait_cycles : kPipeWaitCycles;
     for (;;) {
         unsigned done;
         // the hint lets the hardware suspend the warp (up to 0.1 ms) instead of
@@ -208,7 +214,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
                      "selp.u32 %0, 1, 0, p;\n\t}\n"
                      : "=r"(done) : "r"(sa(bar)), "r"(parity), "r"(100000u) : "memory");
         if (done) return true;
-        if (clock64() - t0 > kPipeWaitCycles) {
+        if (clock64() - t0 > bound) {
             atomicOr(err, ERR_TIMEOUT);
             return false;
         }
@@ -355,10 +361,15 @@ __device__ __forceinline__ void copy_commit(const CopyPlan &pl, const Sys &S, in
     const int sp = lane < kSegs ? start : 0x7fffffff;
     for (int i0 = 0; i0 * 32 < m_seg; i0 += 32) {
         const int k = (i0 + lane) * 32;
-        int n = 0;
+        // binary search over the non-decreasing starts: the last segment s
+        // with start <= k (segment 0 starts at 0)
+        int lo = 0;
 #pragma unroll
-        for (int s = 0; s < kSegs; ++s) n += __shfl_sync(0xffffffffu, sp, s) <= k;
-        if (k < m_seg) M.segc[i0 + lane] = (unsigned char)(n - 1);
+        for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, sp, min(lo + step, 31));
+            if (lo + step < kSegs && v <= k) lo += step;
+        }
+        if (k < m_seg) M.segc[i0 + lane] = (unsigned char)lo;
     }
     __syncwarp();
 }
@@ -790,6 +801,7 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
         const long long tc0 = PT_NOW();
         if (g < total) plan(g);
         bool ok = true;
+        bool withhold = c_pipe_stall != 0;
         for (;;) {
             // the following tile, claimed now so that its round trip overlaps this one's copies
             int gn = 0;
@@ -857,13 +869,18 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             const long long ti1 = PT_NOW();
-            if (lane == 0) {
-                sh.issued[r] += 1;
-                mbar_arrive_tx(&sh.bar_raw_full[r], (unsigned)pl.m_seg * 16u);
+            if (withhold) {
+                // test hook: this fill never arrives, so the waits behind it run out
+                withhold = false;
+            } else {
+                if (lane == 0) {
+                    sh.issued[r] += 1;
+                    mbar_arrive_tx(&sh.bar_raw_full[r], (unsigned)pl.m_seg * 16u);
+                }
+                __syncwarp();
+                if (lane < kSegs && pl.c > 0)
+                    bulk_copy(R + (pl.incl - pl.c), pl.sg.base, (unsigned)pl.c * 16u, &sh.bar_raw_full[r]);
             }
-            __syncwarp();
-            if (lane < kSegs && pl.c > 0)
-                bulk_copy(R + (pl.incl - pl.c), pl.sg.base, (unsigned)pl.c * 16u, &sh.bar_raw_full[r]);
             __syncwarp();
             if (lane == 0) {
                 PT_ADD(15, ti1 - ti0);
@@ -1080,8 +1097,9 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
                     // the entry is written right after its index was taken
                     const long long t0 = clock64();
                     int v;
+                    const long long bound = c_pipe_wait_cycles > 0 ? c_pipe_wait_cycles : kPipeWaitCycles;
                     while ((v = *((volatile int *)&dense_list[d])) == 0) {
-                        if (clock64() - t0 > kPipeWaitCycles) {
+                        if (clock64() - t0 > bound) {
                             atomicOr(err0, ERR_TIMEOUT);
                             break;
                         }
@@ -1170,6 +1188,13 @@ static cudaError_t config_pipe_t(size_t smem)
     }
     return cudaFuncSetAttribute(k_step_pipe<MODEL, AAP_PIPE_SORT_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 std::max(want, limit.load()));
+}
+
+cudaError_t set_pipe_test(long long wait_cycles, int stall)
+{
+    cudaError_t e = cudaMemcpyToSymbol(c_pipe_wait_cycles, &wait_cycles, sizeof(wait_cycles));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_pipe_stall, &stall, sizeof(stall));
 }
 
 cudaError_t configure_pipe_kernel(int model, size_t smem)

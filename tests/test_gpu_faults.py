@@ -2,7 +2,9 @@
 host (aap_test_fail_alloc_after) at every allocation of aap_create must return
 AAP_ENOMEM, release everything the call had taken, and leave the library
 usable; a failed allocation inside a call on a live handle leaves the handle
-usable."""
+usable.  The pipelined step kernel's bounded waits are made to run out by a
+withheld tile (aap_test_pipe_wait): the kernel ends with AAP_ETIMEOUT and the
+context stays usable."""
 import numpy as np
 import pytest
 
@@ -74,3 +76,37 @@ def test_failed_allocation_inside_a_call_keeps_the_handle(lib):
     finally:
         A.aap_test_fail_alloc_after(-1)
         A.aap_destroy(h)
+
+
+def test_pipeline_wait_runs_out_and_reports(lib):
+    """The pipelined step kernel's hand-offs are bounded mbarrier waits.  With
+    the bound shortened to 2e7 SM cycles and every block's copy warp
+    withholding its first tile (a fill that never arrives), the sort and update
+    warps behind it give up, the kernel sets its timeout bit and ends, later
+    steps of the handle return at once, and the handle reports AAP_ETIMEOUT at
+    its next synchronising call.  The context stays usable: afterwards a fresh
+    pipelined handle and a whole-block one agree bit for bit."""
+    p = params(n=30000, lx=122.0, ly=122.0, eta=0.35, v=0.5, seed=19, threads=1024)
+    A.aap_test_pipe_wait(20_000_000, 1)
+    try:
+        h = A.aap_create(p)
+        try:
+            assert A.aap_get_layout(h).threads == 1024
+            A.aap_step(h, 3)
+            with pytest.raises(A.AapError) as e:
+                A.aap_observe(h)
+            assert e.value.code == A.AAP_ETIMEOUT
+        finally:
+            A.aap_destroy(h)
+    finally:
+        A.aap_test_pipe_wait(0, 0)
+    q = params(n=30000, lx=122.0, ly=122.0, eta=0.35, v=0.5, seed=19, threads=512)
+    h1, h2 = A.aap_create(p), A.aap_create(q)
+    try:
+        for h in (h1, h2):
+            A.aap_step(h, 12)
+        for u, v in zip(A.aap_get_state(h1, p.n), A.aap_get_state(h2, p.n)):
+            assert np.array_equal(u, v)
+    finally:
+        A.aap_destroy(h1)
+        A.aap_destroy(h2)
