@@ -10,12 +10,14 @@
 // start at zero and receive zero gradient, so they stay zero).
 //
 // Kernels:
-//   k_conv<CIN, COUT, MODE>   implicit-GEMM convolution on the tcgen05
+//   k_conv_ws<CIN, COUT, MODE> implicit-GEMM convolution on the tcgen05
 //                             tensor cores (BF16 x BF16 -> FP32 accumulator in
-//                             TMEM, M = 128 pixels, N = COUT): forward with
-//                             bias + ReLU, forward with the residual update,
-//                             or the data gradient (flipped, transposed
-//                             weights) masked by the ReLU of the layer input
+//                             TMEM, M = 128 pixels, N = COUT), warp-specialised
+//                             (halo copies, MMA issue and epilogue overlap over
+//                             a block's tiles): forward with bias + ReLU,
+//                             forward with the residual update, or the data
+//                             gradient (flipped, transposed weights) masked by
+//                             the ReLU of the layer input
 //   k_conv_dw<CIN, COUT>      weight and bias gradients, FP32 FMAs over BF16
 //                             operands, one partial per block, reduced in a
 //                             fixed order (deterministic)
@@ -44,7 +46,6 @@ typedef __nv_bfloat16 bf16;
 constexpr int kTH = 16, kTW = 8;
 constexpr int kHaloPix = (kTH + 2) * (kTW + 2);     // 180 input pixels with the 1-pixel ring
 constexpr int kPlane = kHaloPix * 16;               // bytes of one 8-channel plane of the halo tile
-constexpr int kWaitLimit = 1 << 22;                 // bounded mbarrier wait (then the error flag)
 
 __device__ int g_sur_err;                           // sticky: 1 = a tensor-core wait gave up
 
@@ -115,38 +116,6 @@ enum { MODE_RELU = 0, MODE_RESID = 1, MODE_MASK = 2, MODE_LINEAR = 3 };
 
 constexpr int kConvThreads = 256;
 
-// The 16 x 8 tile t (tiles ordered by image, then row, then column) with its
-// one-pixel ring, as 8-channel planes of 16-byte pixels (circular padding).
-template <int CIN>
-__device__ __forceinline__ void stage_halo(unsigned char *s_in, const bf16 *__restrict__ in, int H, int W, int t)
-{
-    constexpr int G = CIN / 8;
-    const int tx = W / kTW, ty = H / kTH;
-    const int b = t / (tx * ty), r = t - b * (tx * ty);
-    const int y0 = (r / tx) * kTH, x0 = (r % tx) * kTW;
-    for (int i = threadIdx.x; i < kHaloPix * G; i += kConvThreads) {
-        const int hp = i / G, g = i - hp * G;
-        const int hy = hp / (kTW + 2), hx = hp - hy * (kTW + 2);
-        int gy = y0 + hy - 1, gx = x0 + hx - 1;
-        gy += (gy < 0) ? H : 0;
-        gy -= (gy >= H) ? H : 0;
-        gx += (gx < 0) ? W : 0;
-        gx -= (gx >= W) ? W : 0;
-        *reinterpret_cast<uint4 *>(s_in + g * kPlane + hp * 16) =
-            *(reinterpret_cast<const uint4 *>(in + (((size_t)b * H + gy) * W + gx) * CIN) + g);
-    }
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t done = 0;
-    for (int it = 0; it < kWaitLimit && !done; ++it)
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}\n"
-                     : "=r"(done) : "r"(bar), "r"(parity));
-    return done != 0;
-}
-
 // out[b, y, x, co] = sum_{tap, ci} w[tap][co][ci] * in[b, (y+dy-1) mod H, (x+dx-1) mod W, ci]
 // (tap = 3 dy + dx), then per MODE:
 //   MODE_RELU   + bias, ReLU, BF16 NHWC out
@@ -160,27 +129,104 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 // every tap is a descriptor view of the same planes (start moved by the tap
 // offset; core matrices 8 pixels of a row, LBO one plane, SBO one halo row).
 // The weights are staged once per block, per (tap, K step) as N x 16 core
-// matrices.  A block walks tiles with two halo buffers and two TMEM
-// accumulators (2 x 32 columns): thread 0 issues the MMAs of tile i and
-// commits them to that buffer's mbarrier while all threads stage tile i+1;
-// then the 8 warps read tile i's accumulator (warp w: TMEM lane quarter
-// w % 4, half of the columns) for the epilogue.
+// matrices.  k_conv_ws below runs the tiles of a block as a pipeline.
+// The halo of tile t staged by nthr threads (thread index i0) of the calling
+// role, asynchronously (cp.async, 16 bytes each, circular padding).
+template <int CIN>
+__device__ __forceinline__ void stage_halo_part(unsigned char *s_in, const bf16 *__restrict__ in, int H, int W, int t,
+                                                int i0, int nthr)
+{
+    constexpr int G = CIN / 8;
+    const int tx = W / kTW, ty = H / kTH;
+    const int b = t / (tx * ty), r = t - b * (tx * ty);
+    const int y0 = (r / tx) * kTH, x0 = (r % tx) * kTW;
+    for (int i = i0; i < kHaloPix * G; i += nthr) {
+        const int hp = i / G, g = i - hp * G;
+        const int hy = hp / (kTW + 2), hx = hp - hy * (kTW + 2);
+        int gy = y0 + hy - 1, gx = x0 + hx - 1;
+        gy += (gy < 0) ? H : 0;
+        gy -= (gy >= H) ? H : 0;
+        gx += (gx < 0) ? W : 0;
+        gx -= (gx >= W) ? W : 0;
+        const uint4 *src = reinterpret_cast<const uint4 *>(in + (((size_t)b * H + gy) * W + gx) * CIN) + g;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(s_in + g * kPlane + hp * 16)),
+                     "l"(src)
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ void bar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Wait for the completion of the phase of the given parity, bounded by about
+// two seconds of SM clock (the hint lets the hardware suspend the warp while
+// it waits); false when the bound ran out (the sticky error flag is set).
+constexpr long long kConvWaitCycles = 4000000000ll;
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done) : "r"(smem_addr(bar)), "r"(parity), "r"(20000u) : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kConvWaitCycles) {
+            atomicOr(&g_sur_err, 1);
+            return false;
+        }
+    }
+}
+
+constexpr int kConvStages = 4;      // halo buffers
+constexpr int kConvAccs = 4;        // TMEM accumulators of 32 columns
+constexpr int kConvProducers = 96;  // threads of warps 1-3
+
+template <int CIN, int COUT>
+__host__ __device__ constexpr size_t conv_ws_smem()
+{
+    constexpr int NP = COUT < 16 ? 16 : COUT;
+    return ((size_t)kConvStages * (CIN / 8) * kPlane + 1023) / 1024 * 1024 + (size_t)9 * (CIN / 16) * ((NP / 8) * 2 * 128) +
+           1024;
+}
+
+// The same convolution as a warp-specialised pipeline over the block's tiles
+// (t = blockIdx.x + i gridDim.x).  Warp 0, one thread: issues the 9 x CIN/16
+// MMAs of tile i from halo buffer i % 4 into accumulator i % 4 and commits
+// them to that buffer's "empty" and that accumulator's "full" mbarrier.
+// Warps 1-3: stage the halo of tile i into buffer i % 4 with cp.async as soon
+// as the buffer's previous MMAs are done (up to four tiles ahead); once a
+// thread's copies of a tile have landed it fences them for the tensor core and
+// arrives on the buffer's "full" mbarrier.  Warps 4-7 (TMEM lane quarters 0-3,
+// one output pixel per thread): read the accumulator, free it, and write the
+// tile's outputs (bias, ReLU, mask or residual per MODE).  Every wait is
+// bounded; a role whose wait runs out stops, and the block drains its copies
+// and MMAs before it frees TMEM.
 template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ in, int H, int W, int ntiles,
-                                                       const bf16 *__restrict__ wt, const float *__restrict__ bias,
-                                                       bf16 *__restrict__ out, const bf16 *__restrict__ mask,
-                                                       const float *__restrict__ resid_in,
-                                                       float *__restrict__ resid_out)
+__global__ void __launch_bounds__(kConvThreads) k_conv_ws(const bf16 *__restrict__ in, int H, int W, int ntiles,
+                                                          const bf16 *__restrict__ wt, const float *__restrict__ bias,
+                                                          bf16 *__restrict__ out, const bf16 *__restrict__ mask,
+                                                          const float *__restrict__ resid_in,
+                                                          float *__restrict__ resid_out)
 {
     constexpr int NP = COUT < 16 ? 16 : COUT;       // MMA N
-    constexpr int NH = NP / 2;                      // accumulator columns read by one warp
     constexpr int G = CIN / 8;                      // 8-channel groups of the input
     constexpr int KC = CIN / 16;                    // K steps per tap
     constexpr int WBLK = (NP / 8) * 2 * 128;        // bytes of one (tap, K step) weight block
-    __shared__ __align__(1024) unsigned char s_in[2][G * kPlane];
-    __shared__ __align__(1024) unsigned char s_w[9 * KC * WBLK];
+    constexpr int NS = kConvStages, NA = kConvAccs;
+    extern __shared__ unsigned char s_dyn[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)s_dyn + 1023) & ~(uintptr_t)1023);
+    unsigned char *s_in = base;                     // [NS][G * kPlane]
+    unsigned char *s_w = base + ((size_t)NS * G * kPlane + 1023) / 1024 * 1024;
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], afull[NA], aempty[NA];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < 9 * NP * G; i += kConvThreads) {
         const int tap = i / (NP * G), rem = i - tap * (NP * G), co = rem / G, g = rem - co * G;
@@ -189,103 +235,147 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ 
         *reinterpret_cast<uint4 *>(s_w + (tap * KC + (g >> 1)) * WBLK + ((co >> 3) * 2 + (g & 1)) * 128 +
                                    (co & 7) * 16) = v;
     }
-    if (blockIdx.x < ntiles) stage_halo<CIN>(s_in[0], in, H, W, blockIdx.x);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_bar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_bar[1])), "r"(1));
+        for (int k = 0; k < NS; ++k) {
+            bar_init(&full[k], kConvProducers);
+            bar_init(&empty[k], 1);
+        }
+        for (int k = 0; k < NA; ++k) {
+            bar_init(&afull[k], 1);
+            bar_init(&aempty[k], 128);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                     "r"(64));
+                     "r"(32 * NA));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    asm volatile("fence.proxy.async.shared::cta;");   // staged operands visible to the tensor core
+    asm volatile("fence.proxy.async.shared::cta;");   // the staged weights, for the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = s_tmem;
     const int tx = W / kTW, ty = H / kTH;
-    bool ok = true;
-    int it = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-        const int buf = it & 1;
-        if (tid == 0) {
+    if (warp == 0) {
+        // ------------------------------------------------------------ MMA --
+        if (lane == 0) {
             constexpr uint32_t idesc = umma_idesc_bf16(128, NP);
-            const uint32_t a0 = smem_addr(s_in[buf]), w0 = smem_addr(s_w);
-            uint32_t acc = 0;
+            const uint32_t w0 = smem_addr(s_w);
+            int i = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+                const int st = i % NS, ac = i % NA;
+                if (!bar_wait(&full[st], (uint32_t)(i / NS) & 1u)) break;
+                if (i >= NA && !bar_wait(&aempty[ac], (uint32_t)((i / NA) & 1) ^ 1u)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t a0 = smem_addr(s_in + (size_t)st * G * kPlane);
+                uint32_t acc = 0;
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap - dy * 3;
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap - dy * 3;
 #pragma unroll
-                for (int kc = 0; kc < KC; ++kc) {
-                    const uint64_t ad =
-                        umma_desc(a0 + 2 * kc * kPlane + (dy * (kTW + 2) + dx) * 16, kPlane, (kTW + 2) * 16);
-                    const uint64_t bd = umma_desc(w0 + (tap * KC + kc) * WBLK, 128, 256);
-                    umma_bf16(tmem + buf * 32, ad, bd, idesc, acc);
-                    acc = 1;
+                    for (int kc = 0; kc < KC; ++kc) {
+                        const uint64_t ad =
+                            umma_desc(a0 + 2 * kc * kPlane + (dy * (kTW + 2) + dx) * 16, kPlane, (kTW + 2) * 16);
+                        const uint64_t bd = umma_desc(w0 + (tap * KC + kc) * WBLK, 128, 256);
+                        umma_bf16(tmem + ac * 32, ad, bd, idesc, acc);
+                        acc = 1;
+                    }
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_addr(&empty[st])));
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_addr(&afull[ac])));
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_addr(&s_bar[buf])));
+            // MMAs still running (only when a wait ran out): the last commit
+            // covers every earlier MMA of this thread
+            if (i > 0 && blockIdx.x + (long long)i * gridDim.x < ntiles) {
+                const int last = i - 1;
+                if (!bar_wait(&afull[last % NA], (uint32_t)(last / NA) & 1u))
+                    bar_wait(&afull[last % NA], (uint32_t)(last / NA) & 1u);
+            }
         }
-        // the next tile's input while the tensor core works (its buffer's
-        // previous MMAs were waited for in the previous iteration)
-        if (t + (int)gridDim.x < ntiles) stage_halo<CIN>(s_in[buf ^ 1], in, H, W, t + gridDim.x);
-        // every thread waits with a bound; the block then agrees on the outcome
-        const bool done = __syncthreads_and(mbar_wait(smem_addr(&s_bar[buf]), (uint32_t)(it >> 1) & 1u)) != 0;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (!done) {
-            // Give-up path.  The MMAs of this buffer may still be running and
-            // writing its TMEM columns (reading s_in / s_w), so the block waits
-            // a second bounded time for that commit before it frees TMEM and
-            // exits; the other buffer's MMAs were already waited for.  Should
-            // the second wait also run out, the tensor core has stopped, and
-            // the block frees its columns all the same (nothing else can end).
-            ok = false;
-            if (tid == 0) atomicOr(&g_sur_err, 1);
-            mbar_wait(smem_addr(&s_bar[buf]), (uint32_t)(it >> 1) & 1u);
-        } else {
-            const int q = warp & 3, h = warp >> 2;
-            uint32_t r[NH];
-            tmem_load<NH>(tmem + buf * 32 + h * NH + ((uint32_t)(q * 32) << 16), r);
-            const int m = q * 32 + lane;
+        __syncwarp();
+    } else if (warp < 4) {
+        // -------------------------------------------------------- producers --
+        const int pt = tid - 32;
+        int i = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int st = i % NS;
+            if (i >= NS && !bar_wait(&empty[st], (uint32_t)((i / NS) & 1) ^ 1u)) {
+                ok = false;
+                break;
+            }
+            stage_halo_part<CIN>(s_in + (size_t)st * G * kPlane, in, H, W, t, pt, kConvProducers);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (i >= 1) {
+                // the previous tile's copies of this thread have landed
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bar_arrive(&full[(i - 1) % NS]);
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (ok && i >= 1) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bar_arrive(&full[(i - 1) % NS]);
+        }
+    } else {
+        // --------------------------------------------------------- epilogue --
+        const int q = warp & 3;                     // TMEM lane quarter of this warp
+        const int m = q * 32 + lane;                // output pixel of the tile
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int ac = i % NA;
+            // warp-uniform: the TMEM load below is a whole-warp instruction
+            if (!__all_sync(0xffffffffu, bar_wait(&afull[ac], (uint32_t)(i / NA) & 1u))) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            uint32_t r[NP];
+            tmem_load<NP>(tmem + ac * 32 + ((uint32_t)(q * 32) << 16), r);
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            bar_arrive(&aempty[ac]);
             const int b = t / (tx * ty), rr = t - b * (tx * ty);
             const int y = (rr / tx) * kTH + m / kTW, x = (rr % tx) * kTW + m % kTW;
             const size_t pix = ((size_t)b * H + y) * W + x;
+            if (MODE == MODE_RESID) {
 #pragma unroll
-            for (int j = 0; j < NH; j += 2) {
-                const int co = h * NH + j;
-                if (co >= COUT) break;
-                float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
-                if (MODE != MODE_MASK) {
-                    v0 += bias[co];
-                    v1 += bias[co + 1];
-                }
-                if (MODE == MODE_RELU) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                }
-                if (MODE == MODE_MASK) {
-                    const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * COUT + co);
-                    if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
-                    if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
-                }
-                if (MODE == MODE_RESID) {
-                    resid_out[pix * 8 + co] = resid_in[pix * 8 + co] + v0;
-                    resid_out[pix * 8 + co + 1] = resid_in[pix * 8 + co + 1] + v1;
-                } else {
-                    *reinterpret_cast<__nv_bfloat162 *>(out + pix * COUT + co) = __floats2bfloat162_rn(v0, v1);
+                for (int co = 0; co < COUT; ++co)
+                    resid_out[pix * 8 + co] = resid_in[pix * 8 + co] + (__uint_as_float(r[co]) + bias[co]);
+            } else {
+                // COUT bf16 outputs of this pixel, written 16 bytes at a time
+#pragma unroll
+                for (int c0 = 0; c0 < COUT; c0 += 8) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int j = 0; j < 8; j += 2) {
+                        const int co = c0 + j;
+                        float v0 = __uint_as_float(r[co]), v1 = __uint_as_float(r[co + 1]);
+                        if (MODE != MODE_MASK) {
+                            v0 += bias[co];
+                            v1 += bias[co + 1];
+                        }
+                        if (MODE == MODE_RELU) {
+                            v0 = fmaxf(v0, 0.f);
+                            v1 = fmaxf(v1, 0.f);
+                        }
+                        if (MODE == MODE_MASK) {
+                            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * COUT + co);
+                            if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                            if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                        }
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                        pk[j / 2] = *reinterpret_cast<const uint32_t *>(&h2);
+                    }
+                    *reinterpret_cast<uint4 *>(out + pix * COUT + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 }
             }
         }
-        asm volatile("fence.proxy.async.shared::cta;");   // the next tile's staged input
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (!ok) break;                                   // block-uniform (from __syncthreads_and)
     }
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32 * NA));
 }
 
 // Weight / bias gradient: dw[co][tap][ci] = sum_p dy[p][co] x[p + tap - 1][ci],
@@ -602,13 +692,44 @@ int sm_count()
     return n;
 }
 
+// The dynamic shared memory of each convolution (above the 48 KB default),
+// set once per instantiation.
+template <int CIN, int COUT, int MODE>
+cudaError_t conv_configure()
+{
+    static std::atomic<int> configured{0};
+    if (configured.load()) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_conv_ws<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)conv_ws_smem<CIN, COUT>());
+    if (e == cudaSuccess) configured.store(1);
+    return e;
+}
+
+// Every instantiation the library launches (called before a predict call
+// can be captured into a graph).
+cudaError_t conv_configure_all()
+{
+    const cudaError_t es[] = {conv_configure<16, 32, MODE_RELU>(),   conv_configure<32, 32, MODE_RELU>(),
+                              conv_configure<32, 8, MODE_RESID>(),   conv_configure<16, 32, MODE_MASK>(),
+                              conv_configure<32, 32, MODE_MASK>(),   conv_configure<16, 32, MODE_LINEAR>(),
+                              conv_configure<32, 32, MODE_LINEAR>(), conv_configure<32, 8, MODE_RELU>(),
+                              conv_configure<32, 8, MODE_LINEAR>(),  conv_configure<16, 8, MODE_RELU>(),
+                              conv_configure<16, 8, MODE_LINEAR>()};
+    for (cudaError_t e : es)
+        if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
 template <int CIN, int COUT, int MODE>
 cudaError_t conv(const bf16 *in, int B, int H, int W, const bf16 *w, const float *bias, bf16 *out, const bf16 *mask,
                  const float *rin, float *rout, cudaStream_t st)
 {
     const int ntiles = (W / kTW) * (H / kTH) * B;
-    k_conv<CIN, COUT, MODE><<<std::min(ntiles, 4 * sm_count()), kConvThreads, 0, st>>>(in, H, W, ntiles, w, bias, out,
-                                                                                       mask, rin, rout);
+    constexpr size_t smem = conv_ws_smem<CIN, COUT>();
+    const cudaError_t ce = conv_configure<CIN, COUT, MODE>();
+    if (ce != cudaSuccess) return ce;
+    k_conv_ws<CIN, COUT, MODE><<<std::min(ntiles, 2 * sm_count()), kConvThreads, smem, st>>>(in, H, W, ntiles, w, bias,
+                                                                                            out, mask, rin, rout);
     return cudaGetLastError();
 }
 
@@ -704,7 +825,7 @@ void sfree(aap_sur *s)
 }
 
 // Output channels of the data-gradient weight layout of layer l (the last
-// layer's 8 are padded to 16, the smallest input width of k_conv).
+// layer's 8 are padded to 16, the smallest input width of k_conv_ws).
 int cob_of(int l) { return std::max(kLayerCout[l], 16); }
 
 int pack_all(aap_sur *s)
@@ -804,6 +925,7 @@ int aap_sur_create(const aap_sur_params *p, void *stream, aap_sur **out)
     if (!(p->rho0 > 0) || !(p->eta_scale > 0) || !(p->lr > 0) || !(p->eps > 0))
         return sfail(AAP_EINVAL, "rho0, eta_scale, lr and eps must be positive");
     if (p->conserve < 0 || p->conserve > 3) return sfail(AAP_EINVAL, "conserve must be in [0, 3]");
+    if (conv_configure_all() != cudaSuccess) return sfail(AAP_ECUDA, "configuring the convolution kernels");
     aap_sur *s = new aap_sur();
     s->p = *p;
     s->stream = static_cast<cudaStream_t>(stream);
