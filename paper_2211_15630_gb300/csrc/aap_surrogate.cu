@@ -18,9 +18,12 @@
 //                             forward with the residual update, or the data
 //                             gradient (flipped, transposed weights) masked by
 //                             the ReLU of the layer input
-//   k_conv_dw<CIN, COUT>      weight and bias gradients, FP32 FMAs over BF16
-//                             operands, one partial per block, reduced in a
-//                             fixed order (deterministic)
+//   k_conv_dw_tc<CIN, COUT>   weight and bias gradients on the tcgen05
+//                             tensor cores (the transposed dy and shifted input
+//                             rows as K-major operands, pixels along K, one
+//                             TMEM accumulator per tap for all of a block's
+//                             tiles), one partial per block, reduced in a fixed
+//                             order (deterministic)
 //   k_adam                    Adam step on the FP32 master weights
 #include <algorithm>
 #include <atomic>
@@ -378,66 +381,226 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_ws(const bf16 *__restrict
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32 * NA));
 }
 
-// Weight / bias gradient: dw[co][tap][ci] = sum_p dy[p][co] x[p + tap - 1][ci],
-// db[co] = sum_p dy[p][co], over a band of `rows` image rows per block (dy
-// holds dy_stride channels per pixel, of which the first COUT are used).
-// part[block][COUT * 9 * CIN + COUT] receives the block's partial sums.
+// Weight / bias gradient on the tensor cores.  For every tap (dy, dx) the
+// block accumulates D_tap[co][ci] = sum_p dy[p][co] x[p + tap - 1][ci] over
+// all its tiles in TMEM (tap accumulator at columns 32 tap): one MMA per tap
+// and K step of 16 pixels (two tile rows), M = 128 rows of which the first
+// COUT are the output channels (the rest read other rows of the transposed dy
+// and are never read back), N = CIN, both operands K-major (pixels along K):
+//   A = dyT[py][co][8 px]       (LBO: one tile row, SBO: 8 channels = 128 B)
+//   B = xT[dx][hy][ci][8 px]    the halo row hy seen from column dx
+//                               (LBO: one halo row, SBO: 128 B)
+// Warps 1-7 fetch a tile's halo and dy into one of two raw staging areas
+// (cp.async, one tile ahead), then write the transposed operands into one of
+// two stages (and add up db in FP32, each
+// thread always for the same output channel, in a fixed order); warp 0, one
+// thread, issues the MMAs of a stage and commits them to its "empty"
+// mbarrier; after the last tile warp 4 (TMEM lanes 0-31 = the output
+// channels) writes the block's partial dw and the threads' db partials are
+// summed in a fixed order.  part[block][COUT * 9 * CIN + COUT].
+constexpr int kDwThreads = 256;
+constexpr int kDwT = kDwThreads - 32;          // transposing threads (warps 1-7)
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) k_conv_dw(const bf16 *__restrict__ x, const bf16 *__restrict__ dy,
-                                                 int dy_stride, int H, int W, int rows, float *__restrict__ part)
+__host__ __device__ constexpr int dw_coutp() { return COUT < 8 ? 8 : COUT; }
+
+template <int CIN, int COUT>
+__host__ __device__ constexpr size_t dw_xt_bytes() { return (size_t)3 * (kTH + 2) * CIN * 16; }
+
+template <int CIN, int COUT>
+__host__ __device__ constexpr size_t dw_dyt_bytes()
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    bf16 *s_x = reinterpret_cast<bf16 *>(smem_raw);                 // (rows+2) x (W+2) x CIN
-    bf16 *s_dy = s_x + (size_t)(rows + 2) * (W + 2) * CIN;          // rows x W x COUT
-    const int b = blockIdx.y, r0 = blockIdx.x * rows;
-    constexpr int VX = CIN / 8, VD = COUT / 8;
-    for (int i = threadIdx.x; i < (rows + 2) * (W + 2) * VX; i += 256) {
-        const int pix = i / VX, v = i - pix * VX;
-        const int hy = pix / (W + 2), hx = pix - hy * (W + 2);
-        int gy = r0 + hy - 1, gx = hx - 1;
-        gy += (gy < 0) ? H : 0;
-        gy -= (gy >= H) ? H : 0;
-        gx += (gx < 0) ? W : 0;
-        gx -= (gx >= W) ? W : 0;
-        *reinterpret_cast<uint4 *>(s_x + (size_t)pix * CIN + v * 8) =
-            *(reinterpret_cast<const uint4 *>(x + (((size_t)b * H + gy) * W + gx) * CIN) + v);
+    // 16 tile rows of COUTP channel rows, plus what the 128 MMA rows of the
+    // last K step read beyond them
+    return ((size_t)(kTH - 1) * dw_coutp<CIN, COUT>() * 16 + 2048 + 1023) / 1024 * 1024;
+}
+
+template <int CIN, int COUT>
+__host__ __device__ constexpr size_t dw_tc_smem()
+{
+    return 2 * ((size_t)kHaloPix * CIN * 2 + (size_t)kTH * kTW * COUT * 2) + 1024 +
+           2 * (dw_xt_bytes<CIN, COUT>() + dw_dyt_bytes<CIN, COUT>()) + 1024;
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kDwThreads, 1) k_conv_dw_tc(const bf16 *__restrict__ x, const bf16 *__restrict__ dy,
+                                                             int dy_stride, int H, int W, int ntiles,
+                                                             float *__restrict__ part)
+{
+    constexpr int COUTP = dw_coutp<CIN, COUT>();
+    constexpr size_t XT = dw_xt_bytes<CIN, COUT>(), DYT = dw_dyt_bytes<CIN, COUT>();
+    extern __shared__ unsigned char s_dyn[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)s_dyn + 1023) & ~(uintptr_t)1023);
+    unsigned char *stage0 = base;                                    // [2][XT + DYT]
+    bf16 *raw_x = reinterpret_cast<bf16 *>(base + 2 * (XT + DYT));   // [2][18 * 10][CIN]
+    bf16 *raw_dy = raw_x + 2 * kHaloPix * CIN;                       // [2][128][COUT]
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t tfull[2], tempty[2], done;
+    __shared__ float s_db[kDwT];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) {
+            bar_init(&tfull[k], kDwT);
+            bar_init(&tempty[k], 1);
+        }
+        bar_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    for (int i = threadIdx.x; i < rows * W * VD; i += 256) {
-        const int pix = i / VD, v = i - pix * VD;
-        const int yy = pix / W, xx = pix - yy * W;
-        *reinterpret_cast<uint4 *>(s_dy + (size_t)pix * COUT + v * 8) =
-            *(reinterpret_cast<const uint4 *>(dy + (((size_t)b * H + r0 + yy) * W + xx) * dy_stride) + v);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+    const int tx = W / kTW, ty = H / kTH;
+    bool ok = true;
+    if (warp == 0) {
+        // ------------------------------------------------------------ MMA --
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma_idesc_bf16(128, CIN);
+            int i = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+                const int st = i & 1;
+                if (!bar_wait(&tfull[st], (uint32_t)(i >> 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t xt = smem_addr(stage0 + st * (XT + DYT)), dyt = xt + (uint32_t)XT;
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ddy = tap / 3, ddx = tap - ddy * 3;
+#pragma unroll
+                    for (int ks = 0; ks < kTH / 2; ++ks) {
+                        const uint64_t ad = umma_desc(dyt + 2 * ks * COUTP * 16, COUTP * 16, 128);
+                        const uint64_t bd = umma_desc(xt + (ddx * (kTH + 2) + 2 * ks + ddy) * CIN * 16, CIN * 16, 128);
+                        umma_bf16(tmem + tap * 32, ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_addr(&tempty[st])));
+            }
+            // every MMA of this block (or, after a wait ran out, those issued)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_addr(&done)));
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------- transposers --
+        const int pt = tid - 32;
+        float db = 0.f;                              // for output channel pt % COUT
+        // the raw halo and dy of tile t into raw buffer rb, asynchronously
+        const auto fetch = [&](int t, int rb) {
+            const int b = t / (tx * ty), rr = t - b * (tx * ty);
+            const int y0 = (rr / tx) * kTH, x0 = (rr % tx) * kTW;
+            bf16 *rx = raw_x + rb * (kHaloPix * CIN), *rd = raw_dy + rb * (kTH * kTW * COUT);
+            for (int k = pt; k < kHaloPix * (CIN / 8); k += kDwT) {
+                const int hp = k / (CIN / 8), g = k - hp * (CIN / 8);
+                const int hy = hp / (kTW + 2), hx = hp - hy * (kTW + 2);
+                int gy = y0 + hy - 1, gx = x0 + hx - 1;
+                gy += (gy < 0) ? H : 0;
+                gy -= (gy >= H) ? H : 0;
+                gx += (gx < 0) ? W : 0;
+                gx -= (gx >= W) ? W : 0;
+                const uint4 *src = reinterpret_cast<const uint4 *>(x + (((size_t)b * H + gy) * W + gx) * CIN) + g;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(rx + hp * CIN + g * 8)),
+                             "l"(src)
+                             : "memory");
+            }
+            for (int k = pt; k < kTH * kTW * (COUT / 8); k += kDwT) {
+                const int px = k / (COUT / 8), g = k - px * (COUT / 8);
+                const int yy = y0 + px / kTW, xx = x0 + px % kTW;
+                const uint4 *src = reinterpret_cast<const uint4 *>(dy + (((size_t)b * H + yy) * W + xx) * dy_stride) + g;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(rd + px * COUT + g * 8)),
+                             "l"(src)
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        if ((int)blockIdx.x < ntiles) fetch(blockIdx.x, 0);
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int st = i & 1, rb = i & 1;
+            // the next tile's raw data in flight while this one is transposed
+            const bool more = t + (int)gridDim.x < ntiles;
+            if (more) {
+                fetch(t + gridDim.x, rb ^ 1);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            // the stage must be free (its previous tile's MMAs are done); the
+            // outcome is made the same for every transposing thread, and the
+            // barrier also completes every thread's copies of this tile
+            const bool free_ok = i < 2 || bar_wait(&tempty[st], (uint32_t)((i >> 1) - 1) & 1u);
+            int all_ok;
+            asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                         "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+                         : "=r"(all_ok) : "r"((int)free_ok), "r"(kDwT) : "memory");
+            if (!all_ok) {
+                ok = false;
+                break;
+            }
+            const bf16 *rx = raw_x + rb * (kHaloPix * CIN), *rd = raw_dy + rb * (kTH * kTW * COUT);
+            unsigned char *xt = stage0 + st * (XT + DYT), *dyt = xt + XT;
+            // xT[dx][hy][ci][j] = halo[hy][dx + j][ci]
+            for (int k = pt; k < 3 * (kTH + 2) * CIN; k += kDwT) {
+                const int ci = k % CIN, r = k / CIN, hy = r % (kTH + 2), dxx = r / (kTH + 2);
+                const unsigned short *src = reinterpret_cast<const unsigned short *>(rx + (hy * (kTW + 2) + dxx) * CIN + ci);
+                uint32_t w4[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w4[j] = (uint32_t)src[(2 * j) * CIN] | ((uint32_t)src[(2 * j + 1) * CIN] << 16);
+                *reinterpret_cast<uint4 *>(xt + ((size_t)(dxx * (kTH + 2) + hy) * CIN + ci) * 16) =
+                    make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+            // dyT[py][co][j] = dy[py][j][co]; db of this thread's channel
+            for (int k = pt; k < kTH * COUT; k += kDwT) {
+                const int co = k % COUT, py = k / COUT;
+                const unsigned short *src = reinterpret_cast<const unsigned short *>(rd + py * kTW * COUT + co);
+                uint32_t w4[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned short lo = src[(2 * j) * COUT], hi = src[(2 * j + 1) * COUT];
+                    db += __uint_as_float((uint32_t)lo << 16);
+                    db += __uint_as_float((uint32_t)hi << 16);
+                    w4[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+                }
+                *reinterpret_cast<uint4 *>(dyt + ((size_t)py * COUTP + co) * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // for the tensor core
+            bar_arrive(&tfull[st]);
+            asm volatile("bar.sync 1, %0;" ::"r"(kDwT) : "memory");       // raw buffer rb read by all
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        s_db[pt] = db;
     }
     __syncthreads();
-    constexpr int TPC = 256 / COUT;      // threads per output channel
-    constexpr int CPT = CIN / TPC;       // input channels per thread
-    static_assert(CPT >= 1 && CIN % TPC == 0, "channel split");
-    const int co = threadIdx.x / TPC, cb = (threadIdx.x % TPC) * CPT;
-    float acc[9][CPT];
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) acc[k][j] = 0.f;
-    float accb = 0.f;
-    for (int yy = 0; yy < rows; ++yy) {
-        for (int xx = 0; xx < W; ++xx) {
-            const float d = __bfloat162float(s_dy[((size_t)yy * W + xx) * COUT + co]);
-            accb += d;
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int ty = tap / 3, tx = tap - ty * 3;
-                const bf16 *px = s_x + ((size_t)(yy + ty) * (W + 2) + xx + tx) * CIN + cb;
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) acc[tap][j] = fmaf(d, __bfloat162float(px[j]), acc[tap][j]);
-            }
+    // all MMAs issued by this block are complete before TMEM is read or freed
+    const bool fin = __syncthreads_and(bar_wait(&done, 0u)) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    float *pb = part + (size_t)blockIdx.x * (COUT * 9 * CIN + COUT);
+    if (fin && warp == 4) {
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+            uint32_t r[32];
+            tmem_load<32>(tmem + tap * 32, r);
+            if (lane < COUT)
+                for (int ci = 0; ci < CIN; ++ci) pb[((size_t)lane * 9 + tap) * CIN + ci] = __uint_as_float(r[ci]);
         }
     }
-    float *pb = part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (COUT * 9 * CIN + COUT);
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) pb[((size_t)co * 9 + tap) * CIN + cb + j] = acc[tap][j];
-    if (threadIdx.x % TPC == 0) pb[COUT * 9 * CIN + co] = accb;
+    if (tid < COUT) {
+        float sdb = 0.f;
+        for (int k = tid; k < kDwT; k += COUT) sdb += s_db[k];
+        pb[COUT * 9 * CIN + tid] = sdb;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    (void)ok;
 }
 
 // out[i] = sum_k part[k][i] in a fixed order (deterministic).
@@ -736,33 +899,26 @@ cudaError_t conv(const bf16 *in, int B, int H, int W, const bf16 *w, const float
 int dw_rows(int H) { return H % 4 == 0 ? 4 : (H % 2 == 0 ? 2 : 1); }
 
 template <int CIN, int COUT>
-size_t dw_smem(int H, int W)
-{
-    const int rows = dw_rows(H);
-    return (size_t)(rows + 2) * (W + 2) * CIN * 2 + (size_t)rows * W * COUT * 2;
-}
-
-template <int CIN, int COUT>
 cudaError_t conv_dw(const bf16 *x, const bf16 *dy, int dy_stride, int B, int H, int W, float *part, float *dw,
                     float *db, cudaStream_t st)
 {
-    const int rows = dw_rows(H);
-    const size_t smem = dw_smem<CIN, COUT>(H, W);
-    // the limit only ever grows, so that a captured graph of a wider field
-    // still launches after a narrower one was configured
-    static std::atomic<int> limit{0};
-    int prev = limit.load();
-    while ((int)smem > prev && !limit.compare_exchange_weak(prev, (int)smem)) {
+    constexpr size_t smem = dw_tc_smem<CIN, COUT>();
+    static std::atomic<int> configured{0};
+    if (!configured.load()) {
+        const cudaError_t e0 = cudaFuncSetAttribute(k_conv_dw_tc<CIN, COUT>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e0 != cudaSuccess) return e0;
+        configured.store(1);
     }
-    cudaError_t e = cudaFuncSetAttribute(k_conv_dw<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         std::max((int)smem, limit.load()));
+    const int ntiles = (W / kTW) * (H / kTH) * B;
+    // one persistent block per SM (each holds 512 TMEM columns), no more
+    // partials than the documented scratch holds
+    const int nblk = std::max(1, std::min(std::min(ntiles, sm_count()), (H / dw_rows(H)) * B));
+    k_conv_dw_tc<CIN, COUT><<<nblk, kDwThreads, smem, st>>>(x, dy, dy_stride, H, W, ntiles, part);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 grid(H / rows, B);
-    k_conv_dw<CIN, COUT><<<grid, 256, smem, st>>>(x, dy, dy_stride, H, W, rows, part);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int len = COUT * 9 * CIN + COUT;
-    k_reduce_parts<<<std::max(1, (len + 255) / 256), 256, 0, st>>>(part, (int)(grid.x * grid.y), len, dw,
-                                                                      COUT * 9 * CIN, db);
+    k_reduce_parts<<<std::max(1, (len + 255) / 256), 256, 0, st>>>(part, nblk, len, dw, COUT * 9 * CIN, db);
     return cudaGetLastError();
 }
 
@@ -963,7 +1119,8 @@ int aap_sur_create(const aap_sur_params *p, void *stream, aap_sur **out)
     A(&s->state2, pix * 8 * 4);
     A(&s->target, pix * 8 * 4);
     A(&s->eta, (size_t)s->maxb * 4);
-    // weight-gradient partials: one per (row band, sample)
+    // weight-gradient partials: one per block of the gradient kernel (at most
+    // one per row band and sample)
     const size_t nblk = (size_t)(s->H / dw_rows(s->H)) * s->maxb;
     s->part_floats = nblk * (32 * 9 * 32 + 32);
     A(&s->part, s->part_floats * 4);
