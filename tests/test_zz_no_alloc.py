@@ -148,3 +148,40 @@ def test_noalloc_rejects_too_many_bins(lib):
         A.aap_coarse_grain_noalloc(0, 0, 0, 0, 10.0, 10.0, 512, 512, 1, 0)
     assert e.value.code == A.AAP_EINVAL
     assert "exceeds" in str(e.value)
+
+
+def test_noalloc_allocates_nothing_and_runs_in_a_captured_graph(lib):
+    """The promise of the entry point: after a first call, a call changes the
+    device's free memory by nothing, and it can be captured into a CUDA graph
+    (where cudaMalloc is barred); the replayed graph gives the fields of a
+    direct call."""
+    p = A.aap_params_default(n=1 << 16, lx=181.0, ly=181.0, eta=0.4, seed=23)
+    h = A.aap_create(p)
+    try:
+        A.aap_step(h, 5)
+        x, y, th = A.aap_get_state(h, p.n)
+    finally:
+        A.aap_destroy(h)
+    xd, yd, td = (torch.from_numpy(v).cuda() for v in (x, y, th))
+    nbx, nby = 90, 60
+    direct = torch.zeros(3 * nbx * nby, dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        A.aap_coarse_grain_noalloc(xd.data_ptr(), yd.data_ptr(), td.data_ptr(), p.n, p.lx, p.ly, nbx, nby,
+                                   direct.data_ptr(), s.cuda_stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with torch.cuda.stream(s):
+        A.aap_coarse_grain_noalloc(xd.data_ptr(), yd.data_ptr(), td.data_ptr(), p.n, p.lx, p.ly, nbx, nby,
+                                   direct.data_ptr(), s.cuda_stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    out = torch.full((3 * nbx * nby,), float("nan"), dtype=torch.float32, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        A.aap_coarse_grain_noalloc(xd.data_ptr(), yd.data_ptr(), td.data_ptr(), p.n, p.lx, p.ly, nbx, nby,
+                                   out.data_ptr(), s.cuda_stream)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, direct)
+    _oracle_close(out.cpu().numpy(), (x, y, th), p, nbx, nby)
