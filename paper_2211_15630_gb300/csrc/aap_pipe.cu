@@ -55,7 +55,13 @@ namespace {
 
 constexpr int kPipeThreads = 1024;
 constexpr int kPipeWarps = kPipeThreads / 32;
-constexpr int kPipeMaxChunks = 2 * kPipeMaxStage / 32 + 1;   // a wide tile spans both raw buffers
+constexpr int kPipeMaxChunks = 2 * kPipeMaxStage / 32 + 1;   // a wide tile spans two raw buffers
+// raw buffers: a tile's holds its staged records from the copy until its
+// update is done (the update reads its own particles' records there)
+#ifndef AAP_PIPE_RAW_BUFFERS
+#define AAP_PIPE_RAW_BUFFERS 3
+#endif
+constexpr int kNR = AAP_PIPE_RAW_BUFFERS;
 constexpr long long kPipeWaitCycles = 4000000000ll;    // about 2 s at 2 GHz
 
 // test hooks (aap_test_pipe_wait): the wait bound (<= 0: kPipeWaitCycles) and
@@ -90,7 +96,8 @@ namespace {
 
 // Segment maps and counts of one staged tile, written by the copy warp.
 struct RawMeta {
-    int tile;                   // tile index, -1: no more tiles, -2: skip (the buffer holds part of a wide tile)
+    int tile;                   // tile index, -1: no more tiles, -2: the second half of the wide tile in the
+                                // buffer before (released with it), -3: empty (released at once)
     int m, m_seg, n_spill, n_own;
     int wide;                   // 1: the tile spans both raw buffers (staged from buffer 0's start)
     int si;                     // system of the tile (ensembles: its replica)
@@ -111,6 +118,7 @@ struct RawMeta {
 // What the update warps need of a sorted tile.
 struct OutMeta {
     int tile;                   // -1: no more tiles, -2: skip (the buffer holds part of a wide tile)
+    int rbuf, rwide;            // raw buffer of the tile's staged records, and whether it spans the next one too
     int n_own, tx, ty, tw, th, W2, twL, twR, thD, thU;   // W2: half cells per extended row, 2 tw + 4
     int wide;                   // a half cell holds enough particles for 512 candidates
 };
@@ -119,26 +127,25 @@ struct PipeShared {
     Sys os[2];                  // system of the tile in each output buffer (read by the update warps)
     int osys[2];                // its index, -1: none yet
     Sys cs;                     // the copy warp's current system
-    RawMeta raw[2];
+    RawMeta raw[kNR];
     OutMeta out[2];
     int chunk[2];               // next chunk of 32 own particles, per output buffer
-    int issued[2], taken[2];    // raw buffer fills issued by the copy warp / sorted
     int flag;                   // a previous step's wait ran out
     int dense_tile;
     int warp_tot[kPipeWarps];
     long long red[5][kPipeWarps];
-    __align__(8) unsigned long long bar_raw_full[2], bar_raw_empty[2], bar_full[2], bar_empty[2];
+    __align__(8) unsigned long long bar_raw_full[kNR], bar_raw_empty[kNR], bar_full[2], bar_empty[2];
 };
 
 // Per-buffer shared arrays, carved from dynamic shared memory.  Buffer b of
 // each kind is reached by pointer arithmetic (no arrays of pointers indexed at
 // run time, which would live in local memory).
 struct PipeBufs {
-    int4 *raw0;                 // [2][cap] staged records as copied; mapped in place by the sort warps
+    int4 *raw0;                 // [kNR][cap] staged records as copied; mapped in place by the sort warps
     float4 *P0;                 // [2][cap] records in cell order: x, y from the tile centre, cos, sin (int32, 2^-22)
-    int4 *own0;                 // [2][cap_own] own particles in cell order: X, Y (tile frame), theta bits, id
     unsigned short *cst0;       // [2][cst_stride] half-cell starts in P
     unsigned short *oq0;        // [2][oq_stride] position in P of own particle o
+    unsigned short *or0;        // [2][oq_stride] its staged record in the tile's raw buffer(s)
     unsigned short *cellw;      // sort scratch: ey << 8 | ex (extended half cell) of staged record k
     unsigned short *slotw;      // flip << 14 | arrival rank in its half cell
     int *hist;                  // [nce] (half cells)
@@ -148,9 +155,9 @@ struct PipeBufs {
     __device__ __forceinline__ int *mhist(int b) const { return mhist0 + b * mh_stride; }
     __device__ __forceinline__ int4 *raw(int b) const { return raw0 + b * cap; }
     __device__ __forceinline__ float4 *P(int b) const { return P0 + b * cap; }
-    __device__ __forceinline__ int4 *own(int b) const { return own0 + b * cap_own; }
     __device__ __forceinline__ unsigned short *cstart(int b) const { return cst0 + b * cst_stride; }
     __device__ __forceinline__ unsigned short *ownq(int b) const { return oq0 + b * oq_stride; }
+    __device__ __forceinline__ unsigned short *ownr(int b) const { return or0 + b * oq_stride; }
 };
 
 __device__ __forceinline__ void carve_pipe(PipeBufs &B, unsigned char *p, int cap, int cap_own, int nce, int hist_words)
@@ -161,14 +168,14 @@ __device__ __forceinline__ void carve_pipe(PipeBufs &B, unsigned char *p, int ca
     B.cst_stride = round_up(nce + 1, 8);
     B.oq_stride = round_up(cap_own, 8);
     B.raw0 = (int4 *)p;
-    p += (size_t)2 * cap * 16;
+    p += (size_t)kNR * cap * 16;
     B.P0 = (float4 *)p;
     p += (size_t)2 * cap * 16;
-    B.own0 = (int4 *)p;
-    p += (size_t)2 * cap_own * 16;
     B.cst0 = (unsigned short *)p;
     p += (size_t)2 * B.cst_stride * 2;
     B.oq0 = (unsigned short *)p;
+    p += (size_t)2 * B.oq_stride * 2;
+    B.or0 = (unsigned short *)p;
     p += (size_t)2 * B.oq_stride * 2;
     B.cellw = (unsigned short *)p;              // sized for a wide tile (two buffers)
     p += (size_t)round_up(2 * cap, 8) * 2;
@@ -192,6 +199,12 @@ __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned coun
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(sa(bar)) : "memory");
+}
+
+// count arrivals at once
+__device__ __forceinline__ void mbar_arrive_cnt(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(sa(bar)), "r"(count) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned bytes)
@@ -474,6 +487,8 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
         if (lane == 0) {
             OutMeta &O = sh.out[b];
             O.tile = M.tile;
+            O.rbuf = r;
+            O.rwide = M.wide;
             O.n_own = min(carry, cap_own);
             O.tx = M.tx; O.ty = M.ty; O.tw = tw; O.th = th; O.W2 = W2;
             O.twL = M.twL; O.twR = M.twR; O.thD = M.thD; O.thU = M.thU;
@@ -488,7 +503,7 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
     const int xc = tw << (M.sx - 1), yc = th << (M.sy - 1);
     const int4 *R = B.raw(r);
     float4 *P = B.P(b);
-    int4 *OWN = B.own(b);
+    unsigned short *OR = B.ownr(b);
     unsigned short *OQ = B.ownq(b);
     for (int k = tid; k < m; k += NS) {
         const unsigned cf = B.cellw[k], sl = B.slotw[k];
@@ -514,7 +529,7 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
         if (ex >= 2 && ex < 2 * tw + 2 && ey >= 1 && ey <= th) {
             const int o = q + B.rowoff[ey];
             if (o < cap_own) {
-                OWN[o] = rk;
+                OR[o] = (unsigned short)k;      // the update reads the record in the raw buffer
                 OQ[o] = (unsigned short)q;
             }
         }
@@ -567,7 +582,8 @@ struct Acc {
 // of the warp must call (the scatter is warp-aggregated).
 template <int MODEL>
 __device__ __forceinline__ void update_one(const Sys &S, const OutMeta &O, const float4 *__restrict__ P,
-                                           const unsigned short *cstart, const int4 *OWN, const unsigned short *OQ,
+                                           const unsigned short *cstart, const int4 *RB, const unsigned short *OR,
+                                           const unsigned short *OQ,
                                            int o, long long step, bool measure, int *mhist, Acc &acc)
 {
     const int nxt = (int)(step & 1) ^ 1;
@@ -576,7 +592,7 @@ __device__ __forceinline__ void update_one(const Sys &S, const OutMeta &O, const
     int dtile = 0, region = 0;
     if (act) {
         const int tw = O.tw, th = O.th, W2 = O.W2;
-        const int4 rk = OWN[o];
+        const int4 rk = RB[OR[o]];                // own regions map to themselves (no shift, no mirror)
         const int X = rk.x, Y = rk.y;
         const float thi = __int_as_float(rk.z);
         const unsigned id = (unsigned)rk.w;
@@ -681,8 +697,8 @@ __device__ __forceinline__ void update_one(const Sys &S, const OutMeta &O, const
 // nceh: half cells of the largest extended tile, (2 tw + 4)(th + 2).
 __host__ __device__ size_t pipe_smem_bytes(int cap, int cap_own, int nceh, int hist_words)
 {
-    return 4 * (size_t)cap * 16 + 2 * (size_t)cap_own * 16 + 2 * (size_t)round_up(nceh + 1, 8) * 2 +
-           2 * (size_t)round_up(cap_own, 8) * 2 + 2 * (size_t)round_up(2 * cap, 8) * 2 +
+    return (size_t)(kNR + 2) * cap * 16 + 2 * (size_t)round_up(nceh + 1, 8) * 2 +
+           4 * (size_t)round_up(cap_own, 8) * 2 + 2 * (size_t)round_up(2 * cap, 8) * 2 +
            (size_t)round_up(nceh, 4) * 4 + (size_t)(kMaxTile + 4) * 4 + 2 * (size_t)round_up(hist_words, 4) * 4;
 }
 
@@ -738,13 +754,13 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
     PipeBufs B;
     carve_pipe(B, smem, cap, cap_own, nceh_max, hist_words);
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kNR; ++b) {
             mbar_init(&sh.bar_raw_full[b], 1);
-            mbar_init(&sh.bar_raw_empty[b], 1);
+            mbar_init(&sh.bar_raw_empty[b], NU);    // released by the update warps (or a token by the sort)
+        }
+        for (int b = 0; b < 2; ++b) {
             mbar_init(&sh.bar_full[b], 1);
             mbar_init(&sh.bar_empty[b], NU);
-            sh.issued[b] = 0;
-            sh.taken[b] = 0;
             sh.osys[b] = -1;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -824,28 +840,30 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
                     if (g < total) plan(g);
                     continue;
                 }
-                if (mode == 2 && r == 1) {
-                    // a wide tile starts at buffer 0: buffer 1 passes a skip token first
-                    if (((used >> 1) & 1u) && !warp_wait(&sh.bar_raw_empty[1], ((kpar >> 1) & 1u) ^ 1u, err0)) {
+                if (mode == 2 && r == kNR - 1) {
+                    // a wide tile needs two adjacent buffers: the last one
+                    // passes an empty token first and the tile starts at 0
+                    if (((used >> r) & 1u) && !warp_wait(&sh.bar_raw_empty[r], ((kpar >> r) & 1u) ^ 1u, err0)) {
                         ok = false;
                         break;
                     }
                     if (lane == 0) {
-                        sh.raw[1].tile = -2;
-                        mbar_arrive(&sh.bar_raw_full[1]);
+                        sh.raw[r].tile = -3;
+                        mbar_arrive(&sh.bar_raw_full[r]);
                     }
-                    kpar ^= 2u;
-                    used |= 2u;
+                    kpar ^= 1u << r;
+                    used |= 1u << r;
                     r = 0;
                 }
             }
-            // the raw buffer (both for a wide tile) must be free (its previous tile sorted)
+            // the raw buffer (both for a wide tile) must be free (its previous tile updated)
             const long long tw0 = PT_NOW();
             if (((used >> r) & 1u) && !warp_wait(&sh.bar_raw_empty[r], ((kpar >> r) & 1u) ^ 1u, err0)) {
                 ok = false;
                 break;
             }
-            if (mode == 2 && ((used >> 1) & 1u) && !warp_wait(&sh.bar_raw_empty[1], ((kpar >> 1) & 1u) ^ 1u, err0)) {
+            if (mode == 2 && ((used >> (r + 1)) & 1u) &&
+                !warp_wait(&sh.bar_raw_empty[r + 1], ((kpar >> (r + 1)) & 1u) ^ 1u, err0)) {
                 ok = false;
                 break;
             }
@@ -873,10 +891,7 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
                 // test hook: this fill never arrives, so the waits behind it run out
                 withhold = false;
             } else {
-                if (lane == 0) {
-                    sh.issued[r] += 1;
-                    mbar_arrive_tx(&sh.bar_raw_full[r], (unsigned)pl.m_seg * 16u);
-                }
+                if (lane == 0) mbar_arrive_tx(&sh.bar_raw_full[r], (unsigned)pl.m_seg * 16u);
                 __syncwarp();
                 if (lane < kSegs && pl.c > 0)
                     bulk_copy(R + (pl.incl - pl.c), pl.sg.base, (unsigned)pl.c * 16u, &sh.bar_raw_full[r]);
@@ -889,16 +904,17 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
             kpar ^= 1u << r;
             used |= 1u << r;
             if (mode == 2) {
-                // the wide tile's second buffer: a skip token (no copies into it)
+                // the wide tile's second buffer: a token (no copies into it;
+                // released together with the tile by the update warps)
                 if (lane == 0) {
-                    sh.raw[1].tile = -2;
-                    mbar_arrive(&sh.bar_raw_full[1]);
+                    sh.raw[r + 1].tile = -2;
+                    mbar_arrive(&sh.bar_raw_full[r + 1]);
                 }
-                kpar ^= 2u;
-                used |= 2u;
-                r = 0;
+                kpar ^= 2u << r;
+                used |= 2u << r;
+                r = (r + 2) % kNR;
             } else {
-                r ^= 1;
+                r = (r + 1) % kNR;
             }
             const long long tq0 = PT_NOW();
             g = __shfl_sync(0xffffffffu, gn, 0);
@@ -915,7 +931,7 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
             // issued at least one wait bound ago and nothing has filled the
             // buffers since, so the phase of each last fill is the barrier's
             // latest and the bounded wait returns at once.
-            for (int b = 0; b < 2; ++b)
+            for (int b = 0; b < kNR; ++b)
                 if ((used >> b) & 1u) warp_wait(&sh.bar_raw_full[b], ((kpar >> b) & 1u) ^ 1u, err0);
         }
         if (lane == 0) PT_ADD(0, PT_NOW() - tc0);
@@ -931,10 +947,12 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
             if (st == 0) PT_ADD(3, PT_NOW() - t0);
             rpar ^= 1u << r;
             const int tile = sh.raw[r].tile;
-            if (tile == -2) {
-                // skip token: the buffer held (or will hold) part of a wide tile
-                if (st == 0) mbar_arrive(&sh.bar_raw_empty[r]);
-                r ^= 1;
+            if (tile == -2 || tile == -3) {
+                // a token: the second half of the wide tile just sorted (the
+                // update warps release it with the tile), or an empty buffer
+                // (released here, for all the update warps)
+                if (tile == -3 && st == 0) mbar_arrive_cnt(&sh.bar_raw_empty[r], (unsigned)NU);
+                r = (r + 1) % kNR;
                 continue;
             }
             const bool end = tile < 0;
@@ -988,8 +1006,6 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
             if (st == 0) {
                 PT_ADD(6, PT_NOW() - t0);
                 PT_ADD(10, 1);
-                sh.taken[r] += 1;
-                mbar_arrive(&sh.bar_raw_empty[r]);
                 mbar_arrive(&sh.bar_full[b]);
                 if (wide) {
                     sh.out[1].tile = -2;
@@ -1005,7 +1021,7 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
             } else {
                 b ^= 1;
             }
-            r ^= 1;
+            r = (r + 1) % kNR;
         }
     } else {
         // ------------------------------------------------- update warps --
@@ -1040,7 +1056,9 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
             }
             const float4 *P = B.P(b);
             const unsigned short *cst = B.cstart(b);
-            const int4 *OWN = B.own(b);
+            const int rb = O.rbuf, rwide = O.rwide;
+            const int4 *RB = B.raw(rb);
+            const unsigned short *OR = B.ownr(b);
             const unsigned short *OQ = B.ownq(b);
             for (;;) {
                 int c = 0;
@@ -1048,11 +1066,14 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
                 c = __shfl_sync(0xffffffffu, c, 0);
                 const int o0 = c * 32;
                 if (o0 >= O.n_own) break;
-                update_one<MODEL>(S, O, P, cst, OWN, OQ, o0 + lane, step, measure, B.mhist(b), acc);
+                update_one<MODEL>(S, O, P, cst, RB, OR, OQ, o0 + lane, step, measure, B.mhist(b), acc);
             }
             __syncwarp();
             if (lane == 0) {
+                // the tile's output buffer and its raw buffer(s) are free
                 mbar_arrive(&sh.bar_empty[b]);
+                mbar_arrive(&sh.bar_raw_empty[rb]);
+                if (rwide) mbar_arrive(&sh.bar_raw_empty[rb + 1]);
                 PT_ADD(8, PT_NOW() - t1);
             }
             b ^= 1;
@@ -1060,11 +1081,6 @@ k_step_pipe(const Sys *__restrict__ sys, int nsys, const int *__restrict__ tile_
         if (acc_sys) flush_acc(acc, acc_sys, cur);
     }
     __syncthreads();
-    // copies still in flight (only after a wait ran out): let them land
-    if (tid == 0) {
-        for (int r = 0; r < 2; ++r)
-            if (sh.issued[r] > sh.taken[r]) mbar_wait(&sh.bar_raw_full[r], (unsigned)(sh.issued[r] - 1) & 1u, err0);
-    }
     // --- the last tiles' histograms -> their systems -----------------------
     flush_hist(sh, B, 0, step, tid, kPipeThreads);
     flush_hist(sh, B, 1, step, tid, kPipeThreads);
