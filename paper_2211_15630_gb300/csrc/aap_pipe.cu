@@ -1,4 +1,5 @@
-// aap_pipe.cu -- the pipelined tile step of one system (sm_103a).
+// aap_pipe.cu -- the pipelined tile step of one system or an ensemble of
+// systems with one species each (sm_103a).
 //
 // One time step (Sec. 2 of Kuersten, "Aligning Active Particles Py
 // Package") with the arithmetic of the whole-block tile routine of
@@ -11,14 +12,16 @@
 //                          regions with periodic shifts or mirror maps,
 //                          Sec. 2.4; the cell lists of Sec. 3.2) and copies
 //                          them global -> shared with one cp.async.bulk per
-//                          segment into one of two raw record buffers,
-//                          completing on that buffer's mbarrier;
+//                          segment into one of three raw record buffers
+//                          (a tile keeps its buffer until its update is
+//                          done), completing on that buffer's mbarrier;
 //   sort warps (NSORT)     map each staged record into the tile's extended
 //                          frame, histogram it by half cell (a cell split in
 //                          two along x), prefix-scan the histogram and place
 //                          the records in half-cell order (x, y and cos, sin
 //                          as exact integers) into one of two output buffers,
-//                          with the tile's own particles listed in that order;
+//                          with the tile's own particles listed in that order
+//                          (their sorted positions and raw records);
 //   update warps (rest)    take chunks of 32 own particles from the ready
 //                          output buffer, sum over three rows of five half
 //                          cells (every point within R of a half cell lies in
@@ -702,8 +705,6 @@ __host__ __device__ size_t pipe_smem_bytes(int cap, int cap_own, int nceh, int h
            (size_t)round_up(nceh, 4) * 4 + (size_t)(kMaxTile + 4) * 4 + 2 * (size_t)round_up(hist_words, 4) * 4;
 }
 
-// The pipelined step of one system with one species (any model): one block
-// of kPipeThreads threads per SM.
 // Flush output buffer b's measured histograms into the system of the tile it
 // held, and clear them.  tid, nt: the calling threads.
 __device__ __forceinline__ void flush_hist(PipeShared &sh, const PipeBufs &B, int b, long long step, int tid, int nt)
