@@ -19,9 +19,10 @@
 //                             gradient (flipped, transposed weights) masked by
 //                             the ReLU of the layer input
 //   k_conv_dw_tc<CIN, COUT>   weight and bias gradients on the tcgen05
-//                             tensor cores (the transposed dy and shifted input
-//                             rows as K-major operands, pixels along K, one
-//                             TMEM accumulator per tap for all of a block's
+//                             tensor cores (shifted input rows and the
+//                             transposed dy as K-major operands, pixels along
+//                             K, the three row shifts stacked along M, one TMEM
+//                             accumulator per column shift for all of a block's
 //                             tiles), one partial per block, reduced in a fixed
 //                             order (deterministic)
 //   k_adam                    Adam step on the FP32 master weights
@@ -381,23 +382,26 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_ws(const bf16 *__restrict
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32 * NA));
 }
 
-// Weight / bias gradient on the tensor cores.  For every tap (dy, dx) the
-// block accumulates D_tap[co][ci] = sum_p dy[p][co] x[p + tap - 1][ci] over
-// all its tiles in TMEM (tap accumulator at columns 32 tap): one MMA per tap
-// and K step of 16 pixels (two tile rows), M = 128 rows of which the first
-// COUT are the output channels (the rest read other rows of the transposed dy
-// and are never read back), N = CIN, both operands K-major (pixels along K):
-//   A = dyT[py][co][8 px]       (LBO: one tile row, SBO: 8 channels = 128 B)
-//   B = xT[dx][hy][ci][8 px]    the halo row hy seen from column dx
-//                               (LBO: one halo row, SBO: 128 B)
+// Weight / bias gradient on the tensor cores.  For every column shift dx the
+// block accumulates D_dx[(dy, ci)][co] = sum_p x[p + (dy, dx) - 1][ci] dy[p][co]
+// over all its tiles in TMEM (accumulator dx at columns 32 dx): one MMA per dx
+// and K step of 16 pixels (two tile rows), M = 128 rows (dy, ci) -- the three
+// row shifts stacked, since the rows of shift dy + 1 are one halo row further
+// on (rows past the third shift are padding the tensor core requires and are
+// never read back) -- N = COUT (at least 16), both operands K-major (pixels
+// along K):
+//   A = xT[dx][hy][ci][8 px]    halo row hy seen from column dx
+//                               (LBO: one halo row, SBO: 8 channels = 128 B)
+//   B = dyT[py][co][8 px]       (LBO: one tile row, SBO: 128 B)
 // Warps 1-7 fetch a tile's halo and dy into one of two raw staging areas
 // (cp.async, one tile ahead), then write the transposed operands into one of
-// two stages (and add up db in FP32, each
-// thread always for the same output channel, in a fixed order); warp 0, one
-// thread, issues the MMAs of a stage and commits them to its "empty"
-// mbarrier; after the last tile warp 4 (TMEM lanes 0-31 = the output
-// channels) writes the block's partial dw and the threads' db partials are
-// summed in a fixed order.  part[block][COUT * 9 * CIN + COUT].
+// two stages with ldmatrix.trans / stmatrix (8 x 8 blocks of 16-bit values)
+// and add up db in FP32 (each thread always for the same output channel, in
+// a fixed order); warp 0, one thread, issues the 24 MMAs of a stage and
+// commits them to its "empty" mbarrier; after the last tile warps 4-7 (TMEM
+// lane quarters 0-3 = rows (dy, ci)) write the block's partial dw and the
+// threads' db partials are summed in a fixed order.
+// part[block][COUT * 9 * CIN + COUT].
 constexpr int kDwThreads = 256;
 constexpr int kDwT = kDwThreads - 32;          // transposing threads (warps 1-7)
 
@@ -448,7 +452,7 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_conv_dw_tc(const bf16 *__rest
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                     "r"(512));
+                     "r"(128));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -460,7 +464,8 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_conv_dw_tc(const bf16 *__rest
     if (warp == 0) {
         // ------------------------------------------------------------ MMA --
         if (lane == 0) {
-            constexpr uint32_t idesc = umma_idesc_bf16(128, CIN);
+            constexpr int NB = COUT < 16 ? 16 : COUT;     // MMA N (output channels, padded)
+            constexpr uint32_t idesc = umma_idesc_bf16(128, NB);
             int i = 0;
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
                 const int st = i & 1;
@@ -470,14 +475,15 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_conv_dw_tc(const bf16 *__rest
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t xt = smem_addr(stage0 + st * (XT + DYT)), dyt = xt + (uint32_t)XT;
-#pragma unroll 1
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int ddy = tap / 3, ddx = tap - ddy * 3;
 #pragma unroll
-                    for (int ks = 0; ks < kTH / 2; ++ks) {
-                        const uint64_t ad = umma_desc(dyt + 2 * ks * COUTP * 16, COUTP * 16, 128);
-                        const uint64_t bd = umma_desc(xt + (ddx * (kTH + 2) + 2 * ks + ddy) * CIN * 16, CIN * 16, 128);
-                        umma_bf16(tmem + tap * 32, ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
+                for (int ks = 0; ks < kTH / 2; ++ks) {
+                    const uint64_t bd = umma_desc(dyt + 2 * ks * COUTP * 16, COUTP * 16, 128);
+#pragma unroll
+                    for (int ddx = 0; ddx < 3; ++ddx) {
+                        // rows (dy, ci): the halo rows 2 ks + dy of column
+                        // shift ddx, one halo row (CIN x 16 bytes) per dy
+                        const uint64_t ad = umma_desc(xt + (ddx * (kTH + 2) + 2 * ks) * CIN * 16, CIN * 16, 128);
+                        umma_bf16(tmem + ddx * 32, ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -546,29 +552,42 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_conv_dw_tc(const bf16 *__rest
             }
             const bf16 *rx = raw_x + rb * (kHaloPix * CIN), *rd = raw_dy + rb * (kTH * kTW * COUT);
             unsigned char *xt = stage0 + st * (XT + DYT), *dyt = xt + XT;
-            // xT[dx][hy][ci][j] = halo[hy][dx + j][ci]
-            for (int k = pt; k < 3 * (kTH + 2) * CIN; k += kDwT) {
-                const int ci = k % CIN, r = k / CIN, hy = r % (kTH + 2), dxx = r / (kTH + 2);
-                const unsigned short *src = reinterpret_cast<const unsigned short *>(rx + (hy * (kTW + 2) + dxx) * CIN + ci);
-                uint32_t w4[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) w4[j] = (uint32_t)src[(2 * j) * CIN] | ((uint32_t)src[(2 * j + 1) * CIN] << 16);
-                *reinterpret_cast<uint4 *>(xt + ((size_t)(dxx * (kTH + 2) + hy) * CIN + ci) * 16) =
-                    make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            // The transposes are 8 x 8 blocks of 16-bit values: ldmatrix.trans
+            // reads 8 rows of 16 bytes (8 pixels x 8 channels) and stmatrix
+            // writes them back as 8 rows of 8 pixels (one per channel); one
+            // warp instruction each moves four blocks.  Lane l addresses row
+            // l % 8 of block l / 8.
+            const int tw8 = pt >> 5, rr8 = lane & 7, mm = lane >> 3;
+            // xT[dx][hy][ci][j] = halo[hy][dx + j][ci]: blocks (dx, hy, g)
+            constexpr int G = CIN / 8;
+            for (int item = tw8; item < 3 * (kTH + 2) * G / 4; item += kDwT / 32) {
+                const int mi = 4 * item + mm, g = mi % G, pr = mi / G, hy = pr % (kTH + 2), dxx = pr / (kTH + 2);
+                uint32_t v[4];
+                asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                             : "r"(smem_addr(rx + (hy * (kTW + 2) + dxx + rr8) * CIN + 8 * g)));
+                asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};"
+                             ::"r"(smem_addr(xt + ((size_t)(dxx * (kTH + 2) + hy) * CIN + 8 * g + rr8) * 16)),
+                               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+                             : "memory");
             }
-            // dyT[py][co][j] = dy[py][j][co]; db of this thread's channel
-            for (int k = pt; k < kTH * COUT; k += kDwT) {
-                const int co = k % COUT, py = k / COUT;
-                const unsigned short *src = reinterpret_cast<const unsigned short *>(rd + py * kTW * COUT + co);
-                uint32_t w4[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const unsigned short lo = src[(2 * j) * COUT], hi = src[(2 * j + 1) * COUT];
-                    db += __uint_as_float((uint32_t)lo << 16);
-                    db += __uint_as_float((uint32_t)hi << 16);
-                    w4[j] = (uint32_t)lo | ((uint32_t)hi << 16);
-                }
-                *reinterpret_cast<uint4 *>(dyt + ((size_t)py * COUTP + co) * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            // dyT[py][co][j] = dy[py][j][co]: blocks (py, q)
+            constexpr int Q = COUT / 8;
+            for (int item = tw8; item < kTH * Q / 4; item += kDwT / 32) {
+                const int mi = 4 * item + mm, q = mi % Q, py = mi / Q;
+                uint32_t v[4];
+                asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                             : "r"(smem_addr(rd + (py * kTW + rr8) * COUT + 8 * q)));
+                asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};"
+                             ::"r"(smem_addr(dyt + ((size_t)py * COUTP + 8 * q + rr8) * 16)),
+                               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+                             : "memory");
+            }
+            // db of this thread's output channel (pt % COUT), pixels in order
+            {
+                const unsigned short *src = reinterpret_cast<const unsigned short *>(rd);
+                for (int k = pt; k < kTH * kTW * COUT; k += kDwT) db += __uint_as_float((uint32_t)src[k] << 16);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // for the tensor core
             bar_arrive(&tfull[st]);
@@ -582,13 +601,16 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_conv_dw_tc(const bf16 *__rest
     const bool fin = __syncthreads_and(bar_wait(&done, 0u)) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
     float *pb = part + (size_t)blockIdx.x * (COUT * 9 * CIN + COUT);
-    if (fin && warp == 4) {
+    if (fin && warp >= 4) {
+        // TMEM lane quarter q = warp % 4 holds rows 32 q .. 32 q + 31 = (dy, ci)
+        const int m = (warp & 3) * 32 + lane, ddy = m / CIN, ci = m % CIN;
 #pragma unroll 1
-        for (int tap = 0; tap < 9; ++tap) {
+        for (int ddx = 0; ddx < 3; ++ddx) {
             uint32_t r[32];
-            tmem_load<32>(tmem + tap * 32, r);
-            if (lane < COUT)
-                for (int ci = 0; ci < CIN; ++ci) pb[((size_t)lane * 9 + tap) * CIN + ci] = __uint_as_float(r[ci]);
+            tmem_load<32>(tmem + ddx * 32 + ((uint32_t)((warp & 3) * 32) << 16), r);
+            if (ddy < 3)
+                for (int co = 0; co < COUT; ++co)
+                    pb[((size_t)co * 9 + 3 * ddy + ddx) * CIN + ci] = __uint_as_float(r[co]);
         }
     }
     if (tid < COUT) {
@@ -599,18 +621,30 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_conv_dw_tc(const bf16 *__rest
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
     (void)ok;
 }
 
-// out[i] = sum_k part[k][i] in a fixed order (deterministic).
-__global__ void k_reduce_parts(const float *__restrict__ part, int nparts, int len, float *__restrict__ w_out,
-                               int wlen, float *__restrict__ b_out)
+// out[i] = sum_k part[k][i] in a fixed order (deterministic): a block takes
+// 32 consecutive i; its eight warps sum eight consecutive ranges of k, and
+// the eight partial sums are added in warp order.
+__global__ void __launch_bounds__(256) k_reduce_parts(const float *__restrict__ part, int nparts, int len,
+                                                      float *__restrict__ w_out, int wlen, float *__restrict__ b_out)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int k = 0; k < nparts; ++k) s += part[(size_t)k * len + i];
-        if (i < wlen) w_out[i] = s; else b_out[i - wlen] = s;
+    __shared__ float s_sum[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const int per = (nparts + 7) / 8, k0 = min(w * per, nparts), k1 = min(k0 + per, nparts);
+    float acc = 0.f;
+    if (i < len)
+        for (int k = k0; k < k1; ++k) acc += part[(size_t)k * len + i];
+    s_sum[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && i < len) {
+        float t = 0.f;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) t += s_sum[v][lane];
+        if (i < wlen) w_out[i] = t; else b_out[i - wlen] = t;
     }
 }
 
@@ -911,14 +945,14 @@ cudaError_t conv_dw(const bf16 *x, const bf16 *dy, int dy_stride, int B, int H, 
         configured.store(1);
     }
     const int ntiles = (W / kTW) * (H / kTH) * B;
-    // one persistent block per SM (each holds 512 TMEM columns), no more
-    // partials than the documented scratch holds
+    // one persistent block per SM (about 117 KB of shared memory each), no
+    // more partials than the documented scratch holds
     const int nblk = std::max(1, std::min(std::min(ntiles, sm_count()), (H / dw_rows(H)) * B));
     k_conv_dw_tc<CIN, COUT><<<nblk, kDwThreads, smem, st>>>(x, dy, dy_stride, H, W, ntiles, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int len = COUT * 9 * CIN + COUT;
-    k_reduce_parts<<<std::max(1, (len + 255) / 256), 256, 0, st>>>(part, nblk, len, dw, COUT * 9 * CIN, db);
+    k_reduce_parts<<<std::max(1, (len + 31) / 32), 256, 0, st>>>(part, nblk, len, dw, COUT * 9 * CIN, db);
     return cudaGetLastError();
 }
 
