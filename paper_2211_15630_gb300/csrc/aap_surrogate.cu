@@ -650,6 +650,16 @@ __global__ void __launch_bounds__(256) k_reduce_parts(const float *__restrict__ 
 
 // Fields in (FP32 planes [B][3][H][W]) -> normalised residual state (FP32 NHWC 8)
 // and the BF16 network input (NHWC 16: 3 fields, the noise strength, zeros).
+// One pixel of a BF16 NHWC 16 tensor: channels 0-3 = (a, b, c, d), the rest
+// zero, written as two 16-byte stores.
+__device__ __forceinline__ void store_input_pixel(bf16 *px, float a, float b, float c, float d)
+{
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b), h1 = __floats2bfloat162_rn(c, d);
+    uint4 *o = reinterpret_cast<uint4 *>(px);
+    o[0] = make_uint4(*reinterpret_cast<const uint32_t *>(&h0), *reinterpret_cast<const uint32_t *>(&h1), 0u, 0u);
+    o[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 __global__ void k_fields_in(const float *__restrict__ f, const float *__restrict__ eta, int B, int H, int W,
                             float rho0, float eta_c, float eta_s, float *__restrict__ state, bf16 *__restrict__ x0)
 {
@@ -660,14 +670,11 @@ __global__ void k_fields_in(const float *__restrict__ f, const float *__restrict
         const float u0 = f[(b * 3 + 0) * plane + p] / rho0 - 1.f;
         const float u1 = f[(b * 3 + 1) * plane + p] / rho0;
         const float u2 = f[(b * 3 + 2) * plane + p] / rho0;
-        float *s = state + i * 8;
-        s[0] = u0; s[1] = u1; s[2] = u2;
-        s[3] = s[4] = s[5] = s[6] = s[7] = 0.f;
+        float4 *s = reinterpret_cast<float4 *>(state + i * 8);
+        s[0] = make_float4(u0, u1, u2, 0.f);
+        s[1] = make_float4(0.f, 0.f, 0.f, 0.f);
         const float e = (eta[b] - eta_c) / eta_s;
-        __nv_bfloat162 *xb = reinterpret_cast<__nv_bfloat162 *>(x0 + i * 16);
-        xb[0] = __floats2bfloat162_rn(u0, u1);
-        xb[1] = __floats2bfloat162_rn(u2, e);
-        for (int k = 2; k < 8; ++k) xb[k] = __floats2bfloat162_rn(0.f, 0.f);
+        store_input_pixel(x0 + i * 16, u0, u1, u2, e);
     }
 }
 
@@ -679,12 +686,9 @@ __global__ void k_state_to_input(const float *__restrict__ state, const float *_
     const long long plane = (long long)H * W;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const long long b = i / plane;
-        const float *s = state + i * 8;
+        const float4 u = *reinterpret_cast<const float4 *>(state + i * 8);
         const float e = (eta[b] - eta_c) / eta_s;
-        __nv_bfloat162 *xb = reinterpret_cast<__nv_bfloat162 *>(x0 + i * 16);
-        xb[0] = __floats2bfloat162_rn(s[0], s[1]);
-        xb[1] = __floats2bfloat162_rn(s[2], e);
-        for (int k = 2; k < 8; ++k) xb[k] = __floats2bfloat162_rn(0.f, 0.f);
+        store_input_pixel(x0 + i * 16, u.x, u.y, u.z, e);
     }
 }
 
@@ -713,17 +717,15 @@ __global__ void k_mse(const float *__restrict__ pred, const float *__restrict__ 
     __shared__ float red[256];
     float s = 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
-        float d[3];
-        const long long b = i / plane;
-        for (int c = 0; c < 3; ++c) {
-            d[c] = pred[i * 8 + c] - target[i * 8 + c];
-            s += d[c] * d[c];
-            if (dmean) d[c] -= dmean[b * 3 + c];     // through the projection P
+        const float4 u = *reinterpret_cast<const float4 *>(pred + i * 8);
+        const float4 v = *reinterpret_cast<const float4 *>(target + i * 8);
+        float d[3] = {u.x - v.x, u.y - v.y, u.z - v.z};
+        for (int c = 0; c < 3; ++c) s += d[c] * d[c];
+        if (dmean) {
+            const long long b = i / plane;
+            for (int c = 0; c < 3; ++c) d[c] -= dmean[b * 3 + c];     // through the projection P
         }
-        __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(dout + i * 16);
-        o[0] = __floats2bfloat162_rn(2.f * scale * d[0], 2.f * scale * d[1]);
-        o[1] = __floats2bfloat162_rn(2.f * scale * d[2], 0.f);
-        for (int k = 2; k < 8; ++k) o[k] = __floats2bfloat162_rn(0.f, 0.f);
+        store_input_pixel(dout + i * 16, 2.f * scale * d[0], 2.f * scale * d[1], 2.f * scale * d[2], 0.f);
     }
     red[threadIdx.x] = s;
     __syncthreads();
