@@ -124,6 +124,7 @@ struct OutMeta {
     int rbuf, rwide;            // raw buffer of the tile's staged records, and whether it spans the next one too
     int n_own, tx, ty, tw, th, W2, twL, twR, thD, thU;   // W2: half cells per extended row, 2 tw + 4
     int wide;                   // a half cell holds enough particles for 512 candidates
+    int dense;                  // more than 1.5 staged records per half cell on average
 };
 
 struct PipeShared {
@@ -496,6 +497,7 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
             O.tx = M.tx; O.ty = M.ty; O.tw = tw; O.th = th; O.W2 = W2;
             O.twL = M.twL; O.twR = M.twR; O.thD = M.thD; O.thU = M.thU;
             O.wide = 15 * mx >= 512;
+            O.dense = 2 * m > 3 * nce;
             sh.chunk[b] = 0;
             if (carry != M.n_own) atomicOr(M.err, ERR_BOUNDS);
         }
@@ -546,7 +548,7 @@ __device__ __forceinline__ void sort_order(PipeShared &sh, const PipeBufs &B, in
 // Langevin sum; cnt counts it).  The staged (cos, sin) are integers in units
 // of 2^-22, so the sums are exact and order-free; ACC is int below 512
 // candidates and long long beyond.
-template <int MODEL, typename ACC>
+template <int MODEL, typename ACC, int UNR>
 __device__ __forceinline__ void neighbour_sum_h(const float4 *__restrict__ P, const unsigned short *cstart, int ec,
                                                 int W2, float4 pi, float r2, ACC &sc, ACC &ss, int &cnt)
 {
@@ -558,7 +560,7 @@ __device__ __forceinline__ void neighbour_sum_h(const float4 *__restrict__ P, co
     for (int dy = -1; dy <= 1; ++dy) {
         const int c0 = ec + dy * W2 - 2;
         const int a = cstart[c0], b = cstart[c0 + 5];
-#pragma unroll 2
+#pragma unroll UNR
         for (int j = a; j < b; ++j) {
             const float4 pj = P[j];
             const float dx = pj.x - pi.x, dyy = pj.y - pi.y;
@@ -610,13 +612,16 @@ __device__ __forceinline__ void update_one(const Sys &S, const OutMeta &O, const
             narrow = ncand < 512;
         }
         if (narrow) {
+            // short candidate rows run faster unrolled twice, long ones
+            // (dense tiles) four times
             int a, b;
-            neighbour_sum_h<MODEL, int>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
+            if (O.dense) neighbour_sum_h<MODEL, int, 4>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
+            else neighbour_sum_h<MODEL, int, 2>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
             sc = (float)a;
             ss = (float)b;
         } else {
             long long a, b;
-            neighbour_sum_h<MODEL, long long>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
+            neighbour_sum_h<MODEL, long long, 4>(P, cstart, ec, W2, pi, S.r2, a, b, cnt);
             sc = (float)a;
             ss = (float)b;
         }

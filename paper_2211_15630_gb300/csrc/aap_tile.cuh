@@ -276,7 +276,7 @@ __device__ __forceinline__ void neighbour_sum(const float4 *__restrict__ P, cons
     for (int dy = -1; dy <= 1; ++dy) {
         const int c0 = ec + dy * W2 - 1;
         const int a = cstart[c0], b = cstart[c0 + 3];
-#pragma unroll 2
+#pragma unroll 4
         for (int j = a; j < b; ++j) {
             const float4 pj = P[j];
             const float dx = pj.x - pi.x, dyy = pj.y - pi.y;
