@@ -58,27 +58,46 @@ __device__ __forceinline__ void coarse_add(unsigned long long *acc, long long nb
 // in exact 64-bit integers (cos scaled by 2^32), so that the fields are
 // reproducible bit for bit.  acc: [3][nbx*nby], zeroed by the caller.  Blocks
 // take whole tiles and read only the stored records (the valid slots of the
-// nine regions), then the spilled records, shared out over the blocks.  The
-// sums go straight to acc: the lanes of a warp that hit one bin are merged
-// by the memory system (a shared-memory window of the tile's bins was slower:
-// same-address shared atomics serialise).
+// nine regions, taken as one index range so that a tile costs one read of
+// its counts and the block's threads stay busy across the small edge
+// regions), then the spilled records, shared out over the blocks.  The sums
+// go straight to acc, one atomic per record and field: merging a warp's
+// lanes of one bin first (by match and reductions, or by runs of records per
+// thread) was slower, as was a shared-memory window of the tile's bins
+// (same-address shared atomics serialise).
 template <int NT>
 __global__ void __launch_bounds__(NT) k_coarse_tiles(Sys S, int b, BinAxis ax, BinAxis ay, unsigned long long *acc)
 {
     const long long nb = (long long)ax.nb * ay.nb;
+    __shared__ int s_pre[kRegions + 1];
     for (int tile = blockIdx.x; tile < S.ntiles; tile += gridDim.x) {
         const int tx = tile % S.ntx, ty = tile / S.ntx;
         const long long ux0 = (long long)S.x0tab[tx] << S.sx, uy0 = (long long)S.y0tab[ty] << S.sy;
         const int4 *base = S.rec[b] + (long long)tile * S.tile_slots;
-        for (int r = 0; r < kRegions; ++r) {
-            const int cnt = min(S.cnt[b][tile * kCntStride + r], S.cap[r]);
-            const int4 *reg = base + S.off[r];
-            for (int k = threadIdx.x; k < cnt; k += NT) {
-                const int4 rec = reg[k];
-                const int ix = coarse_bin(ux0 + rec.x, ax), iy = coarse_bin(uy0 + rec.y, ay);
-                coarse_add(acc, nb, (long long)iy * ax.nb + ix, __int_as_float(rec.z));
+        if (threadIdx.x < 32) {
+            // the regions' record counts and their prefix
+            const int l = threadIdx.x;
+            const int c = l < kRegions ? min(S.cnt[b][tile * kCntStride + l], S.cap[l]) : 0;
+            int v = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, v, o);
+                if (l >= o) v += t;
             }
+            if (l < kRegions) s_pre[l + 1] = v;
+            if (l == 0) s_pre[0] = 0;
         }
+        __syncthreads();
+        const int total = s_pre[kRegions];      // records of the tile; record k is in region r
+                                                // for s_pre[r] <= k < s_pre[r + 1]
+        for (int k = threadIdx.x; k < total; k += NT) {
+            int r = 0;
+            while (k >= s_pre[r + 1]) ++r;
+            const int4 rec = base[S.off[r] + k - s_pre[r]];
+            const int ix = coarse_bin(ux0 + rec.x, ax), iy = coarse_bin(uy0 + rec.y, ay);
+            coarse_add(acc, nb, (long long)iy * ax.nb + ix, __int_as_float(rec.z));
+        }
+        __syncthreads();
     }
     const int nsp = min(S.spill_cnt[b], S.spill_cap);
     for (int e = blockIdx.x * NT + threadIdx.x; e < nsp; e += gridDim.x * NT) {
