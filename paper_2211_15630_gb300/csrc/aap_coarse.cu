@@ -13,24 +13,31 @@ namespace aapk {
 
 namespace {
 
-// Bin of a fixed-point coordinate u (units of the box axis): the definition is
-// the FP64 product (int)(u * (cs / 2^s) * (nb / L)) clamped to [0, nb).  It is
-// evaluated in FP32 and taken from there unless the FP32 value lies within its
-// error bound (3 roundings of 2^-24 relative, widened to 2.5e-7 t + 1e-6) of a
-// bin edge, where the FP64 product decides; so the result is the FP64 one for
-// every particle, with FP64 work (slow on this GPU) for a few in a million.
+// Bin of the fixed-point coordinate u = cell0 2^s + off (units of the box
+// axis; cell0 the first cell of the record's tile, off >= 0 its offset in the
+// tile): the definition is the FP64 product (int)(u * (cs / 2^s) * (nb / L))
+// clamped to [0, nb).  It is evaluated in FP32 as cell0 * (bins per cell) +
+// off * (bins per unit), with no 64-bit integer conversion (those run on
+// the FP64 pipe, which is narrow on this GPU), and taken from there unless
+// the FP32 value t lies within its error bound of a bin edge, where the FP64
+// product decides.  Both terms are >= 0, so the five roundings of at most
+// 2^-24 relative each (the two factors, off, the product, the fused sum)
+// stay below 4 2^-24 t = 2.4e-7 t; the margin is 3e-7 t + 1e-6.  So the
+// result is the FP64 one for every particle, with FP64 work for a few in ten
+// thousand.
 struct BinAxis {
     double cs_unit, f;          // cs / 2^s, nb / L
-    float f_unit;               // bins per unit
-    int nb;
+    float f_unit, f_cell;       // bins per unit, bins per cell
+    int nb, s;
 };
 
-__device__ __forceinline__ int coarse_bin(long long u, const BinAxis &a)
+__device__ __forceinline__ int coarse_bin(int cell0, int off, const BinAxis &a)
 {
-    const float t = (float)u * a.f_unit;
-    const float fl = floorf(t), fr = t - fl, m = fmaf(t, 2.5e-7f, 1e-6f);
+    const float t = fmaf((float)cell0, a.f_cell, (float)off * a.f_unit);
+    const float fl = floorf(t), fr = t - fl, m = fmaf(t, 3e-7f, 1e-6f);
     int i = (int)fl;
-    if (fr < m || fr > 1.0f - m) i = (int)(((double)u * a.cs_unit) * a.f);
+    if (off < 0 || fr < m || fr > 1.0f - m)
+        i = (int)(((double)(((long long)cell0 << a.s) + off) * a.cs_unit) * a.f);
     return min(max(i, 0), a.nb - 1);
 }
 
@@ -72,7 +79,7 @@ __global__ void __launch_bounds__(NT) k_coarse_tiles(Sys S, int b, BinAxis ax, B
     __shared__ int s_pre[kRegions + 1];
     for (int tile = blockIdx.x; tile < S.ntiles; tile += gridDim.x) {
         const int tx = tile % S.ntx, ty = tile / S.ntx;
-        const long long ux0 = (long long)S.x0tab[tx] << S.sx, uy0 = (long long)S.y0tab[ty] << S.sy;
+        const int cx0 = S.x0tab[tx], cy0 = S.y0tab[ty];
         const int4 *base = S.rec[b] + (long long)tile * S.tile_slots;
         if (threadIdx.x < 32) {
             // the regions' record counts and their prefix
@@ -94,7 +101,7 @@ __global__ void __launch_bounds__(NT) k_coarse_tiles(Sys S, int b, BinAxis ax, B
             int r = 0;
             while (k >= s_pre[r + 1]) ++r;
             const int4 rec = base[S.off[r] + k - s_pre[r]];
-            const int ix = coarse_bin(ux0 + rec.x, ax), iy = coarse_bin(uy0 + rec.y, ay);
+            const int ix = coarse_bin(cx0, rec.x, ax), iy = coarse_bin(cy0, rec.y, ay);
             coarse_add(acc, nb, (long long)iy * ax.nb + ix, __int_as_float(rec.z));
         }
         __syncthreads();
@@ -104,8 +111,7 @@ __global__ void __launch_bounds__(NT) k_coarse_tiles(Sys S, int b, BinAxis ax, B
         const int4 rec = S.spill_rec[b][e];
         const int tile = S.spill_key[b][e] / kCntStride;
         const int tx = tile % S.ntx, ty = tile / S.ntx;
-        const int ix = coarse_bin(((long long)S.x0tab[tx] << S.sx) + rec.x, ax);
-        const int iy = coarse_bin(((long long)S.y0tab[ty] << S.sy) + rec.y, ay);
+        const int ix = coarse_bin(S.x0tab[tx], rec.x, ax), iy = coarse_bin(S.y0tab[ty], rec.y, ay);
         coarse_add(acc, nb, (long long)iy * ax.nb + ix, __int_as_float(rec.z));
     }
 }
@@ -135,11 +141,15 @@ cudaError_t launch_coarse(const Sys &S, int b, int nbx, int nby, unsigned long l
     ax.cs_unit = S.csx_d / (double)(1ll << S.sx);
     ax.f = (double)nbx / S.lx;
     ax.f_unit = (float)(ax.cs_unit * ax.f);
+    ax.f_cell = (float)(S.csx_d * ax.f);
     ax.nb = nbx;
+    ax.s = S.sx;
     ay.cs_unit = S.csy_d / (double)(1ll << S.sy);
     ay.f = (double)nby / S.ly;
     ay.f_unit = (float)(ay.cs_unit * ay.f);
+    ay.f_cell = (float)(S.csy_d * ay.f);
     ay.nb = nby;
+    ay.s = S.sy;
     int dev = 0, nsm = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(S.ntiles, 8 * nsm));
