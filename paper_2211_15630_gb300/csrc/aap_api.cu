@@ -372,7 +372,7 @@ int set_capacity(aap_handle *h, double factor)
     AAP_CK(aapk::configure_step_kernel(L.model, L.threads, smem, &bps));
     if (bps < 1) return fail(AAP_EINVAL, "step kernel does not fit on an SM with this tiling");
     L.grid_step = std::max(1, std::min(S.ntiles, bps * nsm));
-    L.grid_finish = std::max(1, std::min(256, ceil_div((long long)S.ntiles * aapk::kCntStride, 256)));
+    L.grid_finish = std::max(1, std::min(64, ceil_div((long long)S.ntiles * (aapk::kCntStride / 4), 1024)));
     L.scratch_per_block = aapk::stage_bytes(L.scratch_cap) + aapk::spill_list_bytes(L.spill_list_cap);
     L.scratch_per_block = (L.scratch_per_block + 255) / 256 * 256;
     L.nsys = 1;

@@ -127,14 +127,25 @@ __global__ void k_finish(Sys *sys, int nsys, const int *__restrict__ tile_base, 
     __shared__ int s_last;
     const long long step = ctl->step;
     const int cur = (int)(step & 1);
-    const long long nw = (long long)tile_base[nsys] * kCntStride;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int g = (int)(i / kCntStride);
-        const int si = nsys > 1 ? sys_of_tile(tile_base, nsys, g) : 0;
-        const int t = g - tile_base[si], w = (int)(i % kCntStride);
-        sys[si].cnt[cur][(long long)t * kCntStride + w] = 0;
-        if (w == 0 && (t & 31) == 0) sys[si].spill_bits[cur][t >> 5] = 0u;    // the tiles' spill marks
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
+    if (nsys == 1) {
+        // one system: its counter lines are one array (16-byte aligned, 64
+        // bytes a tile), cleared by 16-byte stores through pointers read once
+        int4 *c4 = reinterpret_cast<int4 *>(sys[0].cnt[cur]);
+        unsigned *sb = sys[0].spill_bits[cur];
+        const int nt = tile_base[1];
+        const long long n4 = (long long)nt * (kCntStride / 4);
+        for (long long i = gt; i < n4; i += gs) c4[i] = make_int4(0, 0, 0, 0);
+        for (long long i = gt; i < (nt + 31) / 32; i += gs) sb[i] = 0u;    // the tiles' spill marks
+    } else {
+        const long long nw = (long long)tile_base[nsys] * kCntStride;
+        for (long long i = gt; i < nw; i += gs) {
+            const int g = (int)(i / kCntStride);
+            const int si = sys_of_tile(tile_base, nsys, g);
+            const int t = g - tile_base[si], w = (int)(i % kCntStride);
+            sys[si].cnt[cur][(long long)t * kCntStride + w] = 0;
+            if (w == 0 && (t & 31) == 0) sys[si].spill_bits[cur][t >> 5] = 0u;    // the tiles' spill marks
+        }
     }
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
