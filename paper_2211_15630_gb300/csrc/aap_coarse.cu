@@ -31,13 +31,20 @@ struct BinAxis {
     int nb, s;
 };
 
+// The FP64 definition, out of line: inlined, the compiler predicates these
+// FP64 instructions into every particle's path, where they occupy the FP64
+// pipe even when the predicate is off.
+__device__ __noinline__ int coarse_bin_fp64(long long u, double cs_unit, double f)
+{
+    return (int)((double)u * cs_unit * f);
+}
+
 __device__ __forceinline__ int coarse_bin(int cell0, int off, const BinAxis &a)
 {
     const float t = fmaf((float)cell0, a.f_cell, (float)off * a.f_unit);
     const float fl = floorf(t), fr = t - fl, m = fmaf(t, 3e-7f, 1e-6f);
     int i = (int)fl;
-    if (off < 0 || fr < m || fr > 1.0f - m)
-        i = (int)(((double)(((long long)cell0 << a.s) + off) * a.cs_unit) * a.f);
+    if (off < 0 || fr < m || fr > 1.0f - m) i = coarse_bin_fp64(((long long)cell0 << a.s) + off, a.cs_unit, a.f);
     return min(max(i, 0), a.nb - 1);
 }
 
